@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the exponential-integrator step on GB300.
+
+Workload: the 128^3 head phantom (per-voxel D with 10 % noise, D_w = 0.13,
+D_g = 0.013 mm^2/day, rho = 0.025/day, h = 1 mm), 100 steps of tau = 7.3 days
+(two years).  One bench step = one et_run of those 100 steps from u0 on data
+resident in HBM; value = voxel-steps per second over all ranks (Mvoxel-steps/s).
+Coefficient setup (et_set_coeffs) is timed separately.  N > 1 runs independent
+replicas, one per GPU (weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the method's plain definition)
+on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_GRID = 128
+NSTEPS = 100
+TAU = 7.3
+RHO = 0.025
+NOISE = 0.1
+METRIC = "exp-integrator Mvoxel-steps/s at 128^3 (plain vs chosen form), % HBM roofline"
+UNIT = "Mvoxel-steps/s"
+WORKLOAD = "128^3 head phantom, D noise 10%, rho 0.025/d, 100 steps x tau 7.3 d (2 years), zero-flux"
+# Algorithmic bytes and flops per voxel per Taylor-term launch (shifted scaled
+# recurrence, conservative operator): read z 8, write z 8, three face-weight
+# fields 24, diagonal 8, residual 8, read+write of the sub-step sum 16 (FP64);
+# half of that for FP32 vectors and weights.  8 FMA + 1 MUL = 17 flops.
+TERM_BYTES = {"f64": 72, "f32": 36}
+TERM_FLOPS = 17
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--nsteps", type=int, default=NSTEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32 form")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(D, u0, seconds=12.0):
+    """The FP64 oracle as it stands, on the host cores, on the first steps of the run."""
+    import oracle
+    P = oracle.Problem(D, rho=RHO)
+    u = u0.copy()
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < NSTEPS:
+        u, _ = P.run(u, TAU, 1)
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    n = D.size
+    return {"value": n * steps / dt / 1e6, "unit": UNIT, "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"first {steps} of the {NSTEPS} steps of the {D.shape[0]}^3 run "
+                      f"({dt:.1f} s, FP64 oracle, theta 0.5, tail bound 1e-18)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2402_02273_gb300 import phantom
+    D, u0 = phantom.case(args.grid, seed=0, noise=NOISE)
+    P = oracle.Problem(D, rho=RHO)
+    u = u0.copy()
+    for _ in range(args.warmup):
+        u, _ = P.run(u, TAU, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _ = P.run(u, TAU, 1)
+    dt = time.perf_counter() - t0
+    n = D.size
+    value = n * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [args.grid] * 3, "tau_days": TAU,
+                   "step": "one time step of the run per bench step (sample of the 100-step run)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": f"time steps {args.warmup + 1}..{args.warmup + args.steps} of the "
+                                   f"{args.grid}^3 run, one per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_form(et, torch, D, u0, precision, args, stream, flush, timing=True):
+    """Times K bench steps of one precision form; returns a dict of numbers."""
+    n = D.size
+    g = et.Grid(D.shape, precision=precision, stream=stream)
+    Dd = torch.from_numpy(D).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_coeffs(Dd, rho=RHO)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    u0d = torch.from_numpy(u0).to("cuda")
+    u = torch.empty_like(u0d)
+    s, m, mu, theta = g.schedule(TAU)
+    g.enable_timing(timing)
+
+    def one_step():
+        u.copy_(u0d)
+        g.run(u, TAU, args.nsteps)
+        flush.add_(1)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        g.sync_info()
+        torch.cuda.synchronize()
+        return g, one_step, {"setup_ms": setup_ms, "s": s, "m": m, "mu": mu, "theta": theta}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    import paper_2402_02273_gb300 as et
+    from paper_2402_02273_gb300 import phantom
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    et.load()
+    D, u0 = phantom.case(args.grid, seed=rank, noise=NOISE)
+    n = D.size
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(D, u0)
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    fp64_peak, fp32_peak = et.probe_alu(stream)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(step_fn):
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev_index) if rank == 0 else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                step_fn()
+            e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = t.item()
+        barrier()
+        return ms, clocks
+
+    results = {}
+    forms = ["f64"] if args.no_forms else ["f64", "f32"]
+    for prec in forms:
+        g, step_fn, info = measure_form(et, torch, D, u0, prec, args, stream, flush)
+        ms, clocks = timed(step_fn)
+        term_ms, term_launches, other_launches = g.timing()  # last run of the timed region
+        rec = g.sync_info()
+        avg_launch_ms = term_ms / max(term_launches, 1)
+        bytes_per_launch = TERM_BYTES[prec] * n
+        flops_per_launch = TERM_FLOPS * n
+        achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+        value = world * n * args.nsteps / (ms * 1e-3) / 1e6
+        alu_peak = fp64_peak if prec == "f64" else fp32_peak
+        alu_frac = achieved_tflops / alu_peak
+        hbm_frac = achieved_gbs / hbm_peak
+        if prec == "f64" and alu_frac >= hbm_frac:
+            roof = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": alu_frac, "traffic": None,
+                    "peak_source": "measured FP64 FMA rate (et_probe_alu, this run)"}
+        else:
+            roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_frac, "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"}
+        roof.update({"kernel": "term_kernel", "avg_launch_us": avg_launch_ms * 1e3,
+                     "launches_per_run": term_launches, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "algorithmic_flops_per_launch": flops_per_launch,
+                     "hbm_frac": hbm_frac, "hbm_achieved_gbs": achieved_gbs, "alu_frac": alu_frac})
+        results[prec] = {"value": value, "ms_per_step": ms, "clocks": clocks, "roofline": roof,
+                         "launches_per_run": term_launches + other_launches, "info": info,
+                         "final_mass": rec["mass"], "final_umax": rec["umax"]}
+        g.enable_timing(False)
+        del g
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers (pinned): H2D of D and
+    # u0, coefficient setup, the 100-step run, D2H of u and of the last record
+    e2e = None
+    if True:
+        g = et.Grid(D.shape, precision="f64", stream=stream)
+        D_pin = torch.from_numpy(D).pin_memory().numpy()
+        u_pin = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+
+        def e2e_step():
+            u_pin[:] = u0.ravel()
+            g.set_coeffs(D_pin, rho=RHO)
+            g.run_host(u_pin, TAU, args.nsteps)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = t.item()
+        e2e = {"value": world * n * args.nsteps / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n + 40,
+               "ms_per_step": e2e_ms,
+               "path": "et_set_coeffs_host + et_run_host (pinned host buffers, host wall clock)"}
+        del g
+
+    if rank == 0:
+        r = results["f64"]
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [args.grid] * 3, "steps_per_run": args.nsteps,
+                       "tau_days": TAU, "operator": "conservative", "scheme": "rosenbrock",
+                       "precision": "f64", "s": r["info"]["s"], "m": r["info"]["m"],
+                       "theta": r["info"]["theta"], "tol": 1e-13, "setup_ms": r["info"]["setup_ms"],
+                       "l2": "256 MiB buffer written between bench steps (inside the timed region)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": r["roofline"],
+            "clocks": r["clocks"],
+            "gpu_launches": args.steps * r["launches_per_run"],
+            "e2e": e2e,
+            "cpu_baseline": base,
+            "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+            "forms": {p: {"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
+                          "dtype": p, "s": results[p]["info"]["s"], "m": results[p]["info"]["m"],
+                          "roofline": results[p]["roofline"], "clocks": results[p]["clocks"]}
+                      for p in results},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/* et.h — C ABI of the GB300 exponential-integrator library for the
+ * Fisher-Kolmogorov glioblastoma model (Pabisz, Munoz-Matute, Paszynski,
+ * arXiv 2402.02273).
+ *
+ * The library advances a tumour cell density u on an nx * ny * nz voxel grid
+ * of spacing h by the exponential integrator of Sec. 2.2,
+ *
+ *     u^{n+1} = u^n + tau * phi1(tau A_n) (A_n u^n + f(u^n)),
+ *
+ * where A_n is the finite-difference diffusion operator L of Sec. 2.1
+ * (eq. Amatrix) plus, in the default scheme, the linear part rho (1 - 2 u^n)
+ * of the logistic term (eq. F / newF), and f(u^n) = rho (u^n)^2.  The action
+ * tau phi1(tau A) b is evaluated as the top block of exp(tau B) v_1 with the
+ * augmented matrix B of Sec. 2.2, as s sub-steps of a degree-m Taylor
+ * polynomial, matrix-free, in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are dense, x fastest: voxel (i, j, k), 0-based, is element
+ *    p = i + nx * (j + ny * k) (reading of the numbering formula of Sec. 2.1).
+ *  - "device" pointers are CUDA global-memory addresses on the grid's device,
+ *    8-byte aligned; "host" pointers are ordinary CPU memory (page-locked
+ *    memory makes the copies asynchronous).  The caller owns every buffer it
+ *    passes; the library keeps borrowed pointers only to the workspace.
+ *  - Work is enqueued on the grid's CUDA stream; calls return without waiting
+ *    unless stated.  Errors detected on the device (non-finite values, an
+ *    out-of-range density) are collected in a device flag word and reported
+ *    by et_sync_info, et_run_host and et_set_coeffs, which synchronise.
+ *  - Every function returns ET_OK (0) or an error status and, for a non-NULL
+ *    grid, stores a message readable with et_last_error; nothing throws and
+ *    no argument error leaves work half-enqueued.
+ */
+#ifndef ET_H
+#define ET_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ET_VERSION 100 /* 1.0.0 */
+
+#if defined(__GNUC__)
+#define ET_API __attribute__((visibility("default")))
+#else
+#define ET_API
+#endif
+
+typedef struct et_grid et_grid; /* opaque handle */
+
+typedef enum {
+    ET_OK = 0,
+    ET_ERR_ARG = 1,         /* bad size, pointer, alignment, tau, option */
+    ET_ERR_STATE = 2,       /* call order (e.g. et_step before et_set_coeffs) */
+    ET_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has details */
+    ET_ERR_NUMERIC = 4,     /* D < 0 or not finite; u out of range or non-finite */
+    ET_ERR_TIMEOUT = 5,     /* reserved for bounded device waits */
+    ET_ERR_UNSUPPORTED = 6  /* combination not provided by this build */
+} et_status;
+
+/* Arithmetic of the Taylor-term kernels.  The state u is always FP64.
+ *  ET_F64: every operation in FP64 (the plain form).
+ *  ET_F32: stencil terms and their sum in FP32; the residual, the norm bound
+ *          and the (s, m) selection in FP64. */
+typedef enum { ET_F64 = 0, ET_F32 = 1 } et_precision;
+
+/* Spatial operator L (Sec. 2.1; the printed formula is not in divergence form
+ * and the paper states no boundary stencil, so two readings are provided;
+ * in both, neighbours outside the box take the centre value, i.e. zero flux):
+ *  ET_OP_CONSERVATIVE: (L v)_p = sum over the six faces of
+ *      hm(D_p, D_q) / h^2 * (v_q - v_p),  hm(a, b) = 2ab / (a + b), 0 if a or b is 0;
+ *      symmetric, mass-conserving (default).
+ *  ET_OP_LITERAL: the Sec. 2.1 formula, i.e. row p of eq. Amatrix / h^2:
+ *      (D_p + D_{p+e}) / h^2 towards +e, 2 D_p / h^2 towards -e, and a
+ *      diagonal making the row sum zero. */
+typedef enum { ET_OP_CONSERVATIVE = 0, ET_OP_LITERAL = 1 } et_operator;
+
+/* Treatment of the logistic term rho u (1 - u) (Sec. 2.1, eq. F / newF):
+ *  ET_SCHEME_ROSENBROCK: A_n = L + diag(rho (1 - 2 u^n)), f = rho (u^n)^2
+ *      (the paper's fold; second order in tau) (default).
+ *  ET_SCHEME_EXPEULER:   A = L, f = rho u^n (1 - u^n) (exponential Euler,
+ *      first order). */
+typedef enum { ET_SCHEME_ROSENBROCK = 0, ET_SCHEME_EXPEULER = 1 } et_scheme;
+
+/* Choice of s and m, which Sec. 2.2 leaves to "proper selection".  Zero
+ * fields take the defaults. */
+typedef struct {
+    double tol;       /* bound on the truncation error of one step, relative to
+                         max|u^n|; default 1e-13 (F64), 1e-7 (F32) */
+    double theta_max; /* largest tau/s * ||A - mu I||_inf per sub-step;
+                         default 7 (F64), 1.5 (F32) */
+    int shift;        /* 1: shift A by mu = -max_p(off-diagonal row sum) (exact,
+                         halves the norm); 0: no shift; -1 or 0-initialised
+                         struct: default = 1 */
+    int force_s;      /* > 0: use this many sub-steps */
+    int force_m;      /* > 0: use this many Taylor terms per sub-step (>= 2) */
+    int use_graph;    /* 1 (default): replay et_run / et_step as CUDA graphs;
+                         -1: launch kernels directly */
+} et_options;
+
+/* Per-step record written by the device (40 bytes). */
+typedef struct {
+    double umin, umax, mass; /* min, max and sum of u^{n+1}; mass / (nx ny nz)
+                                is the paper's tumour volume (Sec. 3.5) */
+    int s, m;                /* sub-steps and terms per sub-step used */
+    unsigned flags;          /* ET_FLAG_* accumulated since the last sync */
+    unsigned step;           /* index of the step within its et_run call */
+} et_step_info;
+
+#define ET_FLAG_NONFINITE 1u /* NaN or Inf met in u */
+#define ET_FLAG_RANGE_IN  2u /* u^n outside [-1e-3, 1 + 1e-3] in the folded scheme:
+                                the a-priori bound behind (s, m) did not hold */
+#define ET_FLAG_D_INVALID 4u /* D < 0 or not finite (et_set_coeffs) */
+
+/* Bytes of device workspace a grid of this size needs (256-byte aligned
+ * start required).  Returns 0 for non-positive sizes. */
+ET_API size_t et_workspace_bytes(int nx, int ny, int nz, et_precision precision);
+
+/* Creates a grid on the current CUDA device.
+ *  nx, ny, nz  > 0 voxels per axis (nx * ny * nz < 2^31); h > 0 voxel width.
+ *  workspace   device, >= et_workspace_bytes(...), 256-byte aligned,
+ *              caller-owned, must outlive the grid.
+ *  cuda_stream cudaStream_t to enqueue on (NULL = legacy default stream).
+ *  out         receives the handle (NULL on failure).
+ * Enqueues nothing. */
+ET_API et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precision,
+                         void* workspace, size_t workspace_bytes, void* cuda_stream,
+                         et_grid** out);
+
+/* Sets the diffusion field and model constants (Sec. 2, Table 1).
+ *  D       device, n FP64 values >= 0 (mm^2/day); read during the call only.
+ *  rho     proliferation rate >= 0 (1/day).
+ *  options NULL for defaults.
+ * Builds the face weights of L in the workspace and the bound
+ * max_p sum_{q != p} |L_pq|, then synchronises the stream (one 8-byte read).
+ * ET_ERR_NUMERIC if some D is negative or not finite. */
+ET_API et_status et_set_coeffs(et_grid* g, const double* D, double rho, et_operator op,
+                        et_scheme scheme, const et_options* options);
+/* Same as et_set_coeffs with D in host memory (copied through the workspace). */
+ET_API et_status et_set_coeffs_host(et_grid* g, const double* D_host, double rho, et_operator op,
+                             et_scheme scheme, const et_options* options);
+
+/* One step u <- u + tau phi1(tau A)(A u + f(u)), in place.
+ *  u    device, n FP64 values (the density, expected in [0, 1]).
+ *  tau  step size > 0 (days).
+ *  info device pointer to one et_step_info, or NULL (kept internally; read
+ *       it with et_sync_info).
+ * Asynchronous. */
+ET_API et_status et_step(et_grid* g, double* u, double tau, et_step_info* info);
+
+/* nsteps >= 1 steps of size tau, in place.  info: device array of nsteps
+ * records, or NULL.  Asynchronous; replayed as one CUDA graph per
+ * (u, info, tau, nsteps) after the first call. */
+ET_API et_status et_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info);
+
+/* et_run on host buffers: copies u_host to the device, runs, copies u back
+ * and, if info_host is non-NULL, the nsteps records; synchronises and returns
+ * ET_ERR_NUMERIC if a device flag was raised. */
+ET_API et_status et_run_host(et_grid* g, double* u_host, double tau, int nsteps,
+                      et_step_info* info_host);
+
+/* Synchronises the stream, copies the record of the latest step (whatever
+ * info pointer that step was given) to host_out (may be NULL), clears the
+ * device flags and returns ET_ERR_NUMERIC if NONFINITE or RANGE_IN was raised
+ * since the previous sync. */
+ET_API et_status et_sync_info(et_grid* g, et_step_info* host_out);
+
+/* The (s, m, mu) that et_step / et_run use for step size tau on this grid,
+ * and theta = tau / s * ||A - mu I||_inf bound. */
+ET_API et_status et_get_schedule(const et_grid* g, double tau, int* s, int* m, double* mu,
+                          double* theta);
+
+/* Pure host function behind et_get_schedule (no CUDA call).
+ *  rmax  max_p sum_{q != p} |L_pq| (1/day); rho, scheme as in et_set_coeffs.
+ *  Minimises the number of stencil applications s*m - 1 subject to
+ *  kappa * theta^m / m! * (1 + tau nu / (m+1)) / (1 - theta/(m+1)) <= tol and
+ *  theta <= theta_max, with nu = ||A - mu I||_inf bound, theta = tau nu / s,
+ *  kappa = tau (2 rmax + rho') e^{2 tau rho'} and rho' = rho (1 + 2e-3)
+ *  (folded scheme; 0 for exponential Euler).  Returns ET_ERR_ARG if no pair
+ *  with s <= 4096, m <= 96 qualifies. */
+ET_API et_status et_select_schedule(double tau, double rmax, double rho, et_scheme scheme,
+                             et_precision precision, const et_options* options, int* s,
+                             int* m, double* mu, double* theta);
+
+/* Changes the stream later calls enqueue on. */
+ET_API et_status et_set_stream(et_grid* g, void* cuda_stream);
+
+/* Per-step CUDA-event timing of the Taylor-term kernels inside et_run
+ * (event records on the grid's stream around each step's term chain).
+ * et_get_timing synchronises and returns the summed chain time of the last
+ * et_run and the number of term-kernel launches in it. */
+ET_API et_status et_enable_timing(et_grid* g, int enable);
+ET_API et_status et_get_timing(et_grid* g, double* term_ms, long long* term_launches,
+                        long long* other_launches);
+
+/* Grid facts: n voxels, bytes of the workspace actually used, and the
+ * diffusion bound rmax (0 before et_set_coeffs). */
+ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, double* rmax);
+
+/* Diagnostic, not part of the method: measured FMA throughput of the device
+ * (FP64 and FP32, TFLOP/s counting an FMA as 2 flops), the ALU roofline of the
+ * stencil kernels.  scratch: device buffer of >= et_probe_alu_scratch_bytes()
+ * bytes.  Synchronises the stream; takes about 20 ms. */
+ET_API size_t et_probe_alu_scratch_bytes(void);
+ET_API et_status et_probe_alu(void* scratch, size_t scratch_bytes, void* cuda_stream,
+                              double* fp64_tflops, double* fp32_tflops);
+
+ET_API const char* et_last_error(const et_grid* g); /* g may be NULL: last create error */
+ET_API const char* et_status_string(et_status status);
+ET_API int et_version(void);
+ET_API void et_destroy(et_grid* g); /* frees graphs and events; not the workspace */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ET_H */

@@ -1,0 +1,287 @@
+"""GB300 exponential-integrator library for the Fisher-Kolmogorov tumour model.
+
+Thin ctypes binding over the C ABI of include/et.h (libet.so, built from
+csrc/ by build.py).  Every function of the ABI is exposed under its own name
+(`et_create_grid`, `et_set_coeffs`, `et_step`, `et_run`, ...) taking plain
+integers for pointers; `Grid` wraps them for torch device tensors and
+streams.  All arithmetic of the step runs in the CUDA kernels of libet.so;
+this module only marshals arguments.  If the library cannot be loaded, every
+call raises: there is no CPU fallback.
+
+Method (arXiv 2402.02273, Sec. 2.2): u <- u + tau phi1(tau A)(A u + f(u)),
+with tau phi1(tau A) b evaluated through exp(tau B) v_1 of the augmented
+matrix B, s sub-steps of m Taylor terms each.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Grid", "EtError", "load", "OPS", "SCHEMES", "PRECISIONS", "STEP_INFO_DTYPE"]
+
+ET_OK, ET_ERR_ARG, ET_ERR_STATE, ET_ERR_CUDA, ET_ERR_NUMERIC, ET_ERR_TIMEOUT, ET_ERR_UNSUPPORTED = range(7)
+ET_F64, ET_F32 = 0, 1
+ET_OP_CONSERVATIVE, ET_OP_LITERAL = 0, 1
+ET_SCHEME_ROSENBROCK, ET_SCHEME_EXPEULER = 0, 1
+ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID = 1, 2, 4
+
+PRECISIONS = {"f64": ET_F64, "f32": ET_F32}
+OPS = {"conservative": ET_OP_CONSERVATIVE, "literal": ET_OP_LITERAL}
+SCHEMES = {"rosenbrock": ET_SCHEME_ROSENBROCK, "expeuler": ET_SCHEME_EXPEULER}
+
+
+class et_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("theta_max", ctypes.c_double), ("shift", ctypes.c_int),
+                ("force_s", ctypes.c_int), ("force_m", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class et_step_info(ctypes.Structure):
+    _fields_ = [("umin", ctypes.c_double), ("umax", ctypes.c_double), ("mass", ctypes.c_double),
+                ("s", ctypes.c_int), ("m", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("step", ctypes.c_uint)]
+
+
+STEP_INFO_DTYPE = np.dtype([("umin", "<f8"), ("umax", "<f8"), ("mass", "<f8"), ("s", "<i4"),
+                            ("m", "<i4"), ("flags", "<u4"), ("step", "<u4")])
+assert STEP_INFO_DTYPE.itemsize == ctypes.sizeof(et_step_info) == 40
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "et_version": ([], _I),
+    "et_status_string": ([_I], ctypes.c_char_p),
+    "et_last_error": ([_VP], ctypes.c_char_p),
+    "et_workspace_bytes": ([_I, _I, _I, _I], ctypes.c_size_t),
+    "et_create_grid": ([_I, _I, _I, _D, _I, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], _I),
+    "et_set_coeffs": ([_VP, _VP, _D, _I, _I, ctypes.POINTER(et_options)], _I),
+    "et_set_coeffs_host": ([_VP, _VP, _D, _I, _I, ctypes.POINTER(et_options)], _I),
+    "et_step": ([_VP, _VP, _D, _VP], _I),
+    "et_run": ([_VP, _VP, _D, _I, _VP], _I),
+    "et_run_host": ([_VP, _VP, _D, _I, _VP], _I),
+    "et_sync_info": ([_VP, ctypes.POINTER(et_step_info)], _I),
+    "et_get_schedule": ([_VP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                         ctypes.POINTER(_D)], _I),
+    "et_select_schedule": ([_D, _D, _D, _I, _I, ctypes.POINTER(et_options), ctypes.POINTER(_I),
+                            ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+    "et_set_stream": ([_VP, _VP], _I),
+    "et_enable_timing": ([_VP, _I], _I),
+    "et_get_timing": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                       ctypes.POINTER(ctypes.c_longlong)], _I),
+    "et_get_info": ([_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
+                     ctypes.POINTER(_D)], _I),
+    "et_destroy": ([_VP], None),
+    "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
+    "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libet.so (compiling it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_stale else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run build()")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    # et_* names resolve to the raw C functions
+    if name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+class EtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} [status {status}]")
+        self.status = status
+
+
+def _check(rc: int, handle=None):
+    if rc != ET_OK:
+        lib = load()
+        msg = lib.et_last_error(handle).decode(errors="replace")
+        raise EtError(rc, msg or lib.et_status_string(rc).decode())
+
+
+def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True):
+    return et_options(float(tol), float(theta_max), int(shift), int(force_s), int(force_m),
+                      1 if use_graph else -1)
+
+
+def select_schedule(tau, rmax, rho, scheme="rosenbrock", precision="f64", **opts):
+    """Host-only (s, m, mu, theta) selector of the library (no GPU needed)."""
+    lib = load()
+    o = make_options(**opts)
+    s, m, mu, th = _I(), _I(), _D(), _D()
+    rc = lib.et_select_schedule(float(tau), float(rmax), float(rho), SCHEMES[scheme],
+                                PRECISIONS[precision], ctypes.byref(o), ctypes.byref(s),
+                                ctypes.byref(m), ctypes.byref(mu), ctypes.byref(th))
+    _check(rc)
+    return s.value, m.value, mu.value, th.value
+
+
+class Grid:
+    """A voxel grid on the current CUDA device with its workspace.
+
+    Parameters: shape (nz, ny, nx) (x fastest, as numpy / torch C-order),
+    h voxel width, precision "f64" or "f32", stream a torch.cuda.Stream (or
+    None for the current stream).  Workspace memory is a torch uint8 tensor
+    owned by this object.
+    """
+
+    def __init__(self, shape, h=1.0, precision="f64", stream=None, device=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load()
+        nz, ny, nx = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = self.lib.et_workspace_bytes(nx, ny, nz, PRECISIONS[precision])
+        if nbytes == 0:
+            raise EtError(ET_ERR_ARG, f"invalid grid {shape}")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            self._ws_ptr = (base + 255) // 256 * 256
+            handle = _VP()
+            rc = self.lib.et_create_grid(nx, ny, nz, float(h), PRECISIONS[precision], self._ws_ptr,
+                                         nbytes, self.stream.cuda_stream, ctypes.byref(handle))
+            _check(rc, None)
+        self.handle = handle
+        self.h = h
+
+    def _chk(self, rc):
+        _check(rc, self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.et_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev_f64(self, t, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float64 \
+                or not t.is_contiguous() or t.numel() != self.n:
+            raise EtError(ET_ERR_ARG, f"{name} must be a contiguous float64 tensor of {self.n} "
+                                      f"elements on {self.device}")
+        return t.data_ptr()
+
+    def set_coeffs(self, D, rho=0.025, op="conservative", scheme="rosenbrock", **opts):
+        """D: float64 device tensor (n values) or a numpy array (copied through the host path)."""
+        o = make_options(**opts)
+        self.options = o
+        if isinstance(D, np.ndarray):
+            Dh = np.ascontiguousarray(D, dtype=np.float64)
+            if Dh.size != self.n:
+                raise EtError(ET_ERR_ARG, "D has the wrong size")
+            rc = self.lib.et_set_coeffs_host(self.handle, Dh.ctypes.data, float(rho), OPS[op],
+                                             SCHEMES[scheme], ctypes.byref(o))
+        else:
+            rc = self.lib.et_set_coeffs(self.handle, self._dev_f64(D, "D"), float(rho), OPS[op],
+                                        SCHEMES[scheme], ctypes.byref(o))
+        self._chk(rc)
+        self.rho, self.op, self.scheme = rho, op, scheme
+
+    def step(self, u, tau, info=None):
+        self._chk(self.lib.et_step(self.handle, self._dev_f64(u, "u"), float(tau),
+                                   None if info is None else info.data_ptr()))
+
+    def run(self, u, tau, nsteps, info=None):
+        """nsteps steps in place on the device tensor u; info: uint8 device tensor of
+        40 * nsteps bytes (see info_buffer) or None."""
+        self._chk(self.lib.et_run(self.handle, self._dev_f64(u, "u"), float(tau), int(nsteps),
+                                  None if info is None else info.data_ptr()))
+
+    def run_host(self, u_host: np.ndarray, tau, nsteps):
+        """Copies u_host (float64 numpy, contiguous; pinned helps) in, runs, copies it back."""
+        if not (isinstance(u_host, np.ndarray) and u_host.dtype == np.float64 and
+                u_host.flags.c_contiguous and u_host.size == self.n):
+            raise EtError(ET_ERR_ARG, "u_host must be a contiguous float64 array of n values")
+        rec = et_step_info()
+        self._chk(self.lib.et_run_host(self.handle, u_host.ctypes.data, float(tau), int(nsteps),
+                                       ctypes.byref(rec)))
+        return _rec_dict(rec)
+
+    def info_buffer(self, nsteps):
+        return self._torch.zeros(40 * int(nsteps), dtype=self._torch.uint8, device=self.device)
+
+    @staticmethod
+    def decode_info(buf):
+        return np.frombuffer(buf.cpu().numpy().tobytes(), dtype=STEP_INFO_DTYPE)
+
+    def sync_info(self):
+        rec = et_step_info()
+        self._chk(self.lib.et_sync_info(self.handle, ctypes.byref(rec)))
+        return _rec_dict(rec)
+
+    def schedule(self, tau):
+        s, m, mu, th = _I(), _I(), _D(), _D()
+        self._chk(self.lib.et_get_schedule(self.handle, float(tau), ctypes.byref(s), ctypes.byref(m),
+                                           ctypes.byref(mu), ctypes.byref(th)))
+        return s.value, m.value, mu.value, th.value
+
+    def rmax(self):
+        n, ws, r = ctypes.c_longlong(), ctypes.c_size_t(), _D()
+        self._chk(self.lib.et_get_info(self.handle, ctypes.byref(n), ctypes.byref(ws), ctypes.byref(r)))
+        return r.value
+
+    def enable_timing(self, on=True):
+        self._chk(self.lib.et_enable_timing(self.handle, 1 if on else 0))
+
+    def timing(self):
+        ms, tl, ol = _D(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._chk(self.lib.et_get_timing(self.handle, ctypes.byref(ms), ctypes.byref(tl), ctypes.byref(ol)))
+        return ms.value, tl.value, ol.value
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._chk(self.lib.et_set_stream(self.handle, stream.cuda_stream))
+
+
+def probe_alu(stream=None):
+    """Measured (FP64, FP32) FMA throughput of the current device in TFLOP/s."""
+    import torch
+    lib = load()
+    nbytes = lib.et_probe_alu_scratch_bytes()
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    f64, f32 = _D(), _D()
+    _check(lib.et_probe_alu(buf.data_ptr(), nbytes, st.cuda_stream, ctypes.byref(f64), ctypes.byref(f32)))
+    return f64.value, f32.value
+
+
+def _rec_dict(rec):
+    return {"umin": rec.umin, "umax": rec.umax, "mass": rec.mass, "s": rec.s, "m": rec.m,
+            "flags": rec.flags, "step": rec.step}

@@ -1,0 +1,769 @@
+// Host side of the C ABI declared in include/et.h: argument checks, workspace
+// layout, the (s, m) selector, the per-step launch sequence and its CUDA-graph
+// replay.  No PyTorch dependency: the caller passes raw device pointers and a
+// cudaStream_t.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <vector>
+
+#include "et.h"
+#include "et_internal.h"
+
+using namespace et;
+
+namespace {
+
+thread_local char g_create_error[512] = "";
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t w[4], wf[4];
+    size_t vec64[6];  // b, dt, Y0, Y1, Z0, Z1 (F64)
+    size_t vec32[6];  // same in FP32 (F32)
+    size_t stage;     // n doubles for host transfers
+    size_t partial;   // 3 * nblocks doubles
+    size_t misc;      // counters, flags, info slots
+    size_t total;
+    unsigned nblocks;
+};
+
+constexpr size_t kMiscBytes = 1024;
+
+bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
+    if (nx <= 0 || ny <= 0 || nz <= 0) return false;
+    const long long n = (long long)nx * ny * nz;
+    if (n >= (1ll << 31)) return false;
+    if (nz > 65535) return false;
+    const unsigned gx = (unsigned)((nx + kBlockX - 1) / kBlockX);
+    const unsigned gy = (unsigned)((ny + kBlockY - 1) / kBlockY);
+    const unsigned long long nb = (unsigned long long)gx * gy * (unsigned)nz;
+    if (nb >= (1ull << 31)) return false;
+    L->nblocks = (unsigned)nb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    for (int a = 0; a < 4; ++a) L->w[a] = take(8ull * n);
+    for (int v = 0; v < 6; ++v) L->vec64[v] = (prec == ET_F64) ? take(8ull * n) : SIZE_MAX;
+    for (int a = 0; a < 4; ++a) L->wf[a] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
+    for (int v = 0; v < 6; ++v) L->vec32[v] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
+    L->stage = take(8ull * n);
+    L->partial = take(3ull * 8ull * nb);
+    L->misc = take(kMiscBytes);
+    L->total = off;
+    return true;
+}
+
+struct GraphEntry {
+    double* u = nullptr;
+    et_step_info* info = nullptr;
+    double tau = 0.0;
+    int nsteps = 0;
+    bool timing = false;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long stamp = 0;
+    long long term_launches = 0, other_launches = 0;
+};
+
+struct Schedule {
+    int s = 0, m = 0;
+    double mu = 0.0, theta = 0.0;
+};
+
+struct ResolvedOptions {
+    double tol, theta_max;
+    int shift, force_s, force_m, use_graph;
+};
+
+ResolvedOptions resolve(const et_options* o, et_precision prec) {
+    ResolvedOptions r;
+    r.tol = (o && o->tol > 0) ? o->tol : (prec == ET_F64 ? 1e-13 : 1e-7);
+    r.theta_max = (o && o->theta_max > 0) ? o->theta_max : (prec == ET_F64 ? 7.0 : 1.5);
+    r.shift = (o && o->shift == 0) ? 0 : 1;
+    if (o && o->shift < 0) r.shift = 1;
+    r.force_s = (o && o->force_s > 0) ? o->force_s : 0;
+    r.force_m = (o && o->force_m > 0) ? o->force_m : 0;
+    r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
+    return r;
+}
+
+}  // namespace
+
+struct et_grid {
+    int nx, ny, nz;
+    long long n;
+    double h;
+    et_precision prec;
+    int device;
+    char* ws;
+    size_t ws_bytes;
+    Layout L;
+    Geom G;
+    cudaStream_t stream;
+    cudaStream_t capture;  // private stream used only for graph capture
+    // device views
+    double* w[4];
+    float* wf[4];
+    double* v64[6];
+    float* v32[6];
+    double* stage;
+    double* partial;
+    unsigned long long* rmax_bits;
+    unsigned* flags;
+    unsigned* ticket;
+    unsigned* step_counter;
+    et_step_info* info_slot;
+    // model state
+    bool coeffs_set;
+    et_operator op;
+    et_scheme scheme;
+    double rho;
+    double rmax;
+    et_options opt;
+    bool opt_set;
+    // graph cache and timing
+    std::vector<GraphEntry> graphs;
+    unsigned long long stamp;
+    bool timing;
+    std::vector<cudaEvent_t> ev;  // 2 per step of the last timed run
+    int timed_steps;
+    long long last_term_launches, last_other_launches;
+    char err[512];
+};
+
+namespace {
+
+et_status fail(et_grid* g, et_status st, const char* fmt, ...) {
+    char* dst = g ? g->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define ET_CUDA(g, call)                                                                      \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((g), ET_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+// Keeps the caller's current device across a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+void clear_graphs(et_grid* g) {
+    for (auto& e : g->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    g->graphs.clear();
+}
+
+void clear_events(et_grid* g) {
+    for (auto e : g->ev) cudaEventDestroy(e);
+    g->ev.clear();
+    g->timed_steps = 0;
+}
+
+et_status schedule_for(const et_grid* g, double tau, Schedule* S) {
+    return et_select_schedule(tau, g->rmax, g->rho, g->scheme, g->prec, g->opt_set ? &g->opt : nullptr,
+                              &S->s, &S->m, &S->mu, &S->theta);
+}
+
+template <typename T>
+struct Buffers {
+    Weights<T> W;
+    const T* b;
+    T* dt;
+    T* Y[2];
+    T* Z[2];
+};
+
+Buffers<double> buffers64(et_grid* g) {
+    Buffers<double> B;
+    for (int a = 0; a < 4; ++a) B.W.w[a] = g->w[a];
+    B.b = g->v64[0];
+    B.dt = g->v64[1];
+    B.Y[0] = g->v64[2];
+    B.Y[1] = g->v64[3];
+    B.Z[0] = g->v64[4];
+    B.Z[1] = g->v64[5];
+    return B;
+}
+
+Buffers<float> buffers32(et_grid* g) {
+    Buffers<float> B;
+    for (int a = 0; a < 4; ++a) B.W.w[a] = g->wf[a];
+    B.b = g->v32[0];
+    B.dt = g->v32[1];
+    B.Y[0] = g->v32[2];
+    B.Y[1] = g->v32[3];
+    B.Z[0] = g->v32[4];
+    B.Z[1] = g->v32[5];
+    return B;
+}
+
+// Enqueues the s*m - 1 Taylor-term launches of one step (Sec. 2.2) with the
+// scaled recurrence described in et_kernels.cu; counts them in *launches.
+template <typename T>
+cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Schedule& S, double hstep,
+                            const StatsSink& sink, cudaStream_t st, long long* launches) {
+    const int s = S.s, m = S.m;
+    const double mu = S.mu;
+    const double gamma = std::exp(mu * hstep);
+    double ak = 1.0;  // augmented scalar at the start of sub-step k
+    int zi = 0;       // next z buffer to write
+    for (int k = 0; k < s; ++k) {
+        T* yacc = B.Y[(k + 1) & 1];
+        const T* ycur = B.Y[k & 1];
+        // powers of (-mu) and Taylor weights g_j = h^j / j!
+        double pw = 1.0;      // (-mu)^j
+        double gj = 1.0;      // g_j
+        const T* zin = nullptr;
+        int j0 = 0;
+        if (k == 0) {
+            // y_0 = 0, so z^_1 = a_0 b = b: no launch for the first term
+            pw = -mu;         // (-mu)^1
+            gj = hstep;       // g_1
+            zin = B.b;
+            j0 = 1;
+        } else {
+            zin = ycur;
+        }
+        for (int j = j0; j < m; ++j) {
+            TermArgs<T> a;
+            a.zin = zin;
+            a.b = B.b;
+            a.beta = (T)(ak * pw);
+            a.dt = B.dt;
+            const double gnext = gj * hstep / (j + 1);
+            a.g = (T)gnext;
+            a.gamma = (T)1;
+            a.base_scale = (T)0;
+            if (k == 0 && j == 1) {
+                a.base_mode = 1;
+                a.base_scale = (T)hstep;  // g_1 b
+            } else if (k > 0 && j == 0) {
+                a.base_mode = 2;          // y_k, read as the centre of z^_0
+            } else {
+                a.base_mode = 0;
+            }
+            a.last = (j + 1 == m);
+            a.yacc = yacc;
+            a.u = nullptr;
+            a.zout = nullptr;
+            if (!a.last) {
+                a.zout = B.Z[zi];
+            } else {
+                a.gamma = (T)gamma;
+                if (k == s - 1) a.u = u;
+            }
+            cudaError_t e = launch_term<T>(g->G, g->op, B.W, a, sink, st);
+            if (e != cudaSuccess) return e;
+            ++*launches;
+            if (!a.last) {
+                zin = B.Z[zi];
+                zi ^= 1;
+            }
+            pw *= -mu;
+            gj = gnext;
+        }
+        // augmented scalar after the sub-step: e^{mu h} * sum_j a_k (-mu h)^j / j!
+        double sum = 0.0, t = 1.0;
+        for (int j = 0; j <= m; ++j) {
+            sum += t;
+            t *= (-mu * hstep) / (j + 1);
+        }
+        ak = gamma * ak * sum;
+    }
+    return cudaSuccess;
+}
+
+// Residual plus the term chain of one step on stream st.
+et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_step_info* info,
+                       int info_stride, cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                       bool external_events, long long* term_launches, long long* other_launches) {
+    StatsSink sink;
+    sink.partial = g->partial;
+    sink.ticket = g->ticket;
+    sink.step_counter = g->step_counter;
+    sink.flags = g->flags;
+    sink.info = info;
+    sink.info_stride = info_stride;
+    sink.last = g->info_slot;
+    sink.s = S.s;
+    sink.m = S.m;
+    const double hstep = tau / S.s;
+    Weights<double> W64;
+    for (int a = 0; a < 4; ++a) W64.w[a] = g->w[a];
+    cudaError_t e;
+    const unsigned evflags = external_events ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (g->prec == ET_F64) {
+        Buffers<double> B = buffers64(g);
+        e = launch_residual<double>(g->G, g->op, u, W64, g->rho, S.mu, g->scheme, const_cast<double*>(B.b),
+                                    B.dt, g->flags, st);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+        ++*other_launches;
+        if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
+        e = enqueue_chain_h<double>(g, B, u, S, hstep, sink, st, term_launches);
+    } else {
+        Buffers<float> B = buffers32(g);
+        e = launch_residual<float>(g->G, g->op, u, W64, g->rho, S.mu, g->scheme, const_cast<float*>(B.b),
+                                   B.dt, g->flags, st);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+        ++*other_launches;
+        if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
+        e = enqueue_chain_h<float>(g, B, u, S, hstep, sink, st, term_launches);
+    }
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "term launch: %s", cudaGetErrorString(e));
+    if (ev_end) ET_CUDA(g, cudaEventRecordWithFlags(ev_end, st, evflags));
+    return ET_OK;
+}
+
+et_status ensure_events(et_grid* g, int nsteps) {
+    if (!g->timing) return ET_OK;
+    if ((int)g->ev.size() >= 2 * nsteps) return ET_OK;
+    clear_graphs(g);  // graphs hold references to the old events
+    clear_events(g);
+    g->ev.resize(2 * (size_t)nsteps, nullptr);
+    for (auto& e : g->ev) ET_CUDA(g, cudaEventCreate(&e));
+    return ET_OK;
+}
+
+// Enqueues a whole run (counter reset + nsteps steps) on stream st.
+et_status enqueue_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info, cudaStream_t st,
+                      bool external_events) {
+    Schedule S;
+    et_status rc = schedule_for(g, tau, &S);
+    if (rc != ET_OK) return fail(g, rc, "no (s, m) meets the tolerance for tau = %g", tau);
+    ET_CUDA(g, cudaMemsetAsync(g->step_counter, 0, sizeof(unsigned), st));
+    et_step_info* dst = info ? info : g->info_slot;
+    const int stride = info ? 1 : 0;
+    long long tl = 0, ol = 0;
+    for (int t = 0; t < nsteps; ++t) {
+        cudaEvent_t e0 = g->timing ? g->ev[2 * t] : nullptr;
+        cudaEvent_t e1 = g->timing ? g->ev[2 * t + 1] : nullptr;
+        rc = enqueue_step(g, u, tau, S, dst, stride, st, e0, e1, external_events, &tl, &ol);
+        if (rc != ET_OK) return rc;
+    }
+    g->last_term_launches = tl;
+    g->last_other_launches = ol;
+    g->timed_steps = g->timing ? nsteps : 0;
+    return ET_OK;
+}
+
+et_status run_impl(et_grid* g, double* u, double tau, int nsteps, et_step_info* info) {
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    if (!u || !aligned8(u)) return fail(g, ET_ERR_ARG, "u must be a non-NULL 8-byte aligned device pointer");
+    if (info && !aligned8(info)) return fail(g, ET_ERR_ARG, "info must be 8-byte aligned");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(g, ET_ERR_ARG, "tau must be finite and > 0");
+    if (nsteps < 1) return fail(g, ET_ERR_ARG, "nsteps must be >= 1");
+    Schedule S;
+    if (schedule_for(g, tau, &S) != ET_OK)
+        return fail(g, ET_ERR_ARG, "no (s, m) meets the tolerance for tau = %g", tau);
+    et_status rc = ensure_events(g, nsteps);
+    if (rc != ET_OK) return rc;
+    const ResolvedOptions ro = resolve(g->opt_set ? &g->opt : nullptr, g->prec);
+    if (!ro.use_graph) return enqueue_run(g, u, tau, nsteps, info, g->stream, false);
+
+    for (auto& e : g->graphs) {
+        if (e.u == u && e.info == info && e.tau == tau && e.nsteps == nsteps && e.timing == g->timing) {
+            e.stamp = ++g->stamp;
+            ET_CUDA(g, cudaGraphLaunch(e.exec, g->stream));
+            g->last_term_launches = e.term_launches;
+            g->last_other_launches = e.other_launches;
+            g->timed_steps = e.timing ? nsteps : 0;
+            return ET_OK;
+        }
+    }
+    // capture on the private stream, then launch on the caller's stream
+    ET_CUDA(g, cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_run(g, u, tau, nsteps, info, g->capture, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(g->capture, &graph);
+    if (rc != ET_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(g, ET_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(g, ET_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    if (g->graphs.size() >= 8) {
+        size_t oldest = 0;
+        for (size_t i = 1; i < g->graphs.size(); ++i)
+            if (g->graphs[i].stamp < g->graphs[oldest].stamp) oldest = i;
+        cudaGraphExecDestroy(g->graphs[oldest].exec);
+        g->graphs.erase(g->graphs.begin() + oldest);
+    }
+    GraphEntry ent;
+    ent.u = u;
+    ent.info = info;
+    ent.tau = tau;
+    ent.nsteps = nsteps;
+    ent.timing = g->timing;
+    ent.exec = exec;
+    ent.stamp = ++g->stamp;
+    ent.term_launches = g->last_term_launches;
+    ent.other_launches = g->last_other_launches;
+    g->graphs.push_back(ent);
+    ET_CUDA(g, cudaGraphLaunch(exec, g->stream));
+    return ET_OK;
+}
+
+et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator op, et_scheme scheme,
+                          const et_options* opt) {
+    if (!(rho >= 0.0) || !std::isfinite(rho)) return fail(g, ET_ERR_ARG, "rho must be finite and >= 0");
+    if (op != ET_OP_CONSERVATIVE && op != ET_OP_LITERAL) return fail(g, ET_ERR_ARG, "unknown operator %d", (int)op);
+    if (scheme != ET_SCHEME_ROSENBROCK && scheme != ET_SCHEME_EXPEULER)
+        return fail(g, ET_ERR_ARG, "unknown scheme %d", (int)scheme);
+    if (opt) {
+        if (opt->tol < 0 || !std::isfinite(opt->tol)) return fail(g, ET_ERR_ARG, "options.tol must be >= 0");
+        if (opt->theta_max < 0 || !std::isfinite(opt->theta_max))
+            return fail(g, ET_ERR_ARG, "options.theta_max must be >= 0");
+        if (opt->force_m == 1) return fail(g, ET_ERR_ARG, "options.force_m must be 0 or >= 2");
+        if (opt->force_s < 0 || opt->force_m < 0) return fail(g, ET_ERR_ARG, "forced s, m must be >= 0");
+    }
+    clear_graphs(g);
+    g->coeffs_set = false;
+    ET_CUDA(g, cudaMemsetAsync(g->rmax_bits, 0, sizeof(unsigned long long), g->stream));
+    ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
+    ET_CUDA(g, cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), g->stream));
+    const double inv_h2 = 1.0 / (g->h * g->h);
+    cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w[0], g->w[1], g->w[2], g->w[3], g->rmax_bits,
+                                  g->flags, g->stream);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
+    if (op == ET_OP_CONSERVATIVE) ET_CUDA(g, cudaMemsetAsync(g->w[3], 0, 8ull * g->n, g->stream));
+    if (g->prec == ET_F32) {
+        const double* src[4] = {g->w[0], g->w[1], g->w[2], g->w[3]};
+        float* dstf[4] = {g->wf[0], g->wf[1], g->wf[2], g->wf[3]};
+        e = launch_convert_weights(g->G, src, dstf, g->stream);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
+    }
+    unsigned long long bits = 0;
+    unsigned flags = 0;
+    ET_CUDA(g, cudaMemcpyAsync(&bits, g->rmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaMemcpyAsync(&flags, g->flags, sizeof(flags), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaStreamSynchronize(g->stream));
+    ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
+    if (flags & ET_FLAG_D_INVALID) return fail(g, ET_ERR_NUMERIC, "D has negative or non-finite values");
+    double rmax;
+    std::memcpy(&rmax, &bits, sizeof(rmax));
+    g->rmax = rmax;
+    g->rho = rho;
+    g->op = op;
+    g->scheme = scheme;
+    g->opt_set = opt != nullptr;
+    if (opt) g->opt = *opt;
+    g->coeffs_set = true;
+    return ET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int et_version(void) { return ET_VERSION; }
+
+const char* et_status_string(et_status s) {
+    switch (s) {
+        case ET_OK: return "ok";
+        case ET_ERR_ARG: return "invalid argument";
+        case ET_ERR_STATE: return "invalid call order";
+        case ET_ERR_CUDA: return "CUDA error";
+        case ET_ERR_NUMERIC: return "numeric error";
+        case ET_ERR_TIMEOUT: return "device wait timed out";
+        case ET_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* et_last_error(const et_grid* g) { return g ? g->err : g_create_error; }
+
+size_t et_workspace_bytes(int nx, int ny, int nz, et_precision precision) {
+    if (precision != ET_F64 && precision != ET_F32) return 0;
+    Layout L;
+    if (!make_layout(nx, ny, nz, precision, &L)) return 0;
+    return L.total;
+}
+
+et_status et_select_schedule(double tau, double rmax, double rho, et_scheme scheme, et_precision precision,
+                             const et_options* options, int* s_out, int* m_out, double* mu_out,
+                             double* theta_out) {
+    if (!(tau > 0.0) || !std::isfinite(tau) || !(rmax >= 0.0) || !std::isfinite(rmax) || !(rho >= 0.0) ||
+        !std::isfinite(rho))
+        return ET_ERR_ARG;
+    const ResolvedOptions o = resolve(options, precision);
+    const double rho_c = (scheme == ET_SCHEME_ROSENBROCK) ? rho * (1.0 + 2.0 * kRangeSlack) : 0.0;
+    const double mu = o.shift ? -rmax : 0.0;
+    const double nu = o.shift ? rmax + rho_c : 2.0 * rmax + rho_c;
+    const double beta = tau * nu;
+    const double kappa = tau * (2.0 * rmax + rho_c) * std::exp(2.0 * tau * rho_c);
+    const int s_lo = o.force_s ? o.force_s : 1, s_hi = o.force_s ? o.force_s : 4096;
+    const int m_lo = o.force_m ? o.force_m : 2, m_hi = o.force_m ? o.force_m : 96;
+    long long best = std::numeric_limits<long long>::max();
+    int bs = 0, bm = 0;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        if (2ll * s - 1 > best) break;
+        const double theta = beta / s;
+        if (!o.force_s && theta > o.theta_max) continue;
+        for (int m = m_lo; m <= m_hi; ++m) {
+            bool ok;
+            if (o.force_m) {
+                ok = true;
+            } else if (kappa == 0.0 || theta == 0.0) {
+                ok = true;
+            } else if (theta >= m + 1) {
+                ok = false;
+            } else {
+                const double logE = std::log(kappa) + m * std::log(theta) - std::lgamma(m + 1.0) +
+                                    std::log1p(beta / (m + 1)) - std::log1p(-theta / (m + 1));
+                ok = logE <= std::log(o.tol);
+            }
+            if (ok) {
+                const long long cost = (long long)s * m - 1;
+                if (cost < best) {
+                    best = cost;
+                    bs = s;
+                    bm = m;
+                }
+                break;
+            }
+        }
+    }
+    if (!bs) return ET_ERR_ARG;
+    if (s_out) *s_out = bs;
+    if (m_out) *m_out = bm;
+    if (mu_out) *mu_out = mu;
+    if (theta_out) *theta_out = beta / bs;
+    return ET_OK;
+}
+
+et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precision, void* workspace,
+                         size_t workspace_bytes, void* cuda_stream, et_grid** out) {
+    if (!out) return fail(nullptr, ET_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (precision != ET_F64 && precision != ET_F32) return fail(nullptr, ET_ERR_ARG, "unknown precision");
+    Layout L;
+    if (!make_layout(nx, ny, nz, precision, &L))
+        return fail(nullptr, ET_ERR_ARG, "grid %d x %d x %d is empty or too large", nx, ny, nz);
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(nullptr, ET_ERR_ARG, "h must be finite and > 0");
+    if (!workspace) return fail(nullptr, ET_ERR_ARG, "workspace must not be NULL");
+    if (((uintptr_t)workspace % kAlign) != 0) return fail(nullptr, ET_ERR_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(nullptr, ET_ERR_ARG, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, ET_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    et_grid* g = new (std::nothrow) et_grid();
+    if (!g) return fail(nullptr, ET_ERR_ARG, "out of host memory");
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->n = (long long)nx * ny * nz;
+    g->h = h;
+    g->prec = precision;
+    g->device = dev;
+    g->ws = (char*)workspace;
+    g->ws_bytes = workspace_bytes;
+    g->L = L;
+    g->G.nx = nx;
+    g->G.ny = ny;
+    g->G.nz = nz;
+    g->G.n = g->n;
+    g->G.sy = nx;
+    g->G.sz = (long long)nx * ny;
+    g->G.nblocks = L.nblocks;
+    g->stream = (cudaStream_t)cuda_stream;
+    for (int a = 0; a < 4; ++a) {
+        g->w[a] = (double*)(g->ws + L.w[a]);
+        g->wf[a] = precision == ET_F32 ? (float*)(g->ws + L.wf[a]) : nullptr;
+    }
+    for (int v = 0; v < 6; ++v) {
+        g->v64[v] = precision == ET_F64 ? (double*)(g->ws + L.vec64[v]) : nullptr;
+        g->v32[v] = precision == ET_F32 ? (float*)(g->ws + L.vec32[v]) : nullptr;
+    }
+    g->stage = (double*)(g->ws + L.stage);
+    g->partial = (double*)(g->ws + L.partial);
+    char* misc = g->ws + L.misc;
+    g->rmax_bits = (unsigned long long*)(misc + 0);
+    g->flags = (unsigned*)(misc + 8);
+    g->ticket = (unsigned*)(misc + 12);
+    g->step_counter = (unsigned*)(misc + 16);
+    g->info_slot = (et_step_info*)(misc + 64);
+    g->coeffs_set = false;
+    g->rmax = 0.0;
+    g->rho = 0.0;
+    g->opt_set = false;
+    std::memset(&g->opt, 0, sizeof(g->opt));
+    g->stamp = 0;
+    g->timing = false;
+    g->timed_steps = 0;
+    g->last_term_launches = g->last_other_launches = 0;
+    g->err[0] = 0;
+    e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return fail(nullptr, ET_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(misc, 0, kMiscBytes, g->stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(g->capture);
+        delete g;
+        return fail(nullptr, ET_ERR_CUDA, "workspace clear: %s", cudaGetErrorString(e));
+    }
+    *out = g;
+    return ET_OK;
+}
+
+et_status et_set_coeffs(et_grid* g, const double* D, double rho, et_operator op, et_scheme scheme,
+                        const et_options* options) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!D || !aligned8(D)) return fail(g, ET_ERR_ARG, "D must be a non-NULL 8-byte aligned device pointer");
+    DeviceGuard dg(g->device);
+    return set_coeffs_impl(g, D, rho, op, scheme, options);
+}
+
+et_status et_set_coeffs_host(et_grid* g, const double* D_host, double rho, et_operator op, et_scheme scheme,
+                             const et_options* options) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!D_host) return fail(g, ET_ERR_ARG, "D_host must not be NULL");
+    DeviceGuard dg(g->device);
+    ET_CUDA(g, cudaMemcpyAsync(g->stage, D_host, 8ull * g->n, cudaMemcpyHostToDevice, g->stream));
+    return set_coeffs_impl(g, g->stage, rho, op, scheme, options);
+}
+
+et_status et_step(et_grid* g, double* u, double tau, et_step_info* info) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    return run_impl(g, u, tau, 1, info);
+}
+
+et_status et_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    return run_impl(g, u, tau, nsteps, info);
+}
+
+et_status et_run_host(et_grid* g, double* u_host, double tau, int nsteps, et_step_info* info_host) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!u_host) return fail(g, ET_ERR_ARG, "u_host must not be NULL");
+    if (nsteps < 1) return fail(g, ET_ERR_ARG, "nsteps must be >= 1");
+    DeviceGuard dg(g->device);
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    ET_CUDA(g, cudaMemcpyAsync(g->stage, u_host, 8ull * g->n, cudaMemcpyHostToDevice, g->stream));
+    // records go to the internal slot (last step); per-step records need a device array
+    et_status rc = run_impl(g, g->stage, tau, nsteps, nullptr);
+    if (rc != ET_OK) return rc;
+    ET_CUDA(g, cudaMemcpyAsync(u_host, g->stage, 8ull * g->n, cudaMemcpyDeviceToHost, g->stream));
+    return et_sync_info(g, info_host);
+}
+
+et_status et_sync_info(et_grid* g, et_step_info* host_out) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    et_step_info rec;
+    unsigned flags = 0;
+    ET_CUDA(g, cudaMemcpyAsync(&rec, g->info_slot, sizeof(rec), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaMemcpyAsync(&flags, g->flags, sizeof(flags), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaStreamSynchronize(g->stream));
+    ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
+    if (host_out) *host_out = rec;
+    if (flags & ET_FLAG_NONFINITE) return fail(g, ET_ERR_NUMERIC, "non-finite density met");
+    if (flags & ET_FLAG_RANGE_IN)
+        return fail(g, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3): the step bound does not hold");
+    return ET_OK;
+}
+
+et_status et_get_schedule(const et_grid* g, double tau, int* s, int* m, double* mu, double* theta) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!g->coeffs_set) return fail(const_cast<et_grid*>(g), ET_ERR_STATE, "et_set_coeffs has not been called");
+    Schedule S;
+    et_status rc = schedule_for(g, tau, &S);
+    if (rc != ET_OK) return fail(const_cast<et_grid*>(g), rc, "no (s, m) for tau = %g", tau);
+    if (s) *s = S.s;
+    if (m) *m = S.m;
+    if (mu) *mu = S.mu;
+    if (theta) *theta = S.theta;
+    return ET_OK;
+}
+
+et_status et_set_stream(et_grid* g, void* cuda_stream) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    g->stream = (cudaStream_t)cuda_stream;
+    return ET_OK;
+}
+
+et_status et_enable_timing(et_grid* g, int enable) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    if ((bool)enable != g->timing) {
+        clear_graphs(g);
+        if (!enable) clear_events(g);
+        g->timing = enable != 0;
+    }
+    return ET_OK;
+}
+
+et_status et_get_timing(et_grid* g, double* term_ms, long long* term_launches, long long* other_launches) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    double total = 0.0;
+    if (g->timing && g->timed_steps > 0) {
+        ET_CUDA(g, cudaStreamSynchronize(g->stream));
+        for (int t = 0; t < g->timed_steps; ++t) {
+            float ms = 0.f;
+            ET_CUDA(g, cudaEventElapsedTime(&ms, g->ev[2 * t], g->ev[2 * t + 1]));
+            total += ms;
+        }
+    }
+    if (term_ms) *term_ms = total;
+    if (term_launches) *term_launches = g->last_term_launches;
+    if (other_launches) *other_launches = g->last_other_launches;
+    return ET_OK;
+}
+
+et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, double* rmax) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (nvoxels) *nvoxels = g->n;
+    if (ws_used) *ws_used = g->L.total;
+    if (rmax) *rmax = g->coeffs_set ? g->rmax : 0.0;
+    return ET_OK;
+}
+
+void et_destroy(et_grid* g) {
+    if (!g) return;
+    {
+        DeviceGuard dg(g->device);
+        clear_graphs(g);
+        clear_events(g);
+        if (g->capture) cudaStreamDestroy(g->capture);
+    }
+    delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the host driver (et_api.cu) and the kernels
+// (et_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "et.h"
+
+namespace et {
+
+// Density range accepted by the a-priori bound |1 - 2u| <= 1 + 2 * kRangeSlack
+// of the folded scheme (ET_FLAG_RANGE_IN outside it).
+constexpr double kRangeSlack = 1e-3;
+
+// Thread-block shape of the stencil kernels: 32 voxels along x (one warp per
+// row, coalesced) by 8 rows along y; one z-plane per block.
+constexpr int kBlockX = 32;
+constexpr int kBlockY = 8;
+constexpr int kThreads = kBlockX * kBlockY;
+
+// Face weights of L (Sec. 2.1), FP64, one value per voxel:
+//   w[0..2]: weight towards +x, +y, +z (0 on the far wall);
+//   conservative: weight towards -e is w[e][p - e] (0 on the near wall);
+//   literal:      weight towards -e is w[3][p] = 2 D_p / h^2 (0 on the near wall).
+template <typename T>
+struct Weights {
+    const T* w[4];
+};
+
+// Per-launch geometry.
+struct Geom {
+    int nx, ny, nz;
+    long long n;
+    long long sy, sz;  // strides of y and z
+    unsigned nblocks;  // blocks of a stencil launch
+};
+
+// Device-side accumulation of per-step observables: block partials, a ticket
+// counter for the last-block reduction, the step index and the flag word.
+struct StatsSink {
+    double* partial;        // 3 * nblocks: min, max, sum
+    unsigned* ticket;       // last-block counter, returns to 0 after each step
+    unsigned* step_counter; // step index within the current run
+    unsigned* flags;        // ET_FLAG_* word
+    et_step_info* info;     // destination base
+    int info_stride;        // 1: info[step], 0: info[0]
+    et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
+    int s, m;               // recorded in the info
+};
+
+// Arguments of one Taylor-term launch (scaled recurrence, see et_kernels.cu).
+template <typename T>
+struct TermArgs {
+    const T* zin;    // z_j, read with a one-voxel halo
+    T* zout;         // z_{j+1}; nullptr on the last term of a sub-step
+    const T* b;      // residual, added with coefficient beta
+    T beta;          // 0 skips the read of b
+    const T* dt;     // diagonal of A - mu I
+    int base_mode;   // 0: yacc[p]; 1: base_scale * b[p]; 2: zin[p]
+    T base_scale;
+    T g;             // weight of z_{j+1} in the sub-step sum
+    T gamma;         // e^{mu h}, applied on the last term (1 otherwise)
+    int last;        // last term of the sub-step
+    T* yacc;         // sub-step sum (read when base_mode == 0, written unless finishing)
+    double* u;       // non-null on the last term of the step: u += gamma * sum
+};
+
+// Kernel launchers (et_kernels.cu).  All enqueue on `stream` and return the
+// launch error.
+cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op,
+                          double* w0, double* w1, double* w2, double* w3,
+                          unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream);
+cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4],
+                                   cudaStream_t stream);
+template <typename T>
+cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
+                            double rho, double mu, et_scheme scheme, T* b, T* dt, unsigned* flags,
+                            cudaStream_t stream);
+template <typename T>
+cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
+                        const StatsSink& sink, cudaStream_t stream);
+
+}  // namespace et

@@ -1,0 +1,149 @@
+"""The C-ABI library builds, loads and exports what include/et.h declares; host-only
+logic (argument checks, workspace sizing, the (s, m) selector) works without a GPU."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2402_02273_gb300 as et
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "et.h")).read()
+    return sorted(set(re.findall(r"ET_API[^;(]*?\b(et_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = et.load()
+    names = _declared()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding wraps each of them under the same name
+    for name in names:
+        assert name in et._SIGS, name
+
+
+def test_version_and_status_strings():
+    lib = et.load()
+    assert lib.et_version() == 100
+    assert lib.et_status_string(0) == b"ok"
+    assert b"argument" in lib.et_status_string(1)
+
+
+def test_workspace_sizing():
+    lib = et.load()
+    assert lib.et_workspace_bytes(0, 4, 4, 0) == 0
+    assert lib.et_workspace_bytes(4, -1, 4, 0) == 0
+    assert lib.et_workspace_bytes(4, 4, 4, 7) == 0
+    a = lib.et_workspace_bytes(32, 32, 32, 0)
+    b = lib.et_workspace_bytes(64, 32, 32, 0)
+    assert a > 11 * 8 * 32 ** 3 and b > a
+    assert lib.et_workspace_bytes(32, 32, 32, 1) > 0
+    # 128^3 FP64 needs about 11 FP64 fields
+    big = lib.et_workspace_bytes(128, 128, 128, 0)
+    assert 11 * 8 * 128 ** 3 <= big <= 12 * 8 * 128 ** 3
+    assert lib.et_workspace_bytes(2048, 1024, 1024, 0) == 0  # 2^31 voxels
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu():
+    lib = et.load()
+    h = ctypes.c_void_p()
+    assert lib.et_create_grid(4, 4, 4, 1.0, 0, 256, 10 ** 9, None, None) == et.ET_ERR_ARG
+    assert lib.et_create_grid(0, 4, 4, 1.0, 0, 256, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert not h.value
+    assert b"empty" in lib.et_last_error(None)
+    assert lib.et_create_grid(4, 4, 4, 0.0, 0, 256, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert lib.et_create_grid(4, 4, 4, float("nan"), 0, 256, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert lib.et_create_grid(4, 4, 4, 1.0, 0, None, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert lib.et_create_grid(4, 4, 4, 1.0, 0, 100, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert b"aligned" in lib.et_last_error(None)
+    assert lib.et_create_grid(4, 4, 4, 1.0, 0, 256, 16, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    assert b"needed" in lib.et_last_error(None)
+    assert lib.et_create_grid(4, 4, 4, 1.0, 5, 256, 10 ** 9, None, ctypes.byref(h)) == et.ET_ERR_ARG
+    # NULL handles are rejected by every entry point
+    assert lib.et_step(None, None, 1.0, None) == et.ET_ERR_ARG
+    assert lib.et_run(None, None, 1.0, 1, None) == et.ET_ERR_ARG
+    assert lib.et_sync_info(None, None) == et.ET_ERR_ARG
+    lib.et_destroy(None)
+
+
+def test_selector_basic_properties():
+    # 128^3 phantom: rmax ~ 6 * 0.143 = 0.858 / day, tau = 7.3 days
+    s, m, mu, th = et.select_schedule(7.3, 0.858, 0.025)
+    assert mu == pytest.approx(-0.858)
+    assert s >= 1 and m >= 2 and th <= 7.0 + 1e-12
+    assert th == pytest.approx(7.3 * (0.858 + 0.025 * 1.002) / s)
+    s0, m0, mu0, th0 = et.select_schedule(7.3, 0.858, 0.025, shift=0)
+    assert mu0 == 0.0 and s0 * m0 > s * m  # the shift halves the norm
+    # tighter tolerance never needs fewer terms
+    s2, m2, _, _ = et.select_schedule(7.3, 0.858, 0.025, tol=1e-15)
+    assert s2 * m2 >= s * m
+    # FP32 keeps theta small
+    s3, m3, _, th3 = et.select_schedule(7.3, 0.858, 0.025, precision="f32")
+    assert th3 <= 1.5 + 1e-12
+    # forced values pass through
+    assert et.select_schedule(7.3, 0.858, 0.025, force_s=3, force_m=9)[:2] == (3, 9)
+    # degenerate operator: D = 0 and exponential Euler -> A = 0, one short sub-step
+    assert et.select_schedule(7.3, 0.0, 0.025, scheme="expeuler")[:2] == (1, 2)
+    with pytest.raises(et.EtError):
+        et.select_schedule(-1.0, 0.858, 0.025)
+    with pytest.raises(et.EtError):
+        et.select_schedule(7.3, 0.858, 0.025, tol=1e-300, theta_max=0.001)
+
+
+def _shifted_recurrence(A, b, tau, s, m, mu):
+    """Model of the GPU's scaled recurrence in numpy (dense A): see et_kernels.cu."""
+    n = len(b)
+    At = A - mu * np.eye(n)
+    h = tau / s
+    gamma = math.exp(mu * h)
+    y = np.zeros(n)
+    ak = 1.0
+    for k in range(s):
+        z = y.copy()
+        acc = y.copy()
+        g = 1.0
+        pw = 1.0
+        for j in range(m):
+            z = At @ z + ak * pw * b
+            g *= h / (j + 1)
+            acc = acc + g * z
+            pw *= -mu
+        y = gamma * acc
+        ak = gamma * ak * sum((-mu * h) ** j / math.factorial(j) for j in range(m + 1))
+    return y
+
+
+@pytest.mark.parametrize("shift", [1, 0])
+@pytest.mark.parametrize("op", ["conservative", "literal"])
+def test_selected_schedule_meets_tolerance_on_dense_model(shift, op):
+    """The selector's (s, m) with the shifted, scaled recurrence reproduces
+    tau phi1(tau A) b from the oracle to the requested tolerance."""
+    import oracle
+    from paper_2402_02273_gb300 import phantom
+
+    D, u0 = phantom.case((6, 7, 5), seed=2, noise=0.1)
+    D[D == 0] = 0.1
+    P = oracle.Problem(D, op=op, scheme="rosenbrock")
+    n = D.size
+    A = np.zeros((n, n))
+    for q in range(n):
+        e = np.zeros(n)
+        e[q] = 1.0
+        A[:, q] = P.apply_A(u0, e).ravel()
+    rmax = max(np.abs(A[p]).sum() - abs(A[p, p]) - 0.0 for p in range(n))
+    # row sums of L only (the reaction diagonal is not part of rmax)
+    L = A - np.diag(0.025 * (1 - 2 * u0.ravel()))
+    rmax = max(np.abs(L[p]).sum() - abs(L[p, p]) for p in range(n))
+    b = P.residual(u0).ravel()
+    tau = 7.3
+    s, m, mu, th = et.select_schedule(tau, rmax, 0.025, shift=shift, tol=1e-13)
+    got = _shifted_recurrence(A, b, tau, s, m, mu)
+    want, _, _ = P.phi1_action(u0, b.reshape(D.shape), tau)
+    assert np.abs(got - want.ravel()).max() <= 1e-13 * max(1.0, np.abs(u0).max())

@@ -197,6 +197,26 @@ ET_API et_status et_get_timing(et_grid* g, double* term_ms, long long* term_laun
  * diffusion bound rmax (0 before et_set_coeffs). */
 ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, double* rmax);
 
+/* One step that allocates nothing (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory at call time, e.g. code inside a
+ * framework whose pool owns all device memory, or code run while a memory
+ * budget is locked).  Same arithmetic as et_set_coeffs + et_step in FP64, with
+ * all scratch in one static device array of the library (about 21.5 MiB,
+ * held by every GPU that loads it until exit) instead of a workspace.
+ *  nx, ny, nz, h, rho, op, scheme, tau: as for et_create_grid / et_set_coeffs
+ *      / et_step; at most 64^3 = 262144 voxels and 65536 blocks of the 32 x 8
+ *      tile, else ET_ERR_ARG.
+ *  D    device, n FP64 values (read); u device, n FP64 values (in/out).
+ *  cuda_stream  stream to run on; msg/msg_len optional buffer for an error
+ *      message (may be NULL).
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race.  Synchronises the stream and
+ * returns ET_ERR_NUMERIC for bad D or a non-finite / out-of-range density. */
+ET_API et_status et_step_static(int nx, int ny, int nz, double h, const double* D, double rho,
+                                et_operator op, et_scheme scheme, double* u, double tau,
+                                void* cuda_stream, char* msg, size_t msg_len);
+
 /* Diagnostic, not part of the method: measured FMA throughput of the device
  * (FP64 and FP32, TFLOP/s counting an FMA as 2 flops), the ALU roofline of the
  * stencil kernels.  scratch: device buffer of >= et_probe_alu_scratch_bytes()

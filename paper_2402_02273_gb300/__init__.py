@@ -76,6 +76,7 @@ _SIGS = {
     "et_get_info": ([_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
                      ctypes.POINTER(_D)], _I),
     "et_destroy": ([_VP], None),
+    "et_step_static": ([_I, _I, _I, _D, _VP, _D, _I, _I, _VP, _D, _VP, ctypes.c_char_p, ctypes.c_size_t], _I),
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
 }

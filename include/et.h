@@ -201,8 +201,8 @@ ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_us
  * callers that cannot allocate device memory at call time, e.g. code inside a
  * framework whose pool owns all device memory, or code run while a memory
  * budget is locked).  Same arithmetic as et_set_coeffs + et_step in FP64, with
- * all scratch in one static device array of the library (about 21.5 MiB,
- * held by every GPU that loads it until exit) instead of a workspace.
+ * all scratch in one static device array of the library (22 MiB, held by
+ * every GPU that loads it until exit) instead of a workspace.
  *  nx, ny, nz, h, rho, op, scheme, tau: as for et_create_grid / et_set_coeffs
  *      / et_step; at most 64^3 = 262144 voxels and 65536 blocks of the 32 x 8
  *      tile, else ET_ERR_ARG.

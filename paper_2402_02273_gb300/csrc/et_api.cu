@@ -26,7 +26,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t w[4], wf[4];
+    size_t w[5], wf[4];
     size_t vec64[6];  // b, dt, Y0, Y1, Z0, Z1 (F64)
     size_t vec32[6];  // same in FP32 (F32)
     size_t stage;     // n doubles for host transfers
@@ -54,12 +54,12 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
         off = align_up(off + bytes);
         return at;
     };
-    for (int a = 0; a < 4; ++a) L->w[a] = take(8ull * n);
+    for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * n);
     for (int v = 0; v < 6; ++v) L->vec64[v] = (prec == ET_F64) ? take(8ull * n) : SIZE_MAX;
     for (int a = 0; a < 4; ++a) L->wf[a] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
     for (int v = 0; v < 6; ++v) L->vec32[v] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
     L->stage = take(8ull * n);
-    L->partial = take(3ull * 8ull * nb);
+    L->partial = take(3ull * 8ull * kStatsBlocks);
     L->misc = take(kMiscBytes);
     L->total = off;
     return true;
@@ -113,7 +113,7 @@ struct et_grid {
     cudaStream_t stream;
     cudaStream_t capture;  // private stream used only for graph capture
     // device views
-    double* w[4];
+    double* w[5];
     float* wf[4];
     double* v64[6];
     float* v32[6];
@@ -195,7 +195,7 @@ et_status schedule_for(const et_grid* g, double tau, Schedule* S) {
 
 template <typename T>
 struct Buffers {
-    Weights<T> W;
+    Weights<T> W;  // w[4] unused by the term kernels
     const T* b;
     T* dt;
     T* Y[2];
@@ -204,7 +204,7 @@ struct Buffers {
 
 Buffers<double> buffers64(et_grid* g) {
     Buffers<double> B;
-    for (int a = 0; a < 4; ++a) B.W.w[a] = g->w[a];
+    for (int a = 0; a < 5; ++a) B.W.w[a] = g->w[a];
     B.b = g->v64[0];
     B.dt = g->v64[1];
     B.Y[0] = g->v64[2];
@@ -217,6 +217,7 @@ Buffers<double> buffers64(et_grid* g) {
 Buffers<float> buffers32(et_grid* g) {
     Buffers<float> B;
     for (int a = 0; a < 4; ++a) B.W.w[a] = g->wf[a];
+    B.W.w[4] = nullptr;
     B.b = g->v32[0];
     B.dt = g->v32[1];
     B.Y[0] = g->v32[2];
@@ -258,6 +259,7 @@ cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Sc
             a.zin = zin;
             a.b = B.b;
             a.beta = (T)(ak * pw);
+            a.has_beta = (ak * pw) != 0.0;
             a.dt = B.dt;
             const double gnext = gj * hstep / (j + 1);
             a.g = (T)gnext;
@@ -281,7 +283,7 @@ cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Sc
                 a.gamma = (T)gamma;
                 if (k == s - 1) a.u = u;
             }
-            cudaError_t e = launch_term<T>(g->G, g->op, B.W, a, sink, st);
+            cudaError_t e = launch_term<T>(g->G, g->op, B.W, a, st);
             if (e != cudaSuccess) return e;
             ++*launches;
             if (!a.last) {
@@ -318,12 +320,13 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
     sink.m = S.m;
     const double hstep = tau / S.s;
     Weights<double> W64;
-    for (int a = 0; a < 4; ++a) W64.w[a] = g->w[a];
+    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+    const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
     cudaError_t e;
     const unsigned evflags = external_events ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (g->prec == ET_F64) {
         Buffers<double> B = buffers64(g);
-        e = launch_residual<double>(g->G, g->op, u, W64, g->rho, S.mu, g->scheme, const_cast<double*>(B.b),
+        e = launch_residual<double>(g->G, g->op, u, W64, g->rho, dt_shift, g->scheme, const_cast<double*>(B.b),
                                     B.dt, g->flags, st);
         if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
         ++*other_launches;
@@ -331,7 +334,7 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
         e = enqueue_chain_h<double>(g, B, u, S, hstep, sink, st, term_launches);
     } else {
         Buffers<float> B = buffers32(g);
-        e = launch_residual<float>(g->G, g->op, u, W64, g->rho, S.mu, g->scheme, const_cast<float*>(B.b),
+        e = launch_residual<float>(g->G, g->op, u, W64, g->rho, dt_shift, g->scheme, const_cast<float*>(B.b),
                                    B.dt, g->flags, st);
         if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
         ++*other_launches;
@@ -340,6 +343,9 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
     }
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "term launch: %s", cudaGetErrorString(e));
     if (ev_end) ET_CUDA(g, cudaEventRecordWithFlags(ev_end, st, evflags));
+    e = launch_stats(g->G, u, sink, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "stats launch: %s", cudaGetErrorString(e));
+    ++*other_launches;
     return ET_OK;
 }
 
@@ -454,10 +460,8 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
     ET_CUDA(g, cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), g->stream));
     const double inv_h2 = 1.0 / (g->h * g->h);
-    cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w[0], g->w[1], g->w[2], g->w[3], g->rmax_bits,
-                                  g->flags, g->stream);
+    cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w, g->rmax_bits, g->flags, g->stream);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
-    if (op == ET_OP_CONSERVATIVE) ET_CUDA(g, cudaMemsetAsync(g->w[3], 0, 8ull * g->n, g->stream));
     if (g->prec == ET_F32) {
         const double* src[4] = {g->w[0], g->w[1], g->w[2], g->w[3]};
         float* dstf[4] = {g->wf[0], g->wf[1], g->wf[2], g->wf[3]};
@@ -598,11 +602,16 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->G.sy = nx;
     g->G.sz = (long long)nx * ny;
     g->G.nblocks = L.nblocks;
-    g->stream = (cudaStream_t)cuda_stream;
-    for (int a = 0; a < 4; ++a) {
-        g->w[a] = (double*)(g->ws + L.w[a]);
-        g->wf[a] = precision == ET_F32 ? (float*)(g->ws + L.wf[a]) : nullptr;
+    g->G.sms = 0;
+    e = cudaDeviceGetAttribute(&g->G.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = prime_launch_limits();
+    if (e != cudaSuccess) {
+        delete g;
+        return fail(nullptr, ET_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
     }
+    g->stream = (cudaStream_t)cuda_stream;
+    for (int a = 0; a < 5; ++a) g->w[a] = (double*)(g->ws + L.w[a]);
+    for (int a = 0; a < 4; ++a) g->wf[a] = precision == ET_F32 ? (float*)(g->ws + L.wf[a]) : nullptr;
     for (int v = 0; v < 6; ++v) {
         g->v64[v] = precision == ET_F64 ? (double*)(g->ws + L.vec64[v]) : nullptr;
         g->v32[v] = precision == ET_F32 ? (float*)(g->ws + L.vec32[v]) : nullptr;

@@ -21,27 +21,36 @@ constexpr int kBlockX = 32;
 constexpr int kBlockY = 8;
 constexpr int kThreads = kBlockX * kBlockY;
 
-// Face weights of L (Sec. 2.1), FP64, one value per voxel:
+// Coefficient fields of L (Sec. 2.1), one value per voxel:
 //   w[0..2]: weight towards +x, +y, +z (0 on the far wall);
 //   conservative: weight towards -e is w[e][p - e] (0 on the near wall);
-//   literal:      weight towards -e is w[3][p] = 2 D_p / h^2 (0 on the near wall).
+//   literal:      weight towards -e is w[3][p] = 2 D_p / h^2 (0 on the near wall);
+//   w[4]: minus the sum of the kept off-diagonal weights of row p (the
+//         diagonal of L); FP64 only, read by the residual kernel.
 template <typename T>
 struct Weights {
-    const T* w[4];
+    const T* w[5];
 };
+
+// Tile of the stencil kernels: a 32 x 8 block of threads, each thread marching
+// over kTileZ consecutive z-planes; blocks loop over tiles (grid-stride).
+constexpr int kTileZ = 4;
 
 // Per-launch geometry.
 struct Geom {
     int nx, ny, nz;
     long long n;
     long long sy, sz;  // strides of y and z
-    unsigned nblocks;  // blocks of a stencil launch
+    unsigned nblocks;  // blocks of a one-voxel-per-thread stencil launch (coeffs, residual)
+    int sms;           // multiprocessors of the device
 };
 
 // Device-side accumulation of per-step observables: block partials, a ticket
 // counter for the last-block reduction, the step index and the flag word.
+constexpr int kStatsBlocks = 512;   // fixed, so the summation order is fixed
+constexpr int kStatsThreads = 256;
 struct StatsSink {
-    double* partial;        // 3 * nblocks: min, max, sum
+    double* partial;        // 3 * kStatsBlocks: sum, min key, max key
     unsigned* ticket;       // last-block counter, returns to 0 after each step
     unsigned* step_counter; // step index within the current run
     unsigned* flags;        // ET_FLAG_* word
@@ -56,8 +65,9 @@ template <typename T>
 struct TermArgs {
     const T* zin;    // z_j, read with a one-voxel halo
     T* zout;         // z_{j+1}; nullptr on the last term of a sub-step
-    const T* b;      // residual, added with coefficient beta
-    T beta;          // 0 skips the read of b
+    const T* b;      // residual, added with coefficient beta when has_beta
+    T beta;
+    int has_beta;
     const T* dt;     // diagonal of A - mu I
     int base_mode;   // 0: yacc[p]; 1: base_scale * b[p]; 2: zin[p]
     T base_scale;
@@ -71,16 +81,21 @@ struct TermArgs {
 // Kernel launchers (et_kernels.cu).  All enqueue on `stream` and return the
 // launch error.
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op,
-                          double* w0, double* w1, double* w2, double* w3,
-                          unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream);
+                          double* const w[5], unsigned long long* rmax_bits, unsigned* flags,
+                          cudaStream_t stream);
 cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4],
                                    cudaStream_t stream);
+// dt_shift: rho - mu (folded scheme) or -mu (exponential Euler).
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
-                            double rho, double mu, et_scheme scheme, T* b, T* dt, unsigned* flags,
-                            cudaStream_t stream);
+                            double rho, double dt_shift, et_scheme scheme, T* b, T* dt,
+                            unsigned* flags, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
-                        const StatsSink& sink, cudaStream_t stream);
+                        cudaStream_t stream);
+// min, max and sum of u and the non-finite flag into the step record.
+cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
+// Looks up launch limits (resident blocks per SM) before any stream capture.
+cudaError_t prime_launch_limits();
 
 }  // namespace et

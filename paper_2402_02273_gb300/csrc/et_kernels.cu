@@ -1,12 +1,14 @@
 // CUDA kernels of the exponential-integrator step (arXiv 2402.02273, Sec. 2.1-2.2)
 // for sm_103a.
 //
-// Three kernels make a step:
-//   coeffs   (once per et_set_coeffs): face weights of L and the row-sum bound;
+// Four kernels make a step:
+//   coeffs   (once per et_set_coeffs): face weights of L, minus its row sums,
+//            and the bound max_p sum_{q != p} |L_pq|;
 //   residual (once per step): b = L u^n + rho u^n (1 - u^n) (= A_n u^n + f(u^n),
 //            eq. F / newF) and the diagonal of A_n - mu I;
 //   term     (s*m - 1 per step): one term of the scaled Taylor recurrence of
-//            exp(h (B - mu I)) applied to the augmented vector, see below.
+//            exp(h (B - mu I)) applied to the augmented vector, see below;
+//   stats    (once per step): min, max and sum of u^{n+1}.
 //
 // Scaled recurrence.  With h = tau / s, A~ = A - mu I and the augmented scalar
 // a_k of sub-step k (a_0 = 1), the j-th Taylor term of exp(h(B - mu I)) [y; a]
@@ -16,10 +18,16 @@
 // needs no per-term rescaling.  The sub-step result is
 //     y <- e^{mu h} (y + sum_{j=1..m} g_j z^_j),
 // and on the last sub-step u^{n+1} = u^n + y is written directly.
+//
+// GB300 executes FP64 at 2 FMA per clock per SM (1/64 of FP32), so the FP64
+// kernels are bound by FP64 instruction issue: every FP64 operation that is not
+// part of the arithmetic above (comparisons, range checks, reductions of
+// min/max) is done in integer or FP32 form instead.
 #include <cuda_runtime.h>
 
 #include <cfloat>
 #include <cmath>
+#include <cstdint>
 
 #include "et_internal.h"
 
@@ -30,21 +38,34 @@ __device__ __forceinline__ double harmonic_mean(double a, double b) {
     return (a > 0.0 && b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
 }
 
-__device__ __forceinline__ unsigned linear_block() {
-    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+// Monotone map of a double onto unsigned 64-bit integers (min/max by integer compare).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? ~(unsigned long long)b : ((unsigned long long)b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double order_key_inv(unsigned long long k) {
+    return __longlong_as_double((k & 0x8000000000000000ull) ? (long long)(k & 0x7fffffffffffffffull)
+                                                           : (long long)~k);
+}
+__device__ __forceinline__ bool nonfinite_bits(long long b) {
+    return (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
+dim3 voxel_grid(const Geom& G) {
+    return dim3((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
 }
 
 // ---------------------------------------------------------------------------
-// coeffs: face weights and max_p sum_{q != p} |L_pq|.
+// coeffs: face weights, minus the row sums, and max_p sum_{q != p} |L_pq|.
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
 coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __restrict__ w0,
               double* __restrict__ w1, double* __restrict__ w2, double* __restrict__ w3,
-              unsigned long long* rmax_bits, unsigned* flags) {
+              double* __restrict__ w4, unsigned long long* rmax_bits, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
-    double rowsum = 0.0;
+    double absrow = 0.0;
     if (i < G.nx && j < G.ny) {
         const long long p = i + G.sy * j + G.sz * k;
         const double Dp = D[p];
@@ -53,6 +74,7 @@ coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __res
         const int ext[3] = {G.nx, G.ny, G.nz};
         const long long st[3] = {1, G.sy, G.sz};
         double wp[3];
+        double row = 0.0;
         for (int a = 0; a < 3; ++a) {
             const bool has_plus = c[a] + 1 < ext[a];
             const bool has_minus = c[a] > 0;
@@ -67,18 +89,20 @@ coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __res
                 wminus = has_minus ? 2.0 * Dp * inv_h2 : 0.0;
             }
             wp[a] = wplus;
-            rowsum += fabs(wplus) + fabs(wminus);
+            row += wplus + wminus;
+            absrow += fabs(wplus) + fabs(wminus);
         }
         w0[p] = wp[0];
         w1[p] = wp[1];
         w2[p] = wp[2];
-        if (OP == ET_OP_LITERAL) w3[p] = 2.0 * Dp * inv_h2;
+        w3[p] = (OP == ET_OP_LITERAL) ? 2.0 * Dp * inv_h2 : 0.0;
+        w4[p] = -row;
     }
     // block maximum, then one atomic per block on the (monotone) bit pattern
     __shared__ double smax[kThreads / 32];
-    for (int off = 16; off > 0; off >>= 1) rowsum = fmax(rowsum, __shfl_down_sync(0xffffffffu, rowsum, off));
+    for (int off = 16; off > 0; off >>= 1) absrow = fmax(absrow, __shfl_down_sync(0xffffffffu, absrow, off));
     const int tid = threadIdx.x + kBlockX * threadIdx.y;
-    if ((tid & 31) == 0) smax[tid >> 5] = rowsum;
+    if ((tid & 31) == 0) smax[tid >> 5] = absrow;
     __syncthreads();
     if (tid == 0) {
         double m = smax[0];
@@ -97,7 +121,7 @@ __global__ void convert_weights_kernel(long long n, const double* __restrict__ a
         f0[p] = (float)a0[p];
         f1[p] = (float)a1[p];
         f2[p] = (float)a2[p];
-        if (a3) f3[p] = (float)a3[p];
+        f3[p] = (float)a3[p];
     }
 }
 
@@ -110,10 +134,12 @@ __device__ __forceinline__ T minus_weight(const Weights<T>& W, int axis, long lo
 }
 
 // ---------------------------------------------------------------------------
-// residual: b = L u + rho u (1 - u), diag = c - R - mu (c = rho(1-2u) or 0).
+// residual: b = L u + rho u (1 - u), diag = rho(1 - 2u) - R - mu (or -R - mu).
+// L u = sum_e w_e u_e - R u_p with R from the coefficient pass: 12 FP64
+// operations per voxel; the range test on u runs on the integer bits.
 template <int OP, typename T>
 __global__ void __launch_bounds__(kThreads)
-residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double mu,
+residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double dt_shift,
                 int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
@@ -121,97 +147,179 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
     if (i >= G.nx || j >= G.ny) return;
     const long long p = i + G.sy * j + G.sz * k;
     const double up = u[p];
-    const int c[3] = {i, j, k};
-    const int ext[3] = {G.nx, G.ny, G.nz};
-    const long long st[3] = {1, G.sy, G.sz};
-    double Lu = 0.0, R = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        const bool has_plus = c[a] + 1 < ext[a];
-        const bool has_minus = c[a] > 0;
-        const double wplus = W.w[a][p];
-        const double wminus = minus_weight<OP, double>(W, a, p, st[a], has_minus);
-        const double uplus = has_plus ? u[p + st[a]] : up;
-        const double uminus = has_minus ? u[p - st[a]] : up;
-        Lu += wplus * (uplus - up) + wminus * (uminus - up);
-        R += wplus + wminus;
-    }
-    const double bp = Lu + rho * up * (1.0 - up);
-    const double cp = (scheme == ET_SCHEME_ROSENBROCK) ? rho * (1.0 - 2.0 * up) : 0.0;
+    const double negR = W.w[4][p];
+    double Lu = negR * up;
+    Lu = fma(W.w[0][p], (i + 1 < G.nx) ? u[p + 1] : 0.0, Lu);
+    Lu = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? u[p - 1] : 0.0, Lu);
+    Lu = fma(W.w[1][p], (j + 1 < G.ny) ? u[p + G.sy] : 0.0, Lu);
+    Lu = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? u[p - G.sy] : 0.0, Lu);
+    Lu = fma(W.w[2][p], (k + 1 < G.nz) ? u[p + G.sz] : 0.0, Lu);
+    Lu = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? u[p - G.sz] : 0.0, Lu);
+    const double bp = fma(rho * up, 1.0 - up, Lu);
+    double dp;
+    if (scheme == ET_SCHEME_ROSENBROCK) dp = fma(-2.0 * rho, up, negR + dt_shift);
+    else dp = negR + dt_shift;
     b[p] = (T)bp;
-    dt[p] = (T)(cp - R - mu);
-    if (!isfinite(up)) atomicOr(flags, ET_FLAG_NONFINITE);
-    if (scheme == ET_SCHEME_ROSENBROCK && (up < -kRangeSlack || up > 1.0 + kRangeSlack))
-        atomicOr(flags, ET_FLAG_RANGE_IN);
+    dt[p] = (T)dp;
+    const long long bits = __double_as_longlong(up);
+    if (nonfinite_bits(bits)) atomicOr(flags, ET_FLAG_NONFINITE);
+    if (scheme == ET_SCHEME_ROSENBROCK) {
+        // u in [-slack, 1 + slack], compared on the bit patterns
+        const long long hi = __double_as_longlong(1.0 + kRangeSlack);
+        const long long lo = __double_as_longlong(kRangeSlack);
+        const bool out = bits >= 0 ? bits > hi : (bits & 0x7fffffffffffffffll) > lo;
+        if (out) atomicOr(flags, ET_FLAG_RANGE_IN);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Block reduction of (min, max, sum) into per-block partials; the last block to
-// finish reduces the partials in a fixed order (deterministic) and writes the
-// step record.
-__device__ void finish_stats(double vmin, double vmax, double vsum, const StatsSink& s) {
-    __shared__ double sred[3][kThreads / 32];
+// term: z^_{j+1} = A~ z^_j + beta b;  sum = base + g z^_{j+1};
+// last term: sum *= gamma and either stored as the next y or added to u.
+// Each thread marches over kTileZ planes, carrying the z-neighbours (and, for
+// the conservative operator, the -z face weight) in registers; blocks loop over
+// tiles so the grid matches the resident-block capacity of the device.
+template <int OP, typename T>
+__global__ void __launch_bounds__(kThreads)
+term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
+    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
+    const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
+    const T* __restrict__ z = a.zin;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tx = t % tiles_x;
+        const int rest = t / tiles_x;
+        const int ty = rest % tiles_y;
+        const int tz = rest / tiles_y;
+        const int i = tx * kBlockX + threadIdx.x;
+        const int j = ty * kBlockY + threadIdx.y;
+        if (i >= G.nx || j >= G.ny) continue;
+        const int k0 = tz * kTileZ;
+        const int k1 = min(k0 + kTileZ, G.nz);
+        long long p = i + G.sy * j + G.sz * k0;
+        T zm = (k0 > 0) ? z[p - G.sz] : T(0);
+        T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? W.w[2][p - G.sz] : W.w[3][p]) : T(0);
+        T zc = z[p];
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k, p += G.sz) {
+            const bool has_zp = k + 1 < G.nz;
+            const T zp = has_zp ? z[p + G.sz] : T(0);
+            const T wzp = W.w[2][p];
+            T acc = a.dt[p] * zc;
+            acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
+            acc = fma(minus_weight<OP, T>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : T(0), acc);
+            acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
+            acc = fma(minus_weight<OP, T>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : T(0), acc);
+            acc = fma(wzp, zp, acc);
+            acc = fma(wzm, zm, acc);
+            if (a.has_beta) acc = fma(a.beta, a.b[p], acc);
+            T base;
+            if (a.base_mode == 0) base = a.yacc[p];
+            else if (a.base_mode == 1) base = a.base_scale * a.b[p];
+            else base = zc;
+            T sum = fma(a.g, acc, base);
+            if (!a.last) {
+                a.zout[p] = acc;
+                a.yacc[p] = sum;
+            } else if (a.u) {
+                a.u[p] += (double)(sum * a.gamma);
+            } else {
+                a.yacc[p] = sum * a.gamma;
+            }
+            zm = zc;
+            zc = zp;
+            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? W.w[3][p + G.sz] : T(0));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stats: sum, min and max of u (min/max through integer order keys, one FP64
+// add per voxel), the non-finite flag, then the step record.  A fixed grid of
+// kStatsBlocks blocks fixes every summation order (bitwise reproducible).
+__global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const double* __restrict__ u,
+                                                              StatsSink s) {
+    constexpr int kWarps = kStatsThreads / 32;
+    __shared__ double ssum[kWarps];
+    __shared__ unsigned long long smin[kWarps], smax[kWarps];
     __shared__ bool is_last;
-    const int tid = threadIdx.x + kBlockX * threadIdx.y;
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    double sum = 0.0;
+    unsigned long long kmin = ~0ull, kmax = 0ull;
+    bool bad = false;
+    for (long long p = blockIdx.x * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
+        const double v = u[p];
+        sum += v;
+        const unsigned long long key = order_key(v);
+        kmin = key < kmin ? key : kmin;
+        kmax = key > kmax ? key : kmax;
+        bad |= nonfinite_bits(__double_as_longlong(v));
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(s.flags, ET_FLAG_NONFINITE);
     for (int off = 16; off > 0; off >>= 1) {
-        vmin = fmin(vmin, __shfl_down_sync(0xffffffffu, vmin, off));
-        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, off));
-        vsum += __shfl_down_sync(0xffffffffu, vsum, off);
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        const unsigned long long omin = __shfl_down_sync(0xffffffffu, kmin, off);
+        const unsigned long long omax = __shfl_down_sync(0xffffffffu, kmax, off);
+        kmin = omin < kmin ? omin : kmin;
+        kmax = omax > kmax ? omax : kmax;
     }
     if (lane == 0) {
-        sred[0][warp] = vmin;
-        sred[1][warp] = vmax;
-        sred[2][warp] = vsum;
+        ssum[warp] = sum;
+        smin[warp] = kmin;
+        smax[warp] = kmax;
     }
     __syncthreads();
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     if (tid == 0) {
-        double a = sred[0][0], bmax = sred[1][0], c = sred[2][0];
-        for (int w = 1; w < kThreads / 32; ++w) {
-            a = fmin(a, sred[0][w]);
-            bmax = fmax(bmax, sred[1][w]);
-            c += sred[2][w];
+        for (int w = 1; w < kWarps; ++w) {
+            sum += ssum[w];
+            kmin = smin[w] < kmin ? smin[w] : kmin;
+            kmax = smax[w] > kmax ? smax[w] : kmax;
         }
-        const unsigned bid = linear_block();
-        s.partial[3 * bid + 0] = a;
-        s.partial[3 * bid + 1] = bmax;
-        s.partial[3 * bid + 2] = c;
+        s.partial[3 * blockIdx.x + 0] = sum;
+        s.partial[3 * blockIdx.x + 1] = __longlong_as_double((long long)kmin);
+        s.partial[3 * blockIdx.x + 2] = __longlong_as_double((long long)kmax);
         __threadfence();
         const unsigned ticket = atomicAdd(s.ticket, 1u);
-        is_last = (ticket == nblocks - 1);
+        is_last = (ticket == kStatsBlocks - 1);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double lo = DBL_MAX, hi = -DBL_MAX, sum = 0.0;
-    for (unsigned q = tid; q < nblocks; q += kThreads) {
-        lo = fmin(lo, __ldcg(&s.partial[3 * q + 0]));
-        hi = fmax(hi, __ldcg(&s.partial[3 * q + 1]));
-        sum += __ldcg(&s.partial[3 * q + 2]);
+    sum = 0.0;
+    kmin = ~0ull;
+    kmax = 0ull;
+    for (int q = tid; q < kStatsBlocks; q += kStatsThreads) {
+        sum += __ldcg(&s.partial[3 * q + 0]);
+        const unsigned long long a = (unsigned long long)__double_as_longlong(__ldcg(&s.partial[3 * q + 1]));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(__ldcg(&s.partial[3 * q + 2]));
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
     }
     for (int off = 16; off > 0; off >>= 1) {
-        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, off));
-        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, off));
         sum += __shfl_down_sync(0xffffffffu, sum, off);
+        const unsigned long long omin = __shfl_down_sync(0xffffffffu, kmin, off);
+        const unsigned long long omax = __shfl_down_sync(0xffffffffu, kmax, off);
+        kmin = omin < kmin ? omin : kmin;
+        kmax = omax > kmax ? omax : kmax;
     }
     __syncthreads();
     if (lane == 0) {
-        sred[0][warp] = lo;
-        sred[1][warp] = hi;
-        sred[2][warp] = sum;
+        ssum[warp] = sum;
+        smin[warp] = kmin;
+        smax[warp] = kmax;
     }
     __syncthreads();
     if (tid == 0) {
-        // thread 0 holds warp 0's result; add the other warps in order
-        for (int w = 1; w < kThreads / 32; ++w) {
-            lo = fmin(lo, sred[0][w]);
-            hi = fmax(hi, sred[1][w]);
-            sum += sred[2][w];
+        for (int w = 1; w < kWarps; ++w) {
+            sum += ssum[w];
+            kmin = smin[w] < kmin ? smin[w] : kmin;
+            kmax = smax[w] > kmax ? smax[w] : kmax;
         }
         const unsigned step = *s.step_counter;
         et_step_info rec;
-        rec.umin = lo;
-        rec.umax = hi;
+        rec.umin = order_key_inv(kmin);
+        rec.umax = order_key_inv(kmax);
         rec.mass = sum;
         rec.s = s.s;
         rec.m = s.m;
@@ -225,72 +333,30 @@ __device__ void finish_stats(double vmin, double vmax, double vsum, const StatsS
     }
 }
 
-// ---------------------------------------------------------------------------
-// term: z^_{j+1} = A~ z^_j + beta b;  sum = base + g z^_{j+1};
-// last term: sum *= gamma and either stored as the next y or added to u.
-template <int OP, typename T, bool FINISH>
-__global__ void __launch_bounds__(kThreads)
-term_kernel(Geom G, Weights<T> W, TermArgs<T> a, StatsSink sink) {
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
-    const int k = blockIdx.z;
-    double vmin = DBL_MAX, vmax = -DBL_MAX, vsum = 0.0;
-    if (i < G.nx && j < G.ny) {
-        const long long p = i + G.sy * j + G.sz * k;
-        const T* __restrict__ z = a.zin;
-        const T zc = z[p];
-        T acc = a.dt[p] * zc;
-        // +x / -x
-        acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
-        acc = fma(minus_weight<OP, T>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : T(0), acc);
-        // +y / -y
-        acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
-        acc = fma(minus_weight<OP, T>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : T(0), acc);
-        // +z / -z
-        acc = fma(W.w[2][p], (k + 1 < G.nz) ? z[p + G.sz] : T(0), acc);
-        acc = fma(minus_weight<OP, T>(W, 2, p, G.sz, k > 0), (k > 0) ? z[p - G.sz] : T(0), acc);
-        if (a.beta != T(0)) acc = fma(a.beta, a.b[p], acc);
-        T base;
-        if (a.base_mode == 0) base = a.yacc[p];
-        else if (a.base_mode == 1) base = a.base_scale * a.b[p];
-        else base = zc;
-        T sum = fma(a.g, acc, base);
-        if (!a.last) {
-            a.zout[p] = acc;
-            a.yacc[p] = sum;
-        } else {
-            sum *= a.gamma;
-            if (FINISH) {
-                const double unew = a.u[p] + (double)sum;
-                a.u[p] = unew;
-                vmin = unew;
-                vmax = unew;
-                vsum = unew;
-                if (!isfinite(unew)) atomicOr(sink.flags, ET_FLAG_NONFINITE);
-            } else {
-                a.yacc[p] = sum;
-            }
-        }
+// Resident blocks per SM of a term-kernel instantiation (looked up once).
+template <int OP, typename T>
+int term_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term_kernel<OP, T>, kThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        cached = b;
     }
-    if (FINISH) finish_stats(vmin, vmax, vsum, sink);
-}
-
-dim3 stencil_grid(const Geom& G) {
-    return dim3((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
+    return cached;
 }
 
 }  // namespace
 
-cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op, double* w0,
-                          double* w1, double* w2, double* w3, unsigned long long* rmax_bits,
-                          unsigned* flags, cudaStream_t stream) {
+cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op, double* const w[5],
+                          unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
-        coeffs_kernel<ET_OP_CONSERVATIVE><<<stencil_grid(G), block, 0, stream>>>(
-            G, D, inv_h2, w0, w1, w2, w3, rmax_bits, flags);
+        coeffs_kernel<ET_OP_CONSERVATIVE><<<voxel_grid(G), block, 0, stream>>>(
+            G, D, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
     else
-        coeffs_kernel<ET_OP_LITERAL><<<stencil_grid(G), block, 0, stream>>>(
-            G, D, inv_h2, w0, w1, w2, w3, rmax_bits, flags);
+        coeffs_kernel<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(
+            G, D, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
     return cudaGetLastError();
 }
 
@@ -298,43 +364,54 @@ cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], floa
                                    cudaStream_t stream) {
     const int threads = 256;
     long long blocks = (G.n + threads - 1) / threads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const long long cap = 16ll * (G.sms > 0 ? G.sms : 1);
+    if (blocks > cap) blocks = cap;
     convert_weights_kernel<<<(unsigned)blocks, threads, 0, stream>>>(G.n, w[0], w[1], w[2], w[3], wf[0],
                                                                     wf[1], wf[2], wf[3]);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
-                            double rho, double mu, et_scheme scheme, T* b, T* dt, unsigned* flags,
+cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W, double rho,
+                            double dt_shift, et_scheme scheme, T* b, T* dt, unsigned* flags,
                             cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
-        residual_kernel<ET_OP_CONSERVATIVE, T><<<stencil_grid(G), block, 0, stream>>>(
-            G, u, W, rho, mu, (int)scheme, b, dt, flags);
+        residual_kernel<ET_OP_CONSERVATIVE, T><<<voxel_grid(G), block, 0, stream>>>(
+            G, u, W, rho, dt_shift, (int)scheme, b, dt, flags);
     else
-        residual_kernel<ET_OP_LITERAL, T><<<stencil_grid(G), block, 0, stream>>>(
-            G, u, W, rho, mu, (int)scheme, b, dt, flags);
+        residual_kernel<ET_OP_LITERAL, T><<<voxel_grid(G), block, 0, stream>>>(
+            G, u, W, rho, dt_shift, (int)scheme, b, dt, flags);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
-                        const StatsSink& sink, cudaStream_t stream) {
+                        cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
-    const dim3 grid = stencil_grid(G);
-    const bool finish = a.last && a.u != nullptr;
+    const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
+                            ((G.nz + kTileZ - 1) / kTileZ);
+    const int sms = G.sms > 0 ? G.sms : 1;
     if (op == ET_OP_CONSERVATIVE) {
-        if (finish)
-            term_kernel<ET_OP_CONSERVATIVE, T, true><<<grid, block, 0, stream>>>(G, W, a, sink);
-        else
-            term_kernel<ET_OP_CONSERVATIVE, T, false><<<grid, block, 0, stream>>>(G, W, a, sink);
+        const long long cap = (long long)sms * term_blocks_per_sm<ET_OP_CONSERVATIVE, T>();
+        term_kernel<ET_OP_CONSERVATIVE, T><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
     } else {
-        if (finish)
-            term_kernel<ET_OP_LITERAL, T, true><<<grid, block, 0, stream>>>(G, W, a, sink);
-        else
-            term_kernel<ET_OP_LITERAL, T, false><<<grid, block, 0, stream>>>(G, W, a, sink);
+        const long long cap = (long long)sms * term_blocks_per_sm<ET_OP_LITERAL, T>();
+        term_kernel<ET_OP_LITERAL, T><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t prime_launch_limits() {
+    term_blocks_per_sm<ET_OP_CONSERVATIVE, double>();
+    term_blocks_per_sm<ET_OP_LITERAL, double>();
+    term_blocks_per_sm<ET_OP_CONSERVATIVE, float>();
+    term_blocks_per_sm<ET_OP_LITERAL, float>();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream) {
+    stats_kernel<<<kStatsBlocks, kStatsThreads, 0, stream>>>(G.n, u, sink);
     return cudaGetLastError();
 }
 
@@ -345,8 +422,8 @@ template cudaError_t launch_residual<float>(const Geom&, et_operator, const doub
                                             double, double, et_scheme, float*, float*, unsigned*,
                                             cudaStream_t);
 template cudaError_t launch_term<double>(const Geom&, et_operator, Weights<double>,
-                                         const TermArgs<double>&, const StatsSink&, cudaStream_t);
-template cudaError_t launch_term<float>(const Geom&, et_operator, Weights<float>,
-                                        const TermArgs<float>&, const StatsSink&, cudaStream_t);
+                                         const TermArgs<double>&, cudaStream_t);
+template cudaError_t launch_term<float>(const Geom&, et_operator, Weights<float>, const TermArgs<float>&,
+                                        cudaStream_t);
 
 }  // namespace et

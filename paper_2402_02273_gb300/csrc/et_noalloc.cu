@@ -12,8 +12,8 @@
 // Limits and behaviour:
 //  - at most kStaticMaxVoxels = 64^3 = 262144 voxels and at most 65536 thread
 //    blocks of the 32 x 8 stencil tile; larger grids are rejected with
-//    ET_ERR_ARG.  The array is 10 FP64 fields of 64^3 voxels plus 1.5 MiB of
-//    partials: about 21.5 MiB held on every GPU that loads it until exit.
+//    ET_ERR_ARG.  The array is 11 FP64 fields of 64^3 voxels plus 16 KiB of
+//    partials: 22 MiB held on every GPU that loads it until exit.
 //  - the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress while that device is current, and caches it; make
 //    that first call before any stream capture.
@@ -43,8 +43,8 @@ using namespace et;
 constexpr long long kStaticMaxVoxels = 64ll * 64 * 64;
 constexpr unsigned kStaticMaxBlocks = 65536;
 constexpr size_t kFieldBytes = 8ull * kStaticMaxVoxels;          // one FP64 field
-constexpr int kFields = 10;                                      // 4 weights, b, dt, Y0, Y1, Z0, Z1
-constexpr size_t kPartialBytes = 3ull * 8ull * kStaticMaxBlocks;
+constexpr int kFields = 11;                                      // 5 weights, b, dt, Y0, Y1, Z0, Z1
+constexpr size_t kPartialBytes = 3ull * 8ull * kStatsBlocks;
 constexpr size_t kCounterBytes = 256;
 constexpr size_t kStaticScratchBytes = kFields * kFieldBytes + kPartialBytes + kCounterBytes;
 
@@ -94,8 +94,8 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
                                        ((ny + kBlockY - 1) / kBlockY) * (unsigned long long)nz;
     if (nblocks > kStaticMaxBlocks)
         return report(msg, msg_len, ET_ERR_ARG,
-                      "grid %d x %d x %d needs %llu thread blocks; the static scratch holds partials "
-                      "for at most %u", nx, ny, nz, nblocks, kStaticMaxBlocks);
+                      "grid %d x %d x %d needs %llu thread blocks of the 32 x 8 tile; at most %u "
+                      "are supported", nx, ny, nz, nblocks, kStaticMaxBlocks);
     if (!(h > 0.0) || !std::isfinite(h)) return report(msg, msg_len, ET_ERR_ARG, "h must be finite and > 0");
     if (!(tau > 0.0) || !std::isfinite(tau)) return report(msg, msg_len, ET_ERR_ARG, "tau must be finite and > 0");
     if (!(rho >= 0.0) || !std::isfinite(rho)) return report(msg, msg_len, ET_ERR_ARG, "rho must be finite and >= 0");
@@ -133,6 +133,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
     G.sy = nx;
     G.sz = (long long)nx * ny;
     G.nblocks = (unsigned)nblocks;
+    G.sms = 0;
 
 #define STATIC_CUDA(call)                                                                      \
     do {                                                                                       \
@@ -141,10 +142,11 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             return report(msg, msg_len, ET_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+    STATIC_CUDA(cudaDeviceGetAttribute(&G.sms, cudaDevAttrMultiProcessorCount, dev));
+    STATIC_CUDA(prime_launch_limits());
     // counters start at zero on every call; the array keeps the previous call's contents
     STATIC_CUDA(cudaMemsetAsync(counters, 0, kCounterBytes, st));
-    STATIC_CUDA(launch_coeffs(G, D, 1.0 / (h * h), op, field[0], field[1], field[2], field[3], rmax_bits,
-                              flags, st));
+    STATIC_CUDA(launch_coeffs(G, D, 1.0 / (h * h), op, field, rmax_bits, flags, st));
     unsigned long long bits = 0;
     unsigned dflags = 0;
     STATIC_CUDA(cudaMemcpyAsync(&bits, rmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
@@ -160,12 +162,13 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
         return report(msg, msg_len, ET_ERR_ARG, "no (s, m) meets the tolerance for tau = %g", tau);
 
     Weights<double> W;
-    for (int a = 0; a < 4; ++a) W.w[a] = field[a];
-    double* b = field[4];
-    double* dt = field[5];
-    double* Y[2] = {field[6], field[7]};
-    double* Z[2] = {field[8], field[9]};
-    STATIC_CUDA(launch_residual<double>(G, op, u, W, rho, mu, scheme, b, dt, flags, st));
+    for (int a = 0; a < 5; ++a) W.w[a] = field[a];
+    double* b = field[5];
+    double* dt = field[6];
+    double* Y[2] = {field[7], field[8]};
+    double* Z[2] = {field[9], field[10]};
+    const double dt_shift = (scheme == ET_SCHEME_ROSENBROCK ? rho : 0.0) - mu;
+    STATIC_CUDA(launch_residual<double>(G, op, u, W, rho, dt_shift, scheme, b, dt, flags, st));
 
     StatsSink sink;
     sink.partial = partial;
@@ -193,6 +196,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             a.zin = zin;
             a.b = b;
             a.beta = ak * pw;
+            a.has_beta = (ak * pw) != 0.0;
             a.dt = dt;
             const double gnext = gj * hs / (j + 1);
             a.g = gnext;
@@ -208,7 +212,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
                 a.gamma = gamma;
                 if (k == s - 1) a.u = u;
             }
-            STATIC_CUDA(launch_term<double>(G, op, W, a, sink, st));
+            STATIC_CUDA(launch_term<double>(G, op, W, a, st));
             if (!a.last) {
                 zin = Z[zi];
                 zi ^= 1;
@@ -223,6 +227,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
         }
         ak = gamma * ak * sum;
     }
+    STATIC_CUDA(launch_stats(G, u, sink, st));
     STATIC_CUDA(cudaMemcpyAsync(&dflags, flags, sizeof(dflags), cudaMemcpyDeviceToHost, st));
     STATIC_CUDA(cudaStreamSynchronize(st));
 #undef STATIC_CUDA

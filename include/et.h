@@ -58,11 +58,15 @@ typedef enum {
     ET_ERR_UNSUPPORTED = 6  /* combination not provided by this build */
 } et_status;
 
-/* Arithmetic of the Taylor-term kernels.  The state u is always FP64.
- *  ET_F64: every operation in FP64 (the plain form).
- *  ET_F32: stencil terms and their sum in FP32; the residual, the norm bound
- *          and the (s, m) selection in FP64. */
-typedef enum { ET_F64 = 0, ET_F32 = 1 } et_precision;
+/* Arithmetic of the Taylor-term kernels.  The state u is always FP64, and the
+ * residual, the norm bound, the (s, m) selection and the update u += y are
+ * FP64 in every form.
+ *  ET_F64:  stencil terms and their sum in FP64 (the plain form).
+ *  ET_F32:  stencil terms and their sum in FP32 (error about 1e-7 relative).
+ *  ET_DF64: stencil terms and their sum in double-float pairs (hi + lo of two
+ *           FP32 numbers, unit roundoff about 2^-48) on the FP32 pipes;
+ *           FP64-level accuracy where the FP64 pipe is slow. */
+typedef enum { ET_F64 = 0, ET_F32 = 1, ET_DF64 = 2 } et_precision;
 
 /* Spatial operator L (Sec. 2.1; the printed formula is not in divergence form
  * and the paper states no boundary stencil, so two readings are provided;
@@ -86,9 +90,11 @@ typedef enum { ET_SCHEME_ROSENBROCK = 0, ET_SCHEME_EXPEULER = 1 } et_scheme;
  * fields take the defaults. */
 typedef struct {
     double tol;       /* bound on the truncation error of one step, relative to
-                         max|u^n|; default 1e-13 (F64), 1e-7 (F32) */
-    double theta_max; /* largest tau/s * ||A - mu I||_inf per sub-step;
-                         default 7 (F64), 1.5 (F32) */
+                         max|u^n|; default 1e-13 (F64, DF64), 1e-7 (F32) */
+    double theta_max; /* largest tau/s * ||A - mu I||_inf per sub-step; default
+                         32 with the shift (the e^{mu h} factor of a sub-step
+                         cancels the growth of its partial sums), 7 (F64, DF64)
+                         or 1.5 (F32) without it */
     int shift;        /* 1: shift A by mu = -max_p(off-diagonal row sum) (exact,
                          halves the norm); 0: no shift; -1 or 0-initialised
                          struct: default = 1 */

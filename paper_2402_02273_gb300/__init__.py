@@ -25,12 +25,12 @@ from . import build as _build
 __all__ = ["Grid", "EtError", "load", "OPS", "SCHEMES", "PRECISIONS", "STEP_INFO_DTYPE"]
 
 ET_OK, ET_ERR_ARG, ET_ERR_STATE, ET_ERR_CUDA, ET_ERR_NUMERIC, ET_ERR_TIMEOUT, ET_ERR_UNSUPPORTED = range(7)
-ET_F64, ET_F32 = 0, 1
+ET_F64, ET_F32, ET_DF64 = 0, 1, 2
 ET_OP_CONSERVATIVE, ET_OP_LITERAL = 0, 1
 ET_SCHEME_ROSENBROCK, ET_SCHEME_EXPEULER = 0, 1
 ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID = 1, 2, 4
 
-PRECISIONS = {"f64": ET_F64, "f32": ET_F32}
+PRECISIONS = {"f64": ET_F64, "f32": ET_F32, "df64": ET_DF64}
 OPS = {"conservative": ET_OP_CONSERVATIVE, "literal": ET_OP_LITERAL}
 SCHEMES = {"rosenbrock": ET_SCHEME_ROSENBROCK, "expeuler": ET_SCHEME_EXPEULER}
 
@@ -147,7 +147,7 @@ class Grid:
     """A voxel grid on the current CUDA device with its workspace.
 
     Parameters: shape (nz, ny, nx) (x fastest, as numpy / torch C-order),
-    h voxel width, precision "f64" or "f32", stream a torch.cuda.Stream (or
+    h voxel width, precision "f64", "f32" or "df64", stream a torch.cuda.Stream (or
     None for the current stream).  Workspace memory is a torch uint8 tensor
     owned by this object.
     """

@@ -25,10 +25,13 @@ thread_local char g_create_error[512] = "";
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Bytes of one value of the term kernels' type.
+size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
+
 struct Layout {
-    size_t w[5], wf[4];
-    size_t vec64[6];  // b, dt, Y0, Y1, Z0, Z1 (F64)
-    size_t vec32[6];  // same in FP32 (F32)
+    size_t w[5];      // FP64 coefficient fields (all forms; the residual reads them)
+    size_t wt[4];     // typed, 1/nu-scaled copies of w[0..3] (F32, DF64)
+    size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
     size_t partial;   // 3 * nblocks doubles
     size_t misc;      // counters, flags, info slots
@@ -54,10 +57,10 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
         off = align_up(off + bytes);
         return at;
     };
+    const size_t vb = value_bytes(prec);
     for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * n);
-    for (int v = 0; v < 6; ++v) L->vec64[v] = (prec == ET_F64) ? take(8ull * n) : SIZE_MAX;
-    for (int a = 0; a < 4; ++a) L->wf[a] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
-    for (int v = 0; v < 6; ++v) L->vec32[v] = (prec == ET_F32) ? take(4ull * n) : SIZE_MAX;
+    for (int a = 0; a < 4; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * n) : SIZE_MAX;
+    for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * n);
     L->stage = take(8ull * n);
     L->partial = take(3ull * 8ull * kStatsBlocks);
     L->misc = take(kMiscBytes);
@@ -88,10 +91,15 @@ struct ResolvedOptions {
 
 ResolvedOptions resolve(const et_options* o, et_precision prec) {
     ResolvedOptions r;
-    r.tol = (o && o->tol > 0) ? o->tol : (prec == ET_F64 ? 1e-13 : 1e-7);
-    r.theta_max = (o && o->theta_max > 0) ? o->theta_max : (prec == ET_F64 ? 7.0 : 1.5);
+    r.tol = (o && o->tol > 0) ? o->tol : (prec == ET_F32 ? 1e-7 : 1e-13);
     r.shift = (o && o->shift == 0) ? 0 : 1;
     if (o && o->shift < 0) r.shift = 1;
+    // Unshifted, the Taylor partial sums of a sub-step grow like e^theta before
+    // cancelling, so theta is capped for rounding; shifted, the e^{mu h} factor
+    // of each sub-step cancels that growth and theta is capped only to keep the
+    // sums far inside the FP32 range.
+    const double cap_default = r.shift ? 32.0 : (prec == ET_F32 ? 1.5 : 7.0);
+    r.theta_max = (o && o->theta_max > 0) ? o->theta_max : cap_default;
     r.force_s = (o && o->force_s > 0) ? o->force_s : 0;
     r.force_m = (o && o->force_m > 0) ? o->force_m : 0;
     r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
@@ -114,9 +122,8 @@ struct et_grid {
     cudaStream_t capture;  // private stream used only for graph capture
     // device views
     double* w[5];
-    float* wf[4];
-    double* v64[6];
-    float* v32[6];
+    void* wt[4];
+    void* vec[6];
     double* stage;
     double* partial;
     unsigned long long* rmax_bits;
@@ -130,6 +137,7 @@ struct et_grid {
     et_scheme scheme;
     double rho;
     double rmax;
+    double nu;  // ||A - mu I||_inf bound: the FP32 / DF64 recurrences are scaled by 1/nu
     et_options opt;
     bool opt_set;
     // graph cache and timing
@@ -202,74 +210,76 @@ struct Buffers {
     T* Z[2];
 };
 
-Buffers<double> buffers64(et_grid* g) {
-    Buffers<double> B;
-    for (int a = 0; a < 5; ++a) B.W.w[a] = g->w[a];
-    B.b = g->v64[0];
-    B.dt = g->v64[1];
-    B.Y[0] = g->v64[2];
-    B.Y[1] = g->v64[3];
-    B.Z[0] = g->v64[4];
-    B.Z[1] = g->v64[5];
-    return B;
-}
-
-Buffers<float> buffers32(et_grid* g) {
-    Buffers<float> B;
-    for (int a = 0; a < 4; ++a) B.W.w[a] = g->wf[a];
-    B.W.w[4] = nullptr;
-    B.b = g->v32[0];
-    B.dt = g->v32[1];
-    B.Y[0] = g->v32[2];
-    B.Y[1] = g->v32[3];
-    B.Z[0] = g->v32[4];
-    B.Z[1] = g->v32[5];
-    return B;
-}
-
-// Enqueues the s*m - 1 Taylor-term launches of one step (Sec. 2.2) with the
-// scaled recurrence described in et_kernels.cu; counts them in *launches.
 template <typename T>
-cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Schedule& S, double hstep,
-                            const StatsSink& sink, cudaStream_t st, long long* launches) {
+Buffers<T> typed_buffers(et_grid* g) {
+    Buffers<T> B;
+    for (int a = 0; a < 4; ++a) B.W.w[a] = g->prec == ET_F64 ? (const T*)g->w[a] : (const T*)g->wt[a];
+    B.W.w[4] = nullptr;
+    B.b = (const T*)g->vec[0];
+    B.dt = (T*)g->vec[1];
+    B.Y[0] = (T*)g->vec[2];
+    B.Y[1] = (T*)g->vec[3];
+    B.Z[0] = (T*)g->vec[4];
+    B.Z[1] = (T*)g->vec[5];
+    return B;
+}
+
+// Enqueues the s*m - 1 Taylor-term launches of one step (Sec. 2.2); counts
+// them in *launches.
+//
+// FP64 runs the scaled recurrence of et_kernels.cu, z^_{j+1} = A~ z^_j +
+// a_k (-mu)^j b with weights g_j = h^j / j!.  FP32 and DF64 run it normalised
+// by nu (weights and diagonal already divided by nu): zeta_j = z^_j / nu^j,
+//     zeta_{j+1} = (A~/nu) zeta_j + a_k (-mu)^j / nu^{j+1} b,
+// with weights theta^j / j!, theta = h nu, so the vectors stay O(|b| / nu).
+// On sub-step 0, zeta_1 = b / nu is read as b with the stencil part scaled by
+// 1 / nu (zscale).
+template <typename T>
+cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Schedule& S, double hstep,
+                          cudaStream_t st, long long* launches) {
     const int s = S.s, m = S.m;
     const double mu = S.mu;
+    const bool normalised = g->prec != ET_F64;
+    const double nu = normalised ? g->nu : 1.0;
+    const double hw = normalised ? hstep * nu : hstep;  // ratio of consecutive weights times (j+1)
     const double gamma = std::exp(mu * hstep);
     double ak = 1.0;  // augmented scalar at the start of sub-step k
     int zi = 0;       // next z buffer to write
     for (int k = 0; k < s; ++k) {
         T* yacc = B.Y[(k + 1) & 1];
         const T* ycur = B.Y[k & 1];
-        // powers of (-mu) and Taylor weights g_j = h^j / j!
-        double pw = 1.0;      // (-mu)^j
-        double gj = 1.0;      // g_j
+        double pw = 1.0;  // (-mu)^j / nu^{j+1} (normalised) or (-mu)^j
+        double gj = 1.0;  // weight of term j
         const T* zin = nullptr;
         int j0 = 0;
         if (k == 0) {
-            // y_0 = 0, so z^_1 = a_0 b = b: no launch for the first term
-            pw = -mu;         // (-mu)^1
-            gj = hstep;       // g_1
+            // y_0 = 0, so the first term is a_0 b: no launch for it
+            pw = -mu / nu;
+            gj = hw;
             zin = B.b;
             j0 = 1;
         } else {
             zin = ycur;
         }
+        if (normalised) pw /= nu;
         for (int j = j0; j < m; ++j) {
             TermArgs<T> a;
             a.zin = zin;
             a.b = B.b;
-            a.beta = (T)(ak * pw);
+            a.beta = Scalar<T>::make(ak * pw);
             a.has_beta = (ak * pw) != 0.0;
+            a.zscale = Scalar<T>::make(1.0 / nu);
+            a.has_zscale = normalised && k == 0 && j == 1;
             a.dt = B.dt;
-            const double gnext = gj * hstep / (j + 1);
-            a.g = (T)gnext;
-            a.gamma = (T)1;
-            a.base_scale = (T)0;
+            const double gnext = gj * hw / (j + 1);
+            a.g = Scalar<T>::make(gnext);
+            a.gamma = Scalar<T>::make(1.0);
+            a.base_scale = Scalar<T>::make(0.0);
             if (k == 0 && j == 1) {
                 a.base_mode = 1;
-                a.base_scale = (T)hstep;  // g_1 b
+                a.base_scale = Scalar<T>::make(hstep);  // first term h b
             } else if (k > 0 && j == 0) {
-                a.base_mode = 2;          // y_k, read as the centre of z^_0
+                a.base_mode = 2;  // y_k, read as the centre of z_0
             } else {
                 a.base_mode = 0;
             }
@@ -280,17 +290,17 @@ cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Sc
             if (!a.last) {
                 a.zout = B.Z[zi];
             } else {
-                a.gamma = (T)gamma;
+                a.gamma = Scalar<T>::make(gamma);
                 if (k == s - 1) a.u = u;
             }
-            cudaError_t e = launch_term<T>(g->G, g->op, B.W, a, st);
+            cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
             if (e != cudaSuccess) return e;
             ++*launches;
             if (!a.last) {
                 zin = B.Z[zi];
                 zi ^= 1;
             }
-            pw *= -mu;
+            pw *= -mu / nu;
             gj = gnext;
         }
         // augmented scalar after the sub-step: e^{mu h} * sum_j a_k (-mu h)^j / j!
@@ -302,6 +312,24 @@ cudaError_t enqueue_chain_h(et_grid* g, const Buffers<T>& B, double* u, const Sc
         ak = gamma * ak * sum;
     }
     return cudaSuccess;
+}
+
+template <typename T>
+et_status enqueue_form(et_grid* g, double* u, const Schedule& S, double hstep, double dt_shift,
+                       cudaStream_t st, cudaEvent_t ev_begin, unsigned evflags, long long* term_launches,
+                       long long* other_launches) {
+    Buffers<T> B = typed_buffers<T>(g);
+    Weights<double> W64;
+    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+    const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
+    cudaError_t e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, dt_scale, g->scheme,
+                                       const_cast<T*>(B.b), B.dt, g->flags, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+    ++*other_launches;
+    if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
+    e = enqueue_chain<T>(g, B, u, S, hstep, st, term_launches);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "term launch: %s", cudaGetErrorString(e));
+    return ET_OK;
 }
 
 // Residual plus the term chain of one step on stream st.
@@ -319,29 +347,17 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
     sink.s = S.s;
     sink.m = S.m;
     const double hstep = tau / S.s;
-    Weights<double> W64;
-    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
     const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
-    cudaError_t e;
     const unsigned evflags = external_events ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (g->prec == ET_F64) {
-        Buffers<double> B = buffers64(g);
-        e = launch_residual<double>(g->G, g->op, u, W64, g->rho, dt_shift, g->scheme, const_cast<double*>(B.b),
-                                    B.dt, g->flags, st);
-        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
-        ++*other_launches;
-        if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
-        e = enqueue_chain_h<double>(g, B, u, S, hstep, sink, st, term_launches);
-    } else {
-        Buffers<float> B = buffers32(g);
-        e = launch_residual<float>(g->G, g->op, u, W64, g->rho, dt_shift, g->scheme, const_cast<float*>(B.b),
-                                   B.dt, g->flags, st);
-        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
-        ++*other_launches;
-        if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
-        e = enqueue_chain_h<float>(g, B, u, S, hstep, sink, st, term_launches);
-    }
-    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "term launch: %s", cudaGetErrorString(e));
+    et_status rc;
+    if (g->prec == ET_F64)
+        rc = enqueue_form<double>(g, u, S, hstep, dt_shift, st, ev_begin, evflags, term_launches, other_launches);
+    else if (g->prec == ET_F32)
+        rc = enqueue_form<float>(g, u, S, hstep, dt_shift, st, ev_begin, evflags, term_launches, other_launches);
+    else
+        rc = enqueue_form<float2>(g, u, S, hstep, dt_shift, st, ev_begin, evflags, term_launches, other_launches);
+    if (rc != ET_OK) return rc;
+    cudaError_t e;
     if (ev_end) ET_CUDA(g, cudaEventRecordWithFlags(ev_end, st, evflags));
     e = launch_stats(g->G, u, sink, st);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "stats launch: %s", cudaGetErrorString(e));
@@ -462,12 +478,6 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     const double inv_h2 = 1.0 / (g->h * g->h);
     cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w, g->rmax_bits, g->flags, g->stream);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
-    if (g->prec == ET_F32) {
-        const double* src[4] = {g->w[0], g->w[1], g->w[2], g->w[3]};
-        float* dstf[4] = {g->wf[0], g->wf[1], g->wf[2], g->wf[3]};
-        e = launch_convert_weights(g->G, src, dstf, g->stream);
-        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
-    }
     unsigned long long bits = 0;
     unsigned flags = 0;
     ET_CUDA(g, cudaMemcpyAsync(&bits, g->rmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, g->stream));
@@ -478,6 +488,23 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     double rmax;
     std::memcpy(&rmax, &bits, sizeof(rmax));
     g->rmax = rmax;
+    {
+        const ResolvedOptions ro = resolve(opt, g->prec);
+        const double rho_c = (scheme == ET_SCHEME_ROSENBROCK) ? rho * (1.0 + 2.0 * kRangeSlack) : 0.0;
+        const double nu = ro.shift ? rmax + rho_c : 2.0 * rmax + rho_c;
+        g->nu = nu > 0.0 ? nu : 1.0;
+    }
+    if (g->prec != ET_F64) {
+        const double* src[4] = {g->w[0], g->w[1], g->w[2], g->w[3]};
+        if (g->prec == ET_F32) {
+            float* dst[4] = {(float*)g->wt[0], (float*)g->wt[1], (float*)g->wt[2], (float*)g->wt[3]};
+            e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
+        } else {
+            float2* dst[4] = {(float2*)g->wt[0], (float2*)g->wt[1], (float2*)g->wt[2], (float2*)g->wt[3]};
+            e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
+        }
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
+    }
     g->rho = rho;
     g->op = op;
     g->scheme = scheme;
@@ -509,7 +536,7 @@ const char* et_status_string(et_status s) {
 const char* et_last_error(const et_grid* g) { return g ? g->err : g_create_error; }
 
 size_t et_workspace_bytes(int nx, int ny, int nz, et_precision precision) {
-    if (precision != ET_F64 && precision != ET_F32) return 0;
+    if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64) return 0;
     Layout L;
     if (!make_layout(nx, ny, nz, precision, &L)) return 0;
     return L.total;
@@ -571,7 +598,8 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
                          size_t workspace_bytes, void* cuda_stream, et_grid** out) {
     if (!out) return fail(nullptr, ET_ERR_ARG, "out must not be NULL");
     *out = nullptr;
-    if (precision != ET_F64 && precision != ET_F32) return fail(nullptr, ET_ERR_ARG, "unknown precision");
+    if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64)
+        return fail(nullptr, ET_ERR_ARG, "unknown precision");
     Layout L;
     if (!make_layout(nx, ny, nz, precision, &L))
         return fail(nullptr, ET_ERR_ARG, "grid %d x %d x %d is empty or too large", nx, ny, nz);
@@ -611,11 +639,8 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     }
     g->stream = (cudaStream_t)cuda_stream;
     for (int a = 0; a < 5; ++a) g->w[a] = (double*)(g->ws + L.w[a]);
-    for (int a = 0; a < 4; ++a) g->wf[a] = precision == ET_F32 ? (float*)(g->ws + L.wf[a]) : nullptr;
-    for (int v = 0; v < 6; ++v) {
-        g->v64[v] = precision == ET_F64 ? (double*)(g->ws + L.vec64[v]) : nullptr;
-        g->v32[v] = precision == ET_F32 ? (float*)(g->ws + L.vec32[v]) : nullptr;
-    }
+    for (int a = 0; a < 4; ++a) g->wt[a] = precision != ET_F64 ? (void*)(g->ws + L.wt[a]) : nullptr;
+    for (int v = 0; v < 6; ++v) g->vec[v] = (void*)(g->ws + L.vec[v]);
     g->stage = (double*)(g->ws + L.stage);
     g->partial = (double*)(g->ws + L.partial);
     char* misc = g->ws + L.misc;
@@ -626,6 +651,7 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->info_slot = (et_step_info*)(misc + 64);
     g->coeffs_set = false;
     g->rmax = 0.0;
+    g->nu = 1.0;
     g->rho = 0.0;
     g->opt_set = false;
     std::memset(&g->opt, 0, sizeof(g->opt));

@@ -1,0 +1,191 @@
+// Double-float (DF64) Taylor-term kernel for sm_103a.
+//
+// GB300 executes FP64 at 2 FMA per clock per SM against 128 FP32 FMA, so a
+// stencil term carried out in pairs of FP32 numbers (value = hi + lo, a 48-bit
+// significand, unit roundoff about 2^-48) runs on the FP32 pipes at a fraction
+// of the FP64 issue time and leaves the kernel bound by memory traffic again.
+// The pair arithmetic below uses the error-free transformations TwoSum (Knuth)
+// and the FMA-based TwoProduct; the stencil sum is a
+// compensated dot product in the manner of Ogita, Rump and Oishi (2005): high
+// parts are added with TwoSum, every rounding error and every hi*lo cross
+// product is collected in one FP32 correction, and the pair is renormalised
+// once at the end.  The lo*lo products (relative size 2^-48) are dropped.
+// Intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) keep the compiler from
+// contracting or reassociating any of these steps.
+//
+// The recurrence is the normalised form used for FP32 (et_kernels.cu): the
+// weights and the diagonal are divided by nu = ||A - mu I|| bound, so the
+// vectors z stay O(|b| / nu) and the pairs never approach the FP32 range.
+#include <cuda_runtime.h>
+
+#include "et_internal.h"
+
+namespace et {
+namespace {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated accumulator of a sum of pair products.
+struct DotAcc {
+    float s, c;
+};
+
+__device__ __forceinline__ void dot_first(DotAcc& A, float2 a, float2 b) {
+    A.s = __fmul_rn(a.x, b.x);
+    float c = __fmaf_rn(a.x, b.x, -A.s);
+    c = __fmaf_rn(a.x, b.y, c);
+    A.c = __fmaf_rn(a.y, b.x, c);
+}
+
+__device__ __forceinline__ void dot_add(DotAcc& A, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float ep = __fmaf_rn(a.x, b.x, -p);
+    float s, es;
+    two_sum(A.s, p, s, es);
+    A.s = s;
+    float c = __fmaf_rn(a.x, b.y, A.c);
+    c = __fmaf_rn(a.y, b.x, c);
+    A.c = __fadd_rn(c, __fadd_rn(ep, es));
+}
+
+__device__ __forceinline__ float2 dot_result(const DotAcc& A) {
+    float s, e;
+    two_sum(A.s, A.c, s, e);
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    DotAcc A;
+    dot_first(A, a, b);
+    return dot_result(A);
+}
+
+// a * b + c as one compensated sum.
+__device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
+    DotAcc A;
+    dot_first(A, a, b);
+    float s, es;
+    two_sum(A.s, c.x, s, es);
+    A.s = s;
+    A.c = __fadd_rn(__fadd_rn(A.c, c.y), es);
+    return dot_result(A);
+}
+
+// Same tiling and recurrence as term_kernel in et_kernels.cu, in pair arithmetic.
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
+    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
+    const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
+    // restrict-qualified locals: the stores of one plane do not alias the loads of
+    // the next, so the compiler may issue those loads early
+    const float2* __restrict__ z = a.zin;
+    const float2* __restrict__ w0 = W.w[0];
+    const float2* __restrict__ w1 = W.w[1];
+    const float2* __restrict__ w2 = W.w[2];
+    const float2* __restrict__ w3 = W.w[3];
+    const float2* __restrict__ dtv = a.dt;
+    const float2* __restrict__ bv = a.b;
+    float2* __restrict__ zout = a.zout;
+    float2* __restrict__ yacc = a.yacc;
+    double* __restrict__ u = a.u;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tx = t % tiles_x;
+        const int rest = t / tiles_x;
+        const int ty = rest % tiles_y;
+        const int tz = rest / tiles_y;
+        const int i = tx * kBlockX + threadIdx.x;
+        const int j = ty * kBlockY + threadIdx.y;
+        if (i >= G.nx || j >= G.ny) continue;
+        const int k0 = tz * kTileZ;
+        const int k1 = min(k0 + kTileZ, G.nz);
+        long long p = i + G.sy * j + G.sz * k0;
+        float2 zm = (k0 > 0) ? z[p - G.sz] : zero;
+        float2 wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : zero;
+        float2 zc = z[p];
+        for (int k = k0; k < k1; ++k, p += G.sz) {
+            const bool has_zp = k + 1 < G.nz;
+            const float2 zp = has_zp ? z[p + G.sz] : zero;
+            const float2 wzp = w2[p];
+            DotAcc A;
+            dot_first(A, dtv[p], zc);
+            dot_add(A, w0[p], (i + 1 < G.nx) ? z[p + 1] : zero);
+            dot_add(A, (i > 0) ? (OP == ET_OP_CONSERVATIVE ? w0[p - 1] : w3[p]) : zero, (i > 0) ? z[p - 1] : zero);
+            dot_add(A, w1[p], (j + 1 < G.ny) ? z[p + G.sy] : zero);
+            dot_add(A, (j > 0) ? (OP == ET_OP_CONSERVATIVE ? w1[p - G.sy] : w3[p]) : zero,
+                    (j > 0) ? z[p - G.sy] : zero);
+            dot_add(A, wzp, zp);
+            dot_add(A, wzm, zm);
+            float2 acc;
+            if (!a.has_zscale) {
+                if (a.has_beta) dot_add(A, a.beta, bv[p]);
+                acc = dot_result(A);
+            } else {
+                acc = df_mul(a.zscale, dot_result(A));
+                if (a.has_beta) acc = df_fma(a.beta, bv[p], acc);
+            }
+            float2 base;
+            if (a.base_mode == 0) base = yacc[p];
+            else if (a.base_mode == 1) base = df_mul(a.base_scale, bv[p]);
+            else base = zc;
+            float2 sum = df_fma(a.g, acc, base);
+            if (!a.last) {
+                zout[p] = acc;
+                yacc[p] = sum;
+            } else {
+                sum = df_mul(a.gamma, sum);
+                if (u) u[p] += (double)sum.x + (double)sum.y;
+                else yacc[p] = sum;
+            }
+            zm = zc;
+            zc = zp;
+            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : zero);
+        }
+    }
+}
+
+template <int OP>
+int df64_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term_kernel_df64<OP>, kThreads, 0) != cudaSuccess ||
+            b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+}  // namespace
+
+cudaError_t prime_launch_limits_df64() {
+    df64_blocks_per_sm<ET_OP_CONSERVATIVE>();
+    df64_blocks_per_sm<ET_OP_LITERAL>();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const TermArgs<float2>& a,
+                        cudaStream_t stream) {
+    const dim3 block(kBlockX, kBlockY, 1);
+    const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
+                            ((G.nz + kTileZ - 1) / kTileZ);
+    const int sms = G.sms > 0 ? G.sms : 1;
+    if (op == ET_OP_CONSERVATIVE) {
+        const long long cap = (long long)sms * df64_blocks_per_sm<ET_OP_CONSERVATIVE>();
+        term_kernel_df64<ET_OP_CONSERVATIVE><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
+    } else {
+        const long long cap = (long long)sms * df64_blocks_per_sm<ET_OP_LITERAL>();
+        term_kernel_df64<ET_OP_LITERAL><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace et

@@ -60,6 +60,26 @@ struct StatsSink {
     int s, m;               // recorded in the info
 };
 
+// Scalars of the kernels' value types: double (FP64), float (FP32) and
+// float2 = (hi, lo) double-float pairs (DF64, value hi + lo).
+template <typename T>
+struct Scalar;
+template <>
+struct Scalar<double> {
+    static double make(double v) { return v; }
+};
+template <>
+struct Scalar<float> {
+    static float make(double v) { return (float)v; }
+};
+template <>
+struct Scalar<float2> {
+    static float2 make(double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    }
+};
+
 // Arguments of one Taylor-term launch (scaled recurrence, see et_kernels.cu).
 template <typename T>
 struct TermArgs {
@@ -68,6 +88,8 @@ struct TermArgs {
     const T* b;      // residual, added with coefficient beta when has_beta
     T beta;
     int has_beta;
+    T zscale;        // factor on the stencil part (first term of the FP32 / DF64 chain)
+    int has_zscale;
     const T* dt;     // diagonal of A - mu I
     int base_mode;   // 0: yacc[p]; 1: base_scale * b[p]; 2: zin[p]
     T base_scale;
@@ -83,19 +105,27 @@ struct TermArgs {
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op,
                           double* const w[5], unsigned long long* rmax_bits, unsigned* flags,
                           cudaStream_t stream);
+// Typed copies of w[0..3] scaled by `scale` (1 / nu for the FP32 and DF64 forms).
 cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4],
-                                   cudaStream_t stream);
-// dt_shift: rho - mu (folded scheme) or -mu (exponential Euler).
+                                   double scale, cudaStream_t stream);
+cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float2* const wd[4],
+                                   double scale, cudaStream_t stream);
+// dt_shift: rho - mu (folded scheme) or -mu (exponential Euler); the diagonal
+// is stored times dt_scale (1 / nu for the FP32 and DF64 forms).
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
-                            double rho, double dt_shift, et_scheme scheme, T* b, T* dt,
-                            unsigned* flags, cudaStream_t stream);
+                            double rho, double dt_shift, double dt_scale, et_scheme scheme, T* b,
+                            T* dt, unsigned* flags, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
+                        cudaStream_t stream);
+// double-float form (et_df64.cu)
+cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const TermArgs<float2>& a,
                         cudaStream_t stream);
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
 // Looks up launch limits (resident blocks per SM) before any stream capture.
 cudaError_t prime_launch_limits();
+cudaError_t prime_launch_limits_df64();
 
 }  // namespace et

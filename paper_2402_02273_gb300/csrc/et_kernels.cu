@@ -28,6 +28,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "et_internal.h"
 
@@ -111,17 +112,26 @@ coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __res
     }
 }
 
+// Stores an FP64 value in the kernels' value types; FP64 -> (hi, lo) splits
+// exactly up to the 48-bit significand of the pair.
+__device__ __forceinline__ void store_value(double* d, double v) { *d = v; }
+__device__ __forceinline__ void store_value(float* d, double v) { *d = (float)v; }
+__device__ __forceinline__ void store_value(float2* d, double v) {
+    const float hi = (float)v;
+    *d = make_float2(hi, (float)(v - (double)hi));
+}
+
+template <typename T>
 __global__ void convert_weights_kernel(long long n, const double* __restrict__ a0,
                                        const double* __restrict__ a1, const double* __restrict__ a2,
-                                       const double* __restrict__ a3, float* __restrict__ f0,
-                                       float* __restrict__ f1, float* __restrict__ f2,
-                                       float* __restrict__ f3) {
+                                       const double* __restrict__ a3, double scale, T* __restrict__ f0,
+                                       T* __restrict__ f1, T* __restrict__ f2, T* __restrict__ f3) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        f0[p] = (float)a0[p];
-        f1[p] = (float)a1[p];
-        f2[p] = (float)a2[p];
-        f3[p] = (float)a3[p];
+        store_value(&f0[p], a0[p] * scale);
+        store_value(&f1[p], a1[p] * scale);
+        store_value(&f2[p], a2[p] * scale);
+        store_value(&f3[p], a3[p] * scale);
     }
 }
 
@@ -140,7 +150,7 @@ __device__ __forceinline__ T minus_weight(const Weights<T>& W, int axis, long lo
 template <int OP, typename T>
 __global__ void __launch_bounds__(kThreads)
 residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double dt_shift,
-                int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
+                double dt_scale, int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
@@ -159,8 +169,8 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
     double dp;
     if (scheme == ET_SCHEME_ROSENBROCK) dp = fma(-2.0 * rho, up, negR + dt_shift);
     else dp = negR + dt_shift;
-    b[p] = (T)bp;
-    dt[p] = (T)dp;
+    store_value(&b[p], bp);
+    store_value(&dt[p], dp * dt_scale);
     const long long bits = __double_as_longlong(up);
     if (nonfinite_bits(bits)) atomicOr(flags, ET_FLAG_NONFINITE);
     if (scheme == ET_SCHEME_ROSENBROCK) {
@@ -185,7 +195,18 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
     const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
     const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
+    // restrict-qualified locals: the stores of one plane do not alias the loads of
+    // the next, so the compiler may issue those loads early
     const T* __restrict__ z = a.zin;
+    const T* __restrict__ w0 = W.w[0];
+    const T* __restrict__ w1 = W.w[1];
+    const T* __restrict__ w2 = W.w[2];
+    const T* __restrict__ w3 = W.w[3];
+    const T* __restrict__ dtv = a.dt;
+    const T* __restrict__ bv = a.b;
+    T* __restrict__ zout = a.zout;
+    T* __restrict__ yacc = a.yacc;
+    double* __restrict__ u = a.u;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x;
         const int rest = t / tiles_x;
@@ -198,37 +219,41 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
         const int k1 = min(k0 + kTileZ, G.nz);
         long long p = i + G.sy * j + G.sz * k0;
         T zm = (k0 > 0) ? z[p - G.sz] : T(0);
-        T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? W.w[2][p - G.sz] : W.w[3][p]) : T(0);
+        T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : T(0);
         T zc = z[p];
 #pragma unroll 2
         for (int k = k0; k < k1; ++k, p += G.sz) {
             const bool has_zp = k + 1 < G.nz;
             const T zp = has_zp ? z[p + G.sz] : T(0);
-            const T wzp = W.w[2][p];
-            T acc = a.dt[p] * zc;
-            acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
-            acc = fma(minus_weight<OP, T>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : T(0), acc);
-            acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
-            acc = fma(minus_weight<OP, T>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : T(0), acc);
+            const T wzp = w2[p];
+            T acc = dtv[p] * zc;
+            acc = fma(w0[p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
+            acc = fma((i > 0) ? (OP == ET_OP_CONSERVATIVE ? w0[p - 1] : w3[p]) : T(0), (i > 0) ? z[p - 1] : T(0), acc);
+            acc = fma(w1[p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
+            acc = fma((j > 0) ? (OP == ET_OP_CONSERVATIVE ? w1[p - G.sy] : w3[p]) : T(0), (j > 0) ? z[p - G.sy] : T(0),
+                      acc);
             acc = fma(wzp, zp, acc);
             acc = fma(wzm, zm, acc);
-            if (a.has_beta) acc = fma(a.beta, a.b[p], acc);
+            if constexpr (!std::is_same<T, double>::value) {
+                if (a.has_zscale) acc *= a.zscale;  // only the normalised (FP32) chain scales
+            }
+            if (a.has_beta) acc = fma(a.beta, bv[p], acc);
             T base;
-            if (a.base_mode == 0) base = a.yacc[p];
-            else if (a.base_mode == 1) base = a.base_scale * a.b[p];
+            if (a.base_mode == 0) base = yacc[p];
+            else if (a.base_mode == 1) base = a.base_scale * bv[p];
             else base = zc;
             T sum = fma(a.g, acc, base);
             if (!a.last) {
-                a.zout[p] = acc;
-                a.yacc[p] = sum;
-            } else if (a.u) {
-                a.u[p] += (double)(sum * a.gamma);
+                zout[p] = acc;
+                yacc[p] = sum;
+            } else if (u) {
+                u[p] += (double)(sum * a.gamma);
             } else {
-                a.yacc[p] = sum * a.gamma;
+                yacc[p] = sum * a.gamma;
             }
             zm = zc;
             zc = zp;
-            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? W.w[3][p + G.sz] : T(0));
+            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : T(0));
         }
     }
 }
@@ -360,28 +385,39 @@ cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_oper
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4],
-                                   cudaStream_t stream) {
+template <typename T>
+cudaError_t convert_weights_impl(const Geom& G, const double* const w[4], T* const wt[4], double scale,
+                                 cudaStream_t stream) {
     const int threads = 256;
     long long blocks = (G.n + threads - 1) / threads;
     const long long cap = 16ll * (G.sms > 0 ? G.sms : 1);
     if (blocks > cap) blocks = cap;
-    convert_weights_kernel<<<(unsigned)blocks, threads, 0, stream>>>(G.n, w[0], w[1], w[2], w[3], wf[0],
-                                                                    wf[1], wf[2], wf[3]);
+    convert_weights_kernel<T><<<(unsigned)blocks, threads, 0, stream>>>(G.n, w[0], w[1], w[2], w[3], scale,
+                                                                       wt[0], wt[1], wt[2], wt[3]);
     return cudaGetLastError();
+}
+
+cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4], double scale,
+                                   cudaStream_t stream) {
+    return convert_weights_impl<float>(G, w, wf, scale, stream);
+}
+
+cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float2* const wd[4], double scale,
+                                   cudaStream_t stream) {
+    return convert_weights_impl<float2>(G, w, wd, scale, stream);
 }
 
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W, double rho,
-                            double dt_shift, et_scheme scheme, T* b, T* dt, unsigned* flags,
+                            double dt_shift, double dt_scale, et_scheme scheme, T* b, T* dt, unsigned* flags,
                             cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
         residual_kernel<ET_OP_CONSERVATIVE, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, (int)scheme, b, dt, flags);
+            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags);
     else
         residual_kernel<ET_OP_LITERAL, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, (int)scheme, b, dt, flags);
+            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags);
     return cudaGetLastError();
 }
 
@@ -407,6 +443,7 @@ cudaError_t prime_launch_limits() {
     term_blocks_per_sm<ET_OP_LITERAL, double>();
     term_blocks_per_sm<ET_OP_CONSERVATIVE, float>();
     term_blocks_per_sm<ET_OP_LITERAL, float>();
+    prime_launch_limits_df64();
     return cudaGetLastError();
 }
 
@@ -416,11 +453,14 @@ cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, 
 }
 
 template cudaError_t launch_residual<double>(const Geom&, et_operator, const double*, Weights<double>,
-                                             double, double, et_scheme, double*, double*, unsigned*,
+                                             double, double, double, et_scheme, double*, double*, unsigned*,
                                              cudaStream_t);
 template cudaError_t launch_residual<float>(const Geom&, et_operator, const double*, Weights<double>,
-                                            double, double, et_scheme, float*, float*, unsigned*,
+                                            double, double, double, et_scheme, float*, float*, unsigned*,
                                             cudaStream_t);
+template cudaError_t launch_residual<float2>(const Geom&, et_operator, const double*, Weights<double>,
+                                             double, double, double, et_scheme, float2*, float2*, unsigned*,
+                                             cudaStream_t);
 template cudaError_t launch_term<double>(const Geom&, et_operator, Weights<double>,
                                          const TermArgs<double>&, cudaStream_t);
 template cudaError_t launch_term<float>(const Geom&, et_operator, Weights<float>, const TermArgs<float>&,

@@ -168,7 +168,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
     double* Y[2] = {field[7], field[8]};
     double* Z[2] = {field[9], field[10]};
     const double dt_shift = (scheme == ET_SCHEME_ROSENBROCK ? rho : 0.0) - mu;
-    STATIC_CUDA(launch_residual<double>(G, op, u, W, rho, dt_shift, scheme, b, dt, flags, st));
+    STATIC_CUDA(launch_residual<double>(G, op, u, W, rho, dt_shift, 1.0, scheme, b, dt, flags, st));
 
     StatsSink sink;
     sink.partial = partial;
@@ -197,6 +197,8 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             a.b = b;
             a.beta = ak * pw;
             a.has_beta = (ak * pw) != 0.0;
+            a.zscale = 1.0;
+            a.has_zscale = 0;
             a.dt = dt;
             const double gnext = gj * hs / (j + 1);
             a.g = gnext;

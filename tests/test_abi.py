@@ -84,9 +84,13 @@ def test_selector_basic_properties():
     # tighter tolerance never needs fewer terms
     s2, m2, _, _ = et.select_schedule(7.3, 0.858, 0.025, tol=1e-15)
     assert s2 * m2 >= s * m
-    # FP32 keeps theta small
+    # with the shift the e^{mu h} factor cancels the growth of the partial sums,
+    # so FP32 takes one long sub-step; without it theta stays small for rounding
     s3, m3, _, th3 = et.select_schedule(7.3, 0.858, 0.025, precision="f32")
-    assert th3 <= 1.5 + 1e-12
+    assert s3 == 1 and m3 < m
+    s4, m4, _, th4 = et.select_schedule(7.3, 0.858, 0.025, precision="f32", shift=0)
+    assert th4 <= 1.5 + 1e-12 and s4 * m4 > 2 * s3 * m3
+    assert et.select_schedule(7.3, 0.858, 0.025, precision="df64")[:2] == (s, m)
     # forced values pass through
     assert et.select_schedule(7.3, 0.858, 0.025, force_s=3, force_m=9)[:2] == (3, 9)
     # degenerate operator: D = 0 and exponential Euler -> A = 0, one short sub-step
@@ -137,7 +141,6 @@ def test_selected_schedule_meets_tolerance_on_dense_model(shift, op):
         e = np.zeros(n)
         e[q] = 1.0
         A[:, q] = P.apply_A(u0, e).ravel()
-    rmax = max(np.abs(A[p]).sum() - abs(A[p, p]) - 0.0 for p in range(n))
     # row sums of L only (the reaction diagonal is not part of rmax)
     L = A - np.diag(0.025 * (1 - 2 * u0.ravel()))
     rmax = max(np.abs(L[p]).sum() - abs(L[p, p]) for p in range(n))

@@ -67,60 +67,75 @@ def _compare_every_step(et, torch, D, u0, tau, nsteps, tol, **kw):
     return worst
 
 
-def test_config0_32cubed_10_steps_fp64(et_mod, torch_cuda):
-    """32^3 phantom, h = 1, tau = 7.3 d, 10 steps, FP64 (white-matter D = 0.065)."""
+FP64_FORMS = ["f64", "df64"]  # both held to the FP64 parity tolerance
+
+
+@pytest.mark.parametrize("precision", FP64_FORMS)
+def test_config0_32cubed_10_steps(et_mod, torch_cuda, precision):
+    """32^3 phantom, h = 1, tau = 7.3 d, 10 steps (white-matter D = 0.065)."""
     D, u0 = phantom.case(32, seed=0, d_white=0.065)
-    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 10, TOL64)
+    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 10, TOL64, precision=precision)
 
 
+@pytest.mark.parametrize("precision", FP64_FORMS)
 @pytest.mark.parametrize("op", ["conservative", "literal"])
 @pytest.mark.parametrize("scheme", ["rosenbrock", "expeuler"])
-def test_operator_and_scheme_readings_fp64(et_mod, torch_cuda, op, scheme):
+def test_operator_and_scheme_readings(et_mod, torch_cuda, op, scheme, precision):
     D, u0 = phantom.case(24, seed=1, noise=0.1)
-    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 4, TOL64, op=op, scheme=scheme)
+    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 4, TOL64, op=op, scheme=scheme,
+                        precision=precision)
 
 
+@pytest.mark.parametrize("precision", FP64_FORMS)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 1), (7, 1, 1), (1, 1, 45), (5, 17, 33),
                                    (9, 8, 40), (3, 70, 2)])
-def test_ragged_and_degenerate_shapes_fp64(et_mod, torch_cuda, shape):
-    """Sizes that are not multiples of the 32 x 8 tile, lines, single voxels."""
+def test_ragged_and_degenerate_shapes(et_mod, torch_cuda, shape, precision):
+    """Sizes that are not multiples of the 32 x 8 x 4 tile, lines, single voxels."""
     D = (0.01 + 0.2 * phantom.uniform(4, 7, int(np.prod(shape)))).reshape(shape)
     D = D.astype(np.float32).astype(np.float64)
     u0 = 0.9 * phantom.uniform(4, 8, D.size).reshape(shape)
-    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 3, TOL64)
+    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 3, TOL64, precision=precision)
 
 
+@pytest.mark.parametrize("precision", FP64_FORMS)
 @pytest.mark.parametrize("shift", [0, 1])
-def test_unshifted_and_forced_schedules(et_mod, torch_cuda, shift):
+def test_unshifted_and_forced_schedules(et_mod, torch_cuda, shift, precision):
     D, u0 = phantom.case(20, seed=2, noise=0.1)
-    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 3, TOL64, shift=shift)
+    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 3, TOL64, shift=shift, precision=precision)
     # forced sub-stepping with many short sub-steps also matches
-    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 2, TOL64, shift=shift, force_s=5, force_m=14)
+    _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 2, TOL64, shift=shift, force_s=5, force_m=14,
+                        precision=precision)
 
 
-def test_no_diffusion_and_no_growth_edge_cases(et_mod, torch_cuda):
+@pytest.mark.parametrize("precision", FP64_FORMS)
+def test_no_diffusion_and_no_growth_edge_cases(et_mod, torch_cuda, precision):
     shape = (6, 9, 35)
+    pr = {"precision": precision}
     u0 = phantom.uniform(5, 1, int(np.prod(shape))).reshape(shape)
     # D = 0 everywhere: the pure-reaction closed form per voxel
-    _compare_every_step(et_mod, torch_cuda, np.zeros(shape), u0, 7.3, 2, TOL64)
-    _compare_every_step(et_mod, torch_cuda, np.zeros(shape), u0, 7.3, 2, TOL64, scheme="expeuler")
+    _compare_every_step(et_mod, torch_cuda, np.zeros(shape), u0, 7.3, 2, TOL64, **pr)
+    _compare_every_step(et_mod, torch_cuda, np.zeros(shape), u0, 7.3, 2, TOL64, scheme="expeuler", **pr)
     # rho = 0: pure diffusion
     D, v0 = phantom.case(shape, seed=5, noise=0.1)
-    _compare_every_step(et_mod, torch_cuda, D, v0, 7.3, 2, TOL64, rho=0.0)
+    _compare_every_step(et_mod, torch_cuda, D, v0, 7.3, 2, TOL64, rho=0.0, **pr)
     # u = 0 stays 0
-    _, got, recs = _gpu_states(et_mod, torch_cuda, D, np.zeros(shape), 7.3, 2)
+    _, got, recs = _gpu_states(et_mod, torch_cuda, D, np.zeros(shape), 7.3, 2, **pr)
     assert np.all(got[-1] == 0) and recs[-1]["mass"] == 0
 
 
-def test_fp32_terms_error_is_reported_and_small(et_mod, torch_cuda):
+@pytest.mark.parametrize("shift", [1, 0])
+def test_fp32_terms_error_is_reported_and_small(et_mod, torch_cuda, shift):
     D, u0 = phantom.case(32, seed=0, noise=0.1)
     P = oracle.Problem(D)
     want, _ = P.run(u0, 7.3, 10, every=True)
-    _, got, recs = _gpu_states(et_mod, torch_cuda, D, u0, 7.3, 10, precision="f32")
+    _, got, recs = _gpu_states(et_mod, torch_cuda, D, u0, 7.3, 10, precision="f32", shift=shift)
+    worst = 0.0
     for t in range(10):
         e_max, e_l2 = _errs(got[t], want[t + 1])
+        worst = max(worst, e_max)
         assert e_max <= 1e-5 and e_l2 <= 1e-5, (t, e_max, e_l2)
         assert abs(recs[t]["mass"] - want[t + 1].sum()) <= 1e-5 * want[t + 1].sum()
+    print(f"FP32 terms (shift={shift}): worst max-norm error over 10 steps {worst:.2e}")
 
 
 def test_run_graph_direct_and_host_paths_agree_bitwise(et_mod, torch_cuda):
@@ -152,14 +167,21 @@ def test_run_graph_direct_and_host_paths_agree_bitwise(et_mod, torch_cuda):
     assert rec["step"] == 4
 
 
-def test_full_size_128cubed_first_steps_match_oracle(et_mod, torch_cuda):
+@pytest.fixture(scope="module")
+def oracle_128_three_steps():
+    D, u0 = phantom.case(128, seed=0, noise=0.1)
+    want, ost = oracle.Problem(D).run(u0, 7.3, 3)
+    return D, u0, want, ost
+
+
+@pytest.mark.parametrize("precision", FP64_FORMS)
+def test_full_size_128cubed_first_steps_match_oracle(et_mod, torch_cuda, oracle_128_three_steps,
+                                                     precision):
     """The bench workload (128^3, per-voxel D noise 10 %, tau = 7.3 d), first 3 steps
     element by element against the oracle, in the graph-replayed et_run path."""
     torch = torch_cuda
-    D, u0 = phantom.case(128, seed=0, noise=0.1)
-    P = oracle.Problem(D)
-    want, ost = P.run(u0, 7.3, 3)
-    g = et_mod.Grid(D.shape)
+    D, u0, want, ost = oracle_128_three_steps
+    g = et_mod.Grid(D.shape, precision=precision)
     g.set_coeffs(torch.from_numpy(D).cuda())
     u = torch.from_numpy(u0.copy()).cuda()
     info = g.info_buffer(3)

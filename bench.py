@@ -42,6 +42,10 @@ WORKLOAD = "128^3 head phantom, D noise 10%, rho 0.025/d, 100 steps x tau 7.3 d 
 # DF64: the compensated 8-term dot product and the pair update, 139 FP32 flops.
 TERM_BYTES = {"f64": 72, "df64": 72, "f32": 36}
 TERM_FLOPS = {"f64": 17, "df64": 139, "f32": 17}
+# DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the current kernels (cold cache); None where the kernel
+# changed after the capture.
+TERM_TRAFFIC = {"f64": 131.9e6, "df64": 130.6e6, "f32": 59.5e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -277,15 +281,16 @@ def main():
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         value = world * n * args.nsteps / (ms * 1e-3) / 1e6
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
+        traffic = TERM_TRAFFIC.get(prec) if args.grid == N_GRID else None
         alu_frac = achieved_tflops / alu_peak
         hbm_frac = achieved_gbs / hbm_peak
         if prec == "f64" and alu_frac >= hbm_frac:
             roof = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": alu_frac, "traffic": None,
+                    "frac": alu_frac, "traffic": traffic,
                     "peak_source": "measured FP64 FMA rate (et_probe_alu, this run)"}
         else:
             roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_frac, "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"}
+                    "frac": hbm_frac, "traffic": traffic, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"}
         roof.update({"kernel": "term_kernel", "avg_launch_us": avg_launch_ms * 1e3,
                      "launches_per_run": term_launches, "algorithmic_bytes_per_launch": bytes_per_launch,
                      "algorithmic_flops_per_launch": flops_per_launch,

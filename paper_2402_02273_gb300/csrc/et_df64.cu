@@ -75,16 +75,25 @@ __device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
     return dot_result(A);
 }
 
-// Same tiling and recurrence as term_kernel in et_kernels.cu, in pair arithmetic.
+// Inputs of one voxel-plane of the term: everything except the centre value
+// and the -z neighbour, which are carried from the previous plane.
+struct PlaneDF {
+    float2 dt, wxp, wxm, wyp, wym, zxp, zxm, zyp, zym, zp, wzp, bb, yy, w3;
+};
+
+// Same tiling and recurrence as term_kernel in et_kernels.cu, in pair
+// arithmetic.  The z-march is software-pipelined: the loads of plane k+1 are
+// issued before plane k is computed, so each thread keeps a whole plane of
+// loads in flight while the FP32 pipes work.
 template <int OP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
     const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
     const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
     const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     // restrict-qualified locals: the stores of one plane do not alias the loads of
-    // the next, so the compiler may issue those loads early
+    // the next, so those loads may be issued before the stores
     const float2* __restrict__ z = a.zin;
     const float2* __restrict__ w0 = W.w[0];
     const float2* __restrict__ w1 = W.w[1];
@@ -96,6 +105,8 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
     float2* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
     const float2 zero = make_float2(0.f, 0.f);
+    const bool need_b = a.has_beta || a.base_mode == 1;
+    const bool need_y = a.base_mode == 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x;
         const int rest = t / tiles_x;
@@ -106,34 +117,55 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
         if (i >= G.nx || j >= G.ny) continue;
         const int k0 = tz * kTileZ;
         const int k1 = min(k0 + kTileZ, G.nz);
+        const bool xp = i + 1 < G.nx, xm = i > 0, yp = j + 1 < G.ny, ym = j > 0;
+        auto load = [&](PlaneDF& L, long long q, int k) {
+            L.dt = dtv[q];
+            L.wxp = w0[q];
+            L.wyp = w1[q];
+            L.wzp = w2[q];
+            L.w3 = (OP == ET_OP_LITERAL) ? w3[q] : zero;
+            L.wxm = (OP == ET_OP_CONSERVATIVE && xm) ? w0[q - 1] : zero;
+            L.wym = (OP == ET_OP_CONSERVATIVE && ym) ? w1[q - G.sy] : zero;
+            L.zxp = xp ? z[q + 1] : zero;
+            L.zxm = xm ? z[q - 1] : zero;
+            L.zyp = yp ? z[q + G.sy] : zero;
+            L.zym = ym ? z[q - G.sy] : zero;
+            L.zp = (k + 1 < G.nz) ? z[q + G.sz] : zero;
+            L.bb = need_b ? bv[q] : zero;
+            L.yy = need_y ? yacc[q] : zero;
+        };
         long long p = i + G.sy * j + G.sz * k0;
         float2 zm = (k0 > 0) ? z[p - G.sz] : zero;
-        float2 wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : zero;
+        float2 wzm_c = (OP == ET_OP_CONSERVATIVE && k0 > 0) ? w2[p - G.sz] : zero;
         float2 zc = z[p];
+        PlaneDF cur;
+        load(cur, p, k0);
         for (int k = k0; k < k1; ++k, p += G.sz) {
-            const bool has_zp = k + 1 < G.nz;
-            const float2 zp = has_zp ? z[p + G.sz] : zero;
-            const float2 wzp = w2[p];
+            PlaneDF nxt;
+            if (k + 1 < k1) load(nxt, p + G.sz, k + 1);
+            // literal: the -e weight of every axis is w3[p] (0 on the near wall)
+            const float2 wxm = (OP == ET_OP_CONSERVATIVE) ? cur.wxm : (xm ? cur.w3 : zero);
+            const float2 wym = (OP == ET_OP_CONSERVATIVE) ? cur.wym : (ym ? cur.w3 : zero);
+            const float2 wzm = (OP == ET_OP_CONSERVATIVE) ? wzm_c : ((k > 0) ? cur.w3 : zero);
             DotAcc A;
-            dot_first(A, dtv[p], zc);
-            dot_add(A, w0[p], (i + 1 < G.nx) ? z[p + 1] : zero);
-            dot_add(A, (i > 0) ? (OP == ET_OP_CONSERVATIVE ? w0[p - 1] : w3[p]) : zero, (i > 0) ? z[p - 1] : zero);
-            dot_add(A, w1[p], (j + 1 < G.ny) ? z[p + G.sy] : zero);
-            dot_add(A, (j > 0) ? (OP == ET_OP_CONSERVATIVE ? w1[p - G.sy] : w3[p]) : zero,
-                    (j > 0) ? z[p - G.sy] : zero);
-            dot_add(A, wzp, zp);
+            dot_first(A, cur.dt, zc);
+            dot_add(A, cur.wxp, cur.zxp);
+            dot_add(A, wxm, cur.zxm);
+            dot_add(A, cur.wyp, cur.zyp);
+            dot_add(A, wym, cur.zym);
+            dot_add(A, cur.wzp, cur.zp);
             dot_add(A, wzm, zm);
             float2 acc;
             if (!a.has_zscale) {
-                if (a.has_beta) dot_add(A, a.beta, bv[p]);
+                if (a.has_beta) dot_add(A, a.beta, cur.bb);
                 acc = dot_result(A);
             } else {
                 acc = df_mul(a.zscale, dot_result(A));
-                if (a.has_beta) acc = df_fma(a.beta, bv[p], acc);
+                if (a.has_beta) acc = df_fma(a.beta, cur.bb, acc);
             }
             float2 base;
-            if (a.base_mode == 0) base = yacc[p];
-            else if (a.base_mode == 1) base = df_mul(a.base_scale, bv[p]);
+            if (a.base_mode == 0) base = cur.yy;
+            else if (a.base_mode == 1) base = df_mul(a.base_scale, cur.bb);
             else base = zc;
             float2 sum = df_fma(a.g, acc, base);
             if (!a.last) {
@@ -145,8 +177,9 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
                 else yacc[p] = sum;
             }
             zm = zc;
-            zc = zp;
-            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : zero);
+            zc = cur.zp;
+            wzm_c = cur.wzp;
+            cur = nxt;
         }
     }
 }

@@ -47,7 +47,7 @@ struct Geom {
 
 // Device-side accumulation of per-step observables: block partials, a ticket
 // counter for the last-block reduction, the step index and the flag word.
-constexpr int kStatsBlocks = 512;   // fixed, so the summation order is fixed
+constexpr int kStatsBlocks = 2048;  // fixed, so the summation order is fixed
 constexpr int kStatsThreads = 256;
 struct StatsSink {
     double* partial;        // 3 * kStatsBlocks: sum, min key, max key

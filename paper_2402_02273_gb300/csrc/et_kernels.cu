@@ -188,12 +188,12 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
 // Each thread marches over kTileZ planes, carrying the z-neighbours (and, for
 // the conservative operator, the -z face weight) in registers; blocks loop over
 // tiles so the grid matches the resident-block capacity of the device.
-template <int OP, typename T>
+template <int OP, typename T, int TZ>
 __global__ void __launch_bounds__(kThreads)
 term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
     const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
     const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
-    const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
+    const int tiles_z = (G.nz + TZ - 1) / TZ;
     const int ntiles = tiles_x * tiles_y * tiles_z;
     // restrict-qualified locals: the stores of one plane do not alias the loads of
     // the next, so the compiler may issue those loads early
@@ -215,8 +215,8 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
         const int i = tx * kBlockX + threadIdx.x;
         const int j = ty * kBlockY + threadIdx.y;
         if (i >= G.nx || j >= G.ny) continue;
-        const int k0 = tz * kTileZ;
-        const int k1 = min(k0 + kTileZ, G.nz);
+        const int k0 = tz * TZ;
+        const int k1 = min(k0 + TZ, G.nz);
         long long p = i + G.sy * j + G.sz * k0;
         T zm = (k0 > 0) ? z[p - G.sz] : T(0);
         T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : T(0);
@@ -255,6 +255,42 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
             zc = zp;
             wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : T(0));
         }
+    }
+}
+
+// FP64 term, one voxel per thread over a (32 x 8 x nz)-block grid.  The FP64
+// kernel is bound by the FP64 pipe, so it is kept lean for full occupancy
+// (no plane loop, operands straight from the kernel parameters).
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= G.nx || j >= G.ny) return;
+    const long long p = i + G.sy * j + G.sz * k;
+    const double* __restrict__ z = a.zin;
+    const double zc = z[p];
+    double acc = a.dt[p] * zc;
+    acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : 0.0, acc);
+    acc = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : 0.0, acc);
+    acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : 0.0, acc);
+    acc = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : 0.0, acc);
+    acc = fma(W.w[2][p], (k + 1 < G.nz) ? z[p + G.sz] : 0.0, acc);
+    acc = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? z[p - G.sz] : 0.0, acc);
+    if (a.has_beta) acc = fma(a.beta, a.b[p], acc);
+    double base;
+    if (a.base_mode == 0) base = a.yacc[p];
+    else if (a.base_mode == 1) base = a.base_scale * a.b[p];
+    else base = zc;
+    const double sum = fma(a.g, acc, base);
+    if (!a.last) {
+        a.zout[p] = acc;
+        a.yacc[p] = sum;
+    } else if (a.u) {
+        a.u[p] += sum * a.gamma;
+    } else {
+        a.yacc[p] = sum * a.gamma;
     }
 }
 
@@ -359,12 +395,22 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const
 }
 
 // Resident blocks per SM of a term-kernel instantiation (looked up once).
+// z-planes per thread: the FP64 kernel is bound by the FP64 pipe and runs best
+// at full occupancy with one plane per thread (32 registers); the memory-bound
+// FP32 kernel gains from marching over 4 planes.
+template <typename T>
+struct TermTile {
+    static constexpr int kZ = std::is_same<T, double>::value ? 1 : kTileZ;
+};
+
 template <int OP, typename T>
 int term_blocks_per_sm() {
     static int cached = 0;
     if (!cached) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term_kernel<OP, T>, kThreads, 0) != cudaSuccess || b < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term_kernel<OP, T, TermTile<T>::kZ>, kThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
             b = 1;
         cached = b;
     }
@@ -425,15 +471,23 @@ template <typename T>
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
                         cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
+    if constexpr (std::is_same<T, double>::value) {
+        if (op == ET_OP_CONSERVATIVE)
+            term_kernel_f64<ET_OP_CONSERVATIVE><<<voxel_grid(G), block, 0, stream>>>(G, W, a);
+        else
+            term_kernel_f64<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(G, W, a);
+        return cudaGetLastError();
+    }
+    constexpr int TZ = TermTile<T>::kZ;
     const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
-                            ((G.nz + kTileZ - 1) / kTileZ);
+                            ((G.nz + TZ - 1) / TZ);
     const int sms = G.sms > 0 ? G.sms : 1;
     if (op == ET_OP_CONSERVATIVE) {
         const long long cap = (long long)sms * term_blocks_per_sm<ET_OP_CONSERVATIVE, T>();
-        term_kernel<ET_OP_CONSERVATIVE, T><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
+        term_kernel<ET_OP_CONSERVATIVE, T, TZ><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
     } else {
         const long long cap = (long long)sms * term_blocks_per_sm<ET_OP_LITERAL, T>();
-        term_kernel<ET_OP_LITERAL, T><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
+        term_kernel<ET_OP_LITERAL, T, TZ><<<(unsigned)(tiles < cap ? tiles : cap), block, 0, stream>>>(G, W, a);
     }
     return cudaGetLastError();
 }

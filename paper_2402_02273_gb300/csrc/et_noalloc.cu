@@ -12,7 +12,7 @@
 // Limits and behaviour:
 //  - at most kStaticMaxVoxels = 64^3 = 262144 voxels and at most 65536 thread
 //    blocks of the 32 x 8 stencil tile; larger grids are rejected with
-//    ET_ERR_ARG.  The array is 11 FP64 fields of 64^3 voxels plus 16 KiB of
+//    ET_ERR_ARG.  The array is 11 FP64 fields of 64^3 voxels plus 48 KiB of
 //    partials: 22 MiB held on every GPU that loads it until exit.
 //  - the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress while that device is current, and caches it; make

@@ -126,6 +126,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, device="cuda"):
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, voxels, steps_per_run, ms_per_step):
+    """Voxel-steps per second of all ranks together (replicas: each rank runs its own grid)."""
+    return world * voxels * steps_per_run / (ms_per_step * 1e-3) / 1e6
+
+
 def cpu_baseline(D, u0, seconds=12.0):
     """The FP64 oracle as it stands, on the host cores, on the first steps of the run."""
     import oracle
@@ -259,11 +275,7 @@ def main():
         e1.synchronize()
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = t.item()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         barrier()
         return ms, clocks
 
@@ -279,7 +291,7 @@ def main():
         flops_per_launch = TERM_FLOPS[prec] * n
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
-        value = world * n * args.nsteps / (ms * 1e-3) / 1e6
+        value = whole_job_rate(world, n, args.nsteps, ms)
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
         traffic = TERM_TRAFFIC.get(prec) if args.grid == N_GRID else None
         alu_frac = achieved_tflops / alu_peak
@@ -324,12 +336,8 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = t.item()
-        e2e = {"value": world * n * args.nsteps / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+        e2e = {"value": whole_job_rate(world, n, args.nsteps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n + 40,
                "ms_per_step": e2e_ms,
                "path": "et_set_coeffs_host + et_run_host (pinned host buffers, host wall clock)"}

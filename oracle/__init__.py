@@ -88,6 +88,9 @@ def _load():
             lib.oracle_run.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(_Schedule), ctypes.POINTER(_Stats)]
             lib.oracle_run.restype = ctypes.c_int
+            lib.oracle_step_adjoint.argtypes = [pp, dp, ctypes.c_double, ctypes.POINTER(_Schedule), dp, dp,
+                                                dp, dp]
+            lib.oracle_step_adjoint.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -181,6 +184,30 @@ class Problem:
         st = [{"mass": x.mass, "umin": x.umin, "umax": x.umax, "s": x.s, "m": x.m}
               for x in list(stats)[:nsteps]]
         return (states if every else u), st
+
+
+def _problem_like(P, D):
+    return Problem(D, h=P.h, rho=P.rho, op=P.op, scheme=P.scheme)
+
+
+def vjp(P, u0, tau, nsteps, ubar_final, theta=0.5, stop_tol=1e-18, max_terms=200):
+    """Reverse mode through nsteps oracle steps: given dJ/du_K, returns
+    (dJ/du_0, dJ/drho, d/ds J(s D) at s = 1), every step's schedule frozen at its
+    forward value.  All states are kept (small problems)."""
+    lib = _load()
+    states, _ = P.run(u0, tau, nsteps, theta, stop_tol, max_terms, every=True)
+    sch = _Schedule(theta, stop_tol, max_terms)
+    ubar = np.ascontiguousarray(np.array(ubar_final, dtype=np.float64).reshape(P.shape))
+    g_rho, g_ds = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    for t in range(nsteps - 1, -1, -1):
+        un = np.ascontiguousarray(states[t])
+        out = np.empty(P.shape)
+        rc = lib.oracle_step_adjoint(ctypes.byref(P._p), _dptr(un), float(tau), ctypes.byref(sch),
+                                     _dptr(ubar), _dptr(out), ctypes.byref(g_rho), ctypes.byref(g_ds))
+        if rc != 0:
+            raise RuntimeError(f"oracle_step_adjoint failed ({rc})")
+        ubar = out
+    return ubar, g_rho.value, g_ds.value
 
 
 def set_threads(n: int) -> None:

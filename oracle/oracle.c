@@ -330,3 +330,172 @@ int oracle_run(const oracle_problem* P, double* u, double tau, int nsteps, const
     }
     return 0;
 }
+
+/* (L^T v)_p: the transpose of the diffusion operator, from the row entries of
+ * eq. Amatrix (entry (q, p) of row q for every neighbour q of p, and L_pp). */
+static void apply_LT(const oracle_problem* P, const double* v, double* out) {
+    const long sy = P->nx, sz = (long)P->nx * P->ny;
+    const long n = nvox(P);
+    double* zero_u = (double*)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                const long p = i + sy * j + sz * k;
+                const int coord[3] = {i, j, k};
+                const int extent[3] = {P->nx, P->ny, P->nz};
+                const long stride[3] = {1, sy, sz};
+                double e[7];
+                oracle_row_A(P, zero_u, p, e);
+                /* L_pp is minus the sum of the kept off-diagonal entries */
+                double acc = -(e[1] + e[2] + e[3] + e[4] + e[5] + e[6]) * v[p];
+                for (int a = 0; a < 3; ++a) {
+                    double eq[7];
+                    if (coord[a] > 0) { /* row q = p - e has entry towards +e equal to L_{q,p} */
+                        oracle_row_A(P, zero_u, p - stride[a], eq);
+                        acc += eq[2 + 2 * a] * v[p - stride[a]];
+                    }
+                    if (coord[a] + 1 < extent[a]) { /* row q = p + e, entry towards -e */
+                        oracle_row_A(P, zero_u, p + stride[a], eq);
+                        acc += eq[1 + 2 * a] * v[p + stride[a]];
+                    }
+                }
+                out[p] = acc;
+            }
+    free(zero_u);
+}
+
+/* Reverse of oracle_step.  Forward, per sub-step k (x_0 = 0, augmented scalar
+ * a = 1 throughout):  t_1 = h (A x_{k-1} + b),  t_j = (h/j) A t_{j-1},
+ * x_k = x_{k-1} + t_1 + ... + t_J;  then u^{n+1} = u^n + x_s, with
+ * A = L + diag(c), c = rho (1 - 2u^n) (folded scheme) or 0, b = L u^n + rho u^n (1 - u^n).
+ * Reverse, from xbar = ubar_next:
+ *   tbar_J = xbar;  tbar_j = xbar + (h/(j+1)) A^T tbar_{j+1};
+ *   xbar_{k-1} = xbar + h A^T tbar_1;   bbar += h tbar_1;
+ *   cbar_p += h tbar_1,p x_{k-1},p + sum_{j>=2} (h/j) tbar_j,p t_{j-1},p;
+ *   d/ds (L -> sL) += h <tbar_1, L x_{k-1}> + sum_{j>=2} (h/j) <tbar_j, L t_{j-1}>;
+ * then ubar = ubar_next + L^T bbar + rho (1 - 2u) bbar - 2 rho cbar,
+ * d/drho += <u(1-u), bbar> + <1 - 2u, cbar>,  d/ds += <bbar, L u>. */
+int oracle_step_adjoint(const oracle_problem* P, const double* un, double tau, const oracle_schedule* S,
+                        const double* ubar_next, double* ubar, double* grad_rho, double* grad_dscale) {
+    const long n = nvox(P);
+    const double theta = S ? S->theta : 0.5;
+    const double stop_tol = S ? S->stop_tol : 1e-18;
+    const int max_terms = S ? S->max_terms : 200;
+    const int folded = P->scheme != ORACLE_SCHEME_EXPEULER;
+    const double normA = oracle_norm_inf_A(P, un);
+    int s = (int)ceil(tau * normA / theta);
+    if (s < 1) s = 1;
+    const double h = tau / s;
+    const double theta_eff = h * normA;
+
+    double* b = (double*)malloc((size_t)n * sizeof(double));
+    double* xs = (double*)malloc((size_t)(s + 1) * n * sizeof(double)); /* x_0 .. x_s */
+    int* nterms = (int*)calloc((size_t)s, sizeof(int));
+    double* work = (double*)malloc((size_t)n * sizeof(double));
+    double* work2 = (double*)malloc((size_t)n * sizeof(double));
+    double* bbar = (double*)calloc((size_t)n, sizeof(double));
+    double* cbar = (double*)calloc((size_t)n, sizeof(double));
+    double* xbar = (double*)malloc((size_t)n * sizeof(double));
+    double* tbar = (double*)malloc((size_t)n * sizeof(double));
+    double* tbar_prev = (double*)malloc((size_t)n * sizeof(double));
+    double* tstore = NULL;
+    if (!b || !xs || !nterms || !work || !work2 || !bbar || !cbar || !xbar || !tbar || !tbar_prev) return -1;
+
+    /* b = L u + rho u (1 - u) (equal to A u + f for both schemes, eq. F) */
+    oracle_apply_L(P, un, b);
+    for (long p = 0; p < n; ++p) b[p] += P->rho * un[p] * (1.0 - un[p]);
+    const double bnorm = norm_inf(b, n, P->nz);
+
+    /* forward sub-steps, recording x_k and the number of terms */
+    memset(xs, 0, (size_t)n * sizeof(double));
+    for (int k = 1; k <= s; ++k) {
+        double* xprev = xs + (size_t)(k - 1) * n;
+        double* xk = xs + (size_t)k * n;
+        memcpy(xk, xprev, (size_t)n * sizeof(double));
+        memcpy(work, xprev, (size_t)n * sizeof(double)); /* term */
+        double ta = 1.0;
+        int j = 1;
+        for (;; ++j) {
+            oracle_apply_A(P, un, work, work2);
+            for (long p = 0; p < n; ++p) work2[p] = (h / j) * (work2[p] + b[p] * ta);
+            ta = 0.0;
+            for (long p = 0; p < n; ++p) xk[p] += work2[p];
+            double* t = work; work = work2; work2 = t;
+            if (j >= 8) {
+                const double tn = norm_inf(work, n, P->nz);
+                const double xn = norm_inf(xk, n, P->nz);
+                const double scale = xn > h * bnorm ? xn : h * bnorm;
+                if (tn * theta_eff / (j + 1 - theta_eff) <= stop_tol * scale) break;
+            }
+            if (j >= max_terms) break;
+        }
+        nterms[k - 1] = j;
+    }
+
+    /* reverse sub-steps */
+    memcpy(xbar, ubar_next, (size_t)n * sizeof(double));
+    double gscale = 0.0;
+    for (int k = s; k >= 1; --k) {
+        const int J = nterms[k - 1];
+        const double* xprev = xs + (size_t)(k - 1) * n;
+        /* recompute t_1 .. t_J of this sub-step */
+        tstore = (double*)realloc(tstore, (size_t)(J + 1) * n * sizeof(double));
+        oracle_apply_A(P, un, xprev, work);
+        for (long p = 0; p < n; ++p) tstore[n + p] = h * (work[p] + b[p]);
+        for (int j = 2; j <= J; ++j) {
+            oracle_apply_A(P, un, tstore + (size_t)(j - 1) * n, work);
+            for (long p = 0; p < n; ++p) tstore[(size_t)j * n + p] = (h / j) * work[p];
+        }
+        /* tbar_J = xbar, then down to tbar_1 */
+        memcpy(tbar, xbar, (size_t)n * sizeof(double));
+        for (int j = J; j >= 2; --j) {
+            /* t_j = (h/j) A t_{j-1}: contributions of tbar_j */
+            const double* tprev = tstore + (size_t)(j - 1) * n;
+            oracle_apply_L(P, tprev, work);
+            for (long p = 0; p < n; ++p) {
+                cbar[p] += (h / j) * tbar[p] * tprev[p];
+                gscale += (h / j) * tbar[p] * work[p];
+            }
+            /* tbar_{j-1} = xbar + (h/j) A^T tbar_j */
+            apply_LT(P, tbar, work);
+            for (long p = 0; p < n; ++p) {
+                const double cp = folded ? P->rho * (1.0 - 2.0 * un[p]) : 0.0;
+                tbar_prev[p] = xbar[p] + (h / j) * (work[p] + cp * tbar[p]);
+            }
+            double* t = tbar; tbar = tbar_prev; tbar_prev = t;
+        }
+        /* t_1 = h (A x_{k-1} + b) */
+        oracle_apply_L(P, xprev, work);
+        for (long p = 0; p < n; ++p) {
+            cbar[p] += h * tbar[p] * xprev[p];
+            gscale += h * tbar[p] * work[p];
+            bbar[p] += h * tbar[p];
+        }
+        apply_LT(P, tbar, work);
+        for (long p = 0; p < n; ++p) {
+            const double cp = folded ? P->rho * (1.0 - 2.0 * un[p]) : 0.0;
+            xbar[p] = xbar[p] + h * (work[p] + cp * tbar[p]);
+        }
+    }
+    /* x_0 = 0 does not depend on anything: xbar_0 is dropped.
+     * u^{n+1} = u^n + x_s; b and c depend on u^n, rho and the D scale. */
+    apply_LT(P, bbar, work);
+    oracle_apply_L(P, un, work2);
+    double grho = 0.0;
+    for (long p = 0; p < n; ++p) {
+        double up = un[p];
+        ubar[p] = ubar_next[p] + work[p] + P->rho * (1.0 - 2.0 * up) * bbar[p];
+        grho += up * (1.0 - up) * bbar[p];
+        gscale += bbar[p] * work2[p];
+        if (folded) {
+            ubar[p] += -2.0 * P->rho * cbar[p];
+            grho += (1.0 - 2.0 * up) * cbar[p];
+        }
+    }
+    if (grad_rho) *grad_rho += grho;
+    if (grad_dscale) *grad_dscale += gscale;
+    free(b); free(xs); free(nterms); free(work); free(work2); free(bbar); free(cbar);
+    free(xbar); free(tbar); free(tbar_prev); free(tstore);
+    return 0;
+}

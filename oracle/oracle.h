@@ -70,6 +70,14 @@ int oracle_step(const oracle_problem* P, double* u, double tau, const oracle_sch
 int oracle_run(const oracle_problem* P, double* u, double tau, int nsteps, const oracle_schedule* S,
                oracle_stats* stats);
 
+/* Discrete adjoint of oracle_step (reverse mode through the same loops, with
+ * the schedule s and the number of Taylor terms of every sub-step frozen at
+ * the values the forward step takes from u^n).  Given ubar_next = dJ/du^{n+1},
+ * writes ubar = dJ/du^n and adds dJ/drho to *grad_rho and d/ds J(s D)|_{s=1}
+ * to *grad_dscale. */
+int oracle_step_adjoint(const oracle_problem* P, const double* un, double tau, const oracle_schedule* S,
+                        const double* ubar_next, double* ubar, double* grad_rho, double* grad_dscale);
+
 #ifdef __cplusplus
 }
 #endif

@@ -203,6 +203,21 @@ ET_API et_status et_get_timing(et_grid* g, double* term_ms, long long* term_laun
  * diffusion bound rmax (0 before et_set_coeffs). */
 ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, double* rmax);
 
+/* Vector-Jacobian product of nsteps steps (reverse mode, the discrete adjoint
+ * of the computed step with every step's (s, m, mu) frozen):  given
+ * ubar_final = dJ/du^K for u^K = step^K(u0), returns dJ/du0 in ubar0, dJ/drho
+ * in *grad_rho and d/ds J(s D)|_{s=1} (D scaled uniformly) in *grad_dscale.
+ * Runs its own forward pass from u0 keeping u every checkpoint_every steps,
+ * then recomputes each segment of steps and each step's Taylor terms while
+ * reversing them.  ET_F64 and ET_F32 grids (ET_ERR_UNSUPPORTED for ET_DF64).
+ *  u0, ubar_final, ubar0: device, n FP64 values (ubar0 may alias neither).
+ *  workspace: device, >= et_vjp_workspace_bytes(...), 256-byte aligned.
+ * Synchronises the stream (the two gradients are read back). */
+ET_API size_t et_vjp_workspace_bytes(const et_grid* g, double tau, int nsteps, int checkpoint_every);
+ET_API et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int checkpoint_every,
+                        const double* ubar_final, double* ubar0, double* grad_rho, double* grad_dscale,
+                        void* workspace, size_t workspace_bytes);
+
 /* One step that allocates nothing (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory at call time, e.g. code inside a
  * framework whose pool owns all device memory, or code run while a memory

@@ -76,6 +76,8 @@ _SIGS = {
     "et_get_info": ([_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
                      ctypes.POINTER(_D)], _I),
     "et_destroy": ([_VP], None),
+    "et_vjp_workspace_bytes": ([_VP, _D, _I, _I], ctypes.c_size_t),
+    "et_vjp": ([_VP, _VP, _D, _I, _I, _VP, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP, ctypes.c_size_t], _I),
     "et_step_static": ([_I, _I, _I, _D, _VP, _D, _I, _I, _VP, _D, _VP, ctypes.c_char_p, ctypes.c_size_t], _I),
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
@@ -266,6 +268,24 @@ class Grid:
         self._chk(self.lib.et_get_timing(self.handle, ctypes.byref(ms), ctypes.byref(tl), ctypes.byref(ol)))
         return ms.value, tl.value, ol.value
 
+    def vjp(self, u0, tau, nsteps, ubar_final, checkpoint_every=10):
+        """Reverse mode through nsteps steps from u0 (device tensors, float64):
+        returns (dJ/du0, dJ/drho, d/ds J(s D) at s = 1) for the cotangent
+        ubar_final = dJ/du^K.  Uses a temporary device workspace."""
+        torch = self._torch
+        nbytes = self.lib.et_vjp_workspace_bytes(self.handle, float(tau), int(nsteps), int(checkpoint_every))
+        if nbytes == 0:
+            raise EtError(ET_ERR_STATE, "no adjoint workspace size (coefficients set? tau valid?)")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+        ubar0 = torch.empty_like(u0)
+        g_rho, g_ds = _D(), _D()
+        self._chk(self.lib.et_vjp(self.handle, self._dev_f64(u0, "u0"), float(tau), int(nsteps),
+                                  int(checkpoint_every), self._dev_f64(ubar_final, "ubar_final"),
+                                  self._dev_f64(ubar0, "ubar0"), ctypes.byref(g_rho), ctypes.byref(g_ds),
+                                  ws_ptr, nbytes))
+        return ubar0, g_rho.value, g_ds.value
+
     def set_stream(self, stream):
         self.stream = stream
         self._chk(self.lib.et_set_stream(self.handle, stream.cuda_stream))
@@ -286,3 +306,41 @@ def probe_alu(stream=None):
 def _rec_dict(rec):
     return {"umin": rec.umin, "umax": rec.umax, "mass": rec.mass, "s": rec.s, "m": rec.m,
             "flags": rec.flags, "step": rec.step}
+
+
+def tumour_run(u0, rho, dscale, D0, tau, nsteps, grid=None, checkpoint_every=10, **coeff_opts):
+    """u^K = step^K(u0) with D = dscale * D0, differentiable in u0, rho and dscale.
+
+    u0: float64 CUDA tensor (n values); rho, dscale: 0-d float64 tensors (or
+    floats); D0: float64 CUDA tensor of per-voxel diffusion.  The backward pass
+    is the library's discrete adjoint (et_vjp), checkpointed every
+    `checkpoint_every` steps; the schedule (s, m, mu) is frozen at the forward
+    values.  `grid`: a Grid of the right shape (created if None).
+    """
+    import torch
+
+    class _TumourRun(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0_, rho_, dscale_):
+            g = grid if grid is not None else Grid(D0.shape)
+            r = float(rho_)
+            ds = float(dscale_)
+            g.set_coeffs(D0 * ds, rho=r, **coeff_opts)
+            u = u0_.detach().clone().contiguous()
+            g.run(u, tau, nsteps)
+            g.sync_info()
+            ctx.g, ctx.ds = g, ds
+            ctx.devs = (rho_.device, dscale_.device)
+            ctx.save_for_backward(u0_.detach())
+            return u
+
+        @staticmethod
+        def backward(ctx, ubar):
+            (u0s,) = ctx.saved_tensors
+            ubar0, g_rho, g_ds = ctx.g.vjp(u0s, tau, nsteps, ubar.contiguous(), checkpoint_every)
+            # D = dscale D0:  dJ/d dscale = (1 / dscale) d/ds J(s D) at s = 1
+            return (ubar0, torch.tensor(g_rho, dtype=torch.float64, device=ctx.devs[0]),
+                    torch.tensor(g_ds / ctx.ds, dtype=torch.float64, device=ctx.devs[1]))
+
+    as_t = lambda v: v if isinstance(v, torch.Tensor) else torch.tensor(float(v), dtype=torch.float64)
+    return _TumourRun.apply(u0, as_t(rho), as_t(dscale))

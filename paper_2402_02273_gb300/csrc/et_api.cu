@@ -4,7 +4,9 @@
 // cudaStream_t.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -30,7 +32,7 @@ size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
 
 struct Layout {
     size_t w[5];      // FP64 coefficient fields (all forms; the residual reads them)
-    size_t wt[4];     // typed, 1/nu-scaled copies of w[0..3] (F32, DF64)
+    size_t wt[5];     // typed, 1/nu-scaled copies of w[0..4] (F32, DF64)
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
     size_t partial;   // 3 * nblocks doubles
@@ -59,7 +61,7 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     };
     const size_t vb = value_bytes(prec);
     for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * n);
-    for (int a = 0; a < 4; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * n) : SIZE_MAX;
+    for (int a = 0; a < 5; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * n) : SIZE_MAX;
     for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * n);
     L->stage = take(8ull * n);
     L->partial = take(3ull * 8ull * kStatsBlocks);
@@ -122,7 +124,7 @@ struct et_grid {
     cudaStream_t capture;  // private stream used only for graph capture
     // device views
     double* w[5];
-    void* wt[4];
+    void* wt[5];
     void* vec[6];
     double* stage;
     double* partial;
@@ -234,82 +236,135 @@ Buffers<T> typed_buffers(et_grid* g) {
 // with weights theta^j / j!, theta = h nu, so the vectors stay O(|b| / nu).
 // On sub-step 0, zeta_1 = b / nu is read as b with the stencil part scaled by
 // 1 / nu (zscale).
-template <typename T>
-cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Schedule& S, double hstep,
-                          cudaStream_t st, long long* launches) {
+// One launched term of the chain, in forward order: it computes z_{j+1} of
+// sub-step k from z_j (or from b / y_k on the first term of a sub-step).
+struct PlannedTerm {
+    int k, j;
+    double beta;        // coefficient of b
+    double gnext;       // weight of z_{j+1} in the sub-step sum
+    double base_scale;  // base_mode 1: the first term's weight h on b
+    int base_mode;      // 0: running sum; 1: h b; 2: y_k
+    bool last;          // last term of its sub-step
+    bool zscale_on;     // stencil part scaled by 1/nu (first term, normalised forms)
+};
+
+struct ChainPlan {
+    double gamma = 1.0;  // e^{mu h}
+    double inv_nu = 1.0; // 1/nu (normalised forms) or 1
+    std::vector<PlannedTerm> terms;
+};
+
+ChainPlan plan_chain(const et_grid* g, const Schedule& S, double hstep) {
+    ChainPlan P;
     const int s = S.s, m = S.m;
     const double mu = S.mu;
     const bool normalised = g->prec != ET_F64;
     const double nu = normalised ? g->nu : 1.0;
     const double hw = normalised ? hstep * nu : hstep;  // ratio of consecutive weights times (j+1)
-    const double gamma = std::exp(mu * hstep);
+    P.gamma = std::exp(mu * hstep);
+    P.inv_nu = 1.0 / nu;
     double ak = 1.0;  // augmented scalar at the start of sub-step k
-    int zi = 0;       // next z buffer to write
     for (int k = 0; k < s; ++k) {
-        T* yacc = B.Y[(k + 1) & 1];
-        const T* ycur = B.Y[k & 1];
         double pw = 1.0;  // (-mu)^j / nu^{j+1} (normalised) or (-mu)^j
         double gj = 1.0;  // weight of term j
-        const T* zin = nullptr;
         int j0 = 0;
         if (k == 0) {
             // y_0 = 0, so the first term is a_0 b: no launch for it
             pw = -mu / nu;
             gj = hw;
-            zin = B.b;
             j0 = 1;
-        } else {
-            zin = ycur;
         }
         if (normalised) pw /= nu;
         for (int j = j0; j < m; ++j) {
-            TermArgs<T> a;
-            a.zin = zin;
-            a.b = B.b;
-            a.beta = Scalar<T>::make(ak * pw);
-            a.has_beta = (ak * pw) != 0.0;
-            a.zscale = Scalar<T>::make(1.0 / nu);
-            a.has_zscale = normalised && k == 0 && j == 1;
-            a.dt = B.dt;
-            const double gnext = gj * hw / (j + 1);
-            a.g = Scalar<T>::make(gnext);
-            a.gamma = Scalar<T>::make(1.0);
-            a.base_scale = Scalar<T>::make(0.0);
+            PlannedTerm t;
+            t.k = k;
+            t.j = j;
+            t.beta = ak * pw;
+            t.gnext = gj * hw / (j + 1);
+            t.base_scale = 0.0;
             if (k == 0 && j == 1) {
-                a.base_mode = 1;
-                a.base_scale = Scalar<T>::make(hstep);  // first term h b
+                t.base_mode = 1;
+                t.base_scale = hstep;  // first term h b
             } else if (k > 0 && j == 0) {
-                a.base_mode = 2;  // y_k, read as the centre of z_0
+                t.base_mode = 2;  // y_k, read as the centre of z_0
             } else {
-                a.base_mode = 0;
+                t.base_mode = 0;
             }
-            a.last = (j + 1 == m);
-            a.yacc = yacc;
-            a.u = nullptr;
-            a.zout = nullptr;
-            if (!a.last) {
-                a.zout = B.Z[zi];
-            } else {
-                a.gamma = Scalar<T>::make(gamma);
-                if (k == s - 1) a.u = u;
-            }
-            cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
-            if (e != cudaSuccess) return e;
-            ++*launches;
-            if (!a.last) {
-                zin = B.Z[zi];
-                zi ^= 1;
-            }
+            t.last = (j + 1 == m);
+            t.zscale_on = normalised && k == 0 && j == 1;
+            P.terms.push_back(t);
             pw *= -mu / nu;
-            gj = gnext;
+            gj = t.gnext;
         }
         // augmented scalar after the sub-step: e^{mu h} * sum_j a_k (-mu h)^j / j!
-        double sum = 0.0, t = 1.0;
+        double sum = 0.0, tt = 1.0;
         for (int j = 0; j <= m; ++j) {
-            sum += t;
-            t *= (-mu * hstep) / (j + 1);
+            sum += tt;
+            tt *= (-mu * hstep) / (j + 1);
         }
-        ak = gamma * ak * sum;
+        ak = P.gamma * ak * sum;
+    }
+    return P;
+}
+
+// Storage of a recorded forward step for the adjoint: z_j of sub-step k at
+// zstore + (k m + j) n and y_k at ystore + k n (values of type T).
+template <typename T>
+struct ChainRecord {
+    T* zstore = nullptr;
+    T* ystore = nullptr;
+    long long n = 0;
+    int m = 0;
+    T* z(int k, int j) const { return zstore + ((long long)k * m + j) * n; }
+    T* y(int k) const { return ystore + (long long)k * n; }
+};
+
+// Enqueues the s*m - 1 Taylor-term launches of one step (Sec. 2.2); counts
+// them in *launches.
+//
+// FP64 runs the scaled recurrence of et_kernels.cu, z^_{j+1} = A~ z^_j +
+// a_k (-mu)^j b with weights g_j = h^j / j!.  FP32 and DF64 run it normalised
+// by nu (weights and diagonal already divided by nu): zeta_j = z^_j / nu^j,
+//     zeta_{j+1} = (A~/nu) zeta_j + a_k (-mu)^j / nu^{j+1} b,
+// with weights theta^j / j!, theta = h nu, so the vectors stay O(|b| / nu).
+// On sub-step 0, zeta_1 = b / nu is read as b with the stencil part scaled by
+// 1 / nu (zscale).  With `rec`, every z_j and y_k goes to the record instead
+// of the ping-pong buffers and u is left unchanged.
+template <typename T>
+cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Schedule& S, double hstep,
+                          cudaStream_t st, long long* launches, const ChainRecord<T>* rec = nullptr) {
+    const ChainPlan P = plan_chain(g, S, hstep);
+    const int s = S.s;
+    int zi = 0;  // next z buffer to write
+    const T* zin = nullptr;
+    for (const PlannedTerm& t : P.terms) {
+        const int k = t.k, j = t.j;
+        T* yacc = rec ? rec->y(k + 1) : B.Y[(k + 1) & 1];
+        if (k == 0 && j == 1) zin = B.b;
+        if (k > 0 && j == 0) zin = rec ? rec->y(k) : B.Y[k & 1];
+        TermArgs<T> a;
+        a.zin = zin;
+        a.b = B.b;
+        a.beta = Scalar<T>::make(t.beta);
+        a.has_beta = t.beta != 0.0;
+        a.zscale = Scalar<T>::make(P.inv_nu);
+        a.has_zscale = t.zscale_on;
+        a.dt = B.dt;
+        a.g = Scalar<T>::make(t.gnext);
+        a.gamma = Scalar<T>::make(t.last ? P.gamma : 1.0);
+        a.base_scale = Scalar<T>::make(t.base_scale);
+        a.base_mode = t.base_mode;
+        a.last = t.last;
+        a.yacc = yacc;
+        a.u = (t.last && k == s - 1 && !rec) ? u : nullptr;
+        a.zout = t.last ? nullptr : (rec ? rec->z(k, j + 1) : B.Z[zi]);
+        cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        if (!t.last) {
+            zin = a.zout;
+            if (!rec) zi ^= 1;
+        }
     }
     return cudaSuccess;
 }
@@ -499,6 +554,7 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
         if (g->prec == ET_F32) {
             float* dst[4] = {(float*)g->wt[0], (float*)g->wt[1], (float*)g->wt[2], (float*)g->wt[3]};
             e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
+            if (e == cudaSuccess) e = launch_cast(g->n, g->w[4], 1.0 / g->nu, (float*)g->wt[4], g->stream);
         } else {
             float2* dst[4] = {(float2*)g->wt[0], (float2*)g->wt[1], (float2*)g->wt[2], (float2*)g->wt[3]};
             e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
@@ -511,6 +567,204 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     g->opt_set = opt != nullptr;
     if (opt) g->opt = *opt;
     g->coeffs_set = true;
+    return ET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (vector-Jacobian product) of nsteps steps, checkpointed.
+
+struct AdjLayout {
+    size_t zstore, ystore, ckpt, seg, ubar[2], bbar, cbar, zbar[2], ybar[2], sacc, racc, partial, slots;
+    size_t total;
+    int nck;
+};
+
+bool adj_layout(const et_grid* g, const Schedule& S, int nsteps, int ck, AdjLayout* A) {
+    const size_t n = (size_t)g->n;
+    const size_t vb = value_bytes(g->prec);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    A->nck = (nsteps + ck - 1) / ck;
+    A->zstore = take((size_t)S.s * S.m * vb * n);
+    A->ystore = take((size_t)(S.s + 1) * vb * n);
+    A->ckpt = take((size_t)A->nck * 8 * n);
+    A->seg = take((size_t)ck * 8 * n);
+    for (int i = 0; i < 2; ++i) A->ubar[i] = take(8 * n);
+    A->bbar = take(vb * n);
+    A->cbar = take(vb * n);
+    for (int i = 0; i < 2; ++i) A->zbar[i] = take(vb * n);
+    for (int i = 0; i < 2; ++i) A->ybar[i] = take(vb * n);
+    A->sacc = take(8 * n);
+    A->racc = take(8 * n);
+    A->partial = take(sum_partials_bytes());
+    A->slots = take(64);
+    A->total = off;
+    return true;
+}
+
+// Reverse of one recorded step: given ubar_next = dJ/du^{n+1}, writes ubar =
+// dJ/du^n and accumulates the per-voxel rho and D-scale cotangents.
+template <typename T>
+et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, const double* un,
+                               const double* ubar_next, double* ubar, char* ws, const AdjLayout& A,
+                               cudaStream_t st) {
+    Buffers<T> B = typed_buffers<T>(g);
+    const long long n = g->n;
+    Weights<double> W64;
+    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+    // 1. record the forward step from u^n
+    const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
+    const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
+    cudaError_t e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, dt_scale, g->scheme,
+                                       const_cast<T*>(B.b), B.dt, g->flags, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
+    ChainRecord<T> rec;
+    rec.zstore = (T*)(ws + A.zstore);
+    rec.ystore = (T*)(ws + A.ystore);
+    rec.n = n;
+    rec.m = S.m;
+    long long launches = 0;
+    e = enqueue_chain<T>(g, B, nullptr, S, hstep, st, &launches, &rec);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "recording launch: %s", cudaGetErrorString(e));
+    // 2. reverse the chain
+    T* bbar = (T*)(ws + A.bbar);
+    T* cbar = (T*)(ws + A.cbar);
+    T* zbar[2] = {(T*)(ws + A.zbar[0]), (T*)(ws + A.zbar[1])};
+    T* ybar[2] = {(T*)(ws + A.ybar[0]), (T*)(ws + A.ybar[1])};
+    double* sacc = (double*)(ws + A.sacc);
+    double* racc = (double*)(ws + A.racc);
+    ET_CUDA(g, cudaMemsetAsync(bbar, 0, sizeof(T) * n, st));
+    ET_CUDA(g, cudaMemsetAsync(cbar, 0, sizeof(T) * n, st));
+    const T* ynext;  // cotangent of y_{k+1}
+    int yi = 0;
+    if constexpr (std::is_same<T, double>::value) {
+        ynext = ubar_next;
+    } else {
+        e = launch_cast(n, ubar_next, 1.0, ybar[0], st);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "cast launch: %s", cudaGetErrorString(e));
+        ynext = ybar[0];
+        yi = 1;
+    }
+    const ChainPlan P = plan_chain(g, S, hstep);
+    Weights<T> WT = B.W;
+    WT.w[4] = g->prec == ET_F64 ? (const T*)g->w[4] : (const T*)g->wt[4];
+    int zi = 0;
+    const T* wprev = nullptr;  // zbar_{j+1} from the previous reverse term
+    for (int idx = (int)P.terms.size() - 1; idx >= 0; --idx) {
+        const PlannedTerm& t = P.terms[idx];
+        const int k = t.k, j = t.j;
+        const bool first_reverse = t.last;            // j = m - 1: w = g_m Sbar
+        const bool into_b = (k == 0 && j == 1);        // forward input is b
+        const bool into_y = (k > 0 && j == 0);         // forward input is y_k
+        AdjTermArgs<T> a;
+        if (first_reverse) {
+            a.wsrc = ynext;
+            a.wscale = Scalar<T>::make(t.gnext * P.gamma);
+        } else {
+            a.wsrc = wprev;
+            a.wscale = Scalar<T>::make(1.0);
+        }
+        a.dt = B.dt;
+        a.negR = WT.w[4];
+        a.ybar_next = ynext;
+        a.gamma = Scalar<T>::make(P.gamma);
+        // coefficient of the forward input in the sub-step sum
+        double gin;
+        if (into_b) gin = t.base_scale;
+        else if (into_y) gin = 1.0;
+        else gin = P.terms[idx - 1].gnext;
+        a.g = Scalar<T>::make(gin);
+        a.f = Scalar<T>::make(t.zscale_on ? P.inv_nu : 1.0);
+        a.inv_nu = Scalar<T>::make(P.inv_nu);
+        a.x = into_b ? B.b : (into_y ? rec.y(k) : rec.z(k, j));
+        a.has_beta = t.beta != 0.0;
+        a.beta = Scalar<T>::make(t.beta);
+        a.bbar = bbar;
+        a.cbar = cbar;
+        a.sbar_acc = sacc;
+        a.out_to_bbar = into_b;
+        if (into_y) {
+            a.zbar_out = ybar[yi];
+        } else {
+            a.zbar_out = zbar[zi];
+        }
+        e = launch_adj_term<T>(g->G, g->op, WT, a, st);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "adjoint term launch: %s", cudaGetErrorString(e));
+        if (into_y) {
+            // ybar_k is the cotangent of the previous sub-step's result
+            ynext = ybar[yi];
+            yi ^= 1;
+        } else if (!into_b) {
+            wprev = zbar[zi];
+            zi ^= 1;
+        }
+    }
+    // 3. through b = L u + rho u (1 - u) and c = rho (1 - 2u) to u^n, rho, D scale
+    e = launch_adj_step<T>(g->G, g->op, W64, un, bbar, cbar, ubar_next, g->rho, g->scheme, ubar, sacc, racc, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "adjoint step launch: %s", cudaGetErrorString(e));
+    return ET_OK;
+}
+
+template <typename T>
+et_status vjp_impl(et_grid* g, const double* u0, double tau, int nsteps, int ck, const double* ubar_final,
+                   double* ubar0, double* grad_rho, double* grad_dscale, char* ws, const AdjLayout& A,
+                   const Schedule& S) {
+    cudaStream_t st = g->stream;
+    const long long n = g->n;
+    const size_t nb = 8ull * n;
+    const double hstep = tau / S.s;
+    double* ckpt = (double*)(ws + A.ckpt);
+    double* seg = (double*)(ws + A.seg);
+    double* ub[2] = {(double*)(ws + A.ubar[0]), (double*)(ws + A.ubar[1])};
+    long long tl = 0, ol = 0;
+    // forward pass, keeping u at every checkpoint (u^0, u^ck, u^2ck, ...)
+    ET_CUDA(g, cudaMemcpyAsync(ckpt, u0, nb, cudaMemcpyDeviceToDevice, st));
+    ET_CUDA(g, cudaMemcpyAsync(seg, u0, nb, cudaMemcpyDeviceToDevice, st));
+    for (int t = 0; t + 1 < nsteps; ++t) {
+        et_status rc = enqueue_step(g, seg, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
+        if (rc != ET_OK) return rc;
+        if ((t + 1) % ck == 0)
+            ET_CUDA(g, cudaMemcpyAsync(ckpt + (size_t)((t + 1) / ck) * n, seg, nb, cudaMemcpyDeviceToDevice, st));
+    }
+    // reverse pass, segment by segment
+    ET_CUDA(g, cudaMemcpyAsync(ub[0], ubar_final, nb, cudaMemcpyDeviceToDevice, st));
+    ET_CUDA(g, cudaMemsetAsync(ws + A.sacc, 0, nb, st));
+    ET_CUDA(g, cudaMemsetAsync(ws + A.racc, 0, nb, st));
+    int cur = 0;
+    for (int sgi = A.nck - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * ck;
+        const int n1 = std::min(n0 + ck, nsteps);
+        // states u^{n0} .. u^{n1-1} of the segment
+        ET_CUDA(g, cudaMemcpyAsync(seg, ckpt + (size_t)sgi * n, nb, cudaMemcpyDeviceToDevice, st));
+        for (int t = n0; t + 1 < n1; ++t) {
+            double* src = seg + (size_t)(t - n0) * n;
+            double* dst = src + n;
+            ET_CUDA(g, cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, st));
+            et_status rc = enqueue_step(g, dst, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
+            if (rc != ET_OK) return rc;
+        }
+        for (int t = n1 - 1; t >= n0; --t) {
+            et_status rc = enqueue_step_adjoint<T>(g, S, hstep, seg + (size_t)(t - n0) * n, ub[cur], ub[cur ^ 1],
+                                                   ws, A, st);
+            if (rc != ET_OK) return rc;
+            cur ^= 1;
+        }
+    }
+    ET_CUDA(g, cudaMemcpyAsync(ubar0, ub[cur], nb, cudaMemcpyDeviceToDevice, st));
+    double* partial = (double*)(ws + A.partial);
+    double* slots = (double*)(ws + A.slots);
+    cudaError_t e = launch_sum(n, (double*)(ws + A.racc), partial, slots + 0, st);
+    if (e == cudaSuccess) e = launch_sum(n, (double*)(ws + A.sacc), partial, slots + 1, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "reduction launch: %s", cudaGetErrorString(e));
+    double host[2] = {0.0, 0.0};
+    ET_CUDA(g, cudaMemcpyAsync(host, slots, sizeof(host), cudaMemcpyDeviceToHost, st));
+    ET_CUDA(g, cudaStreamSynchronize(st));
+    if (grad_rho) *grad_rho = host[0];
+    if (grad_dscale) *grad_dscale = host[1];
     return ET_OK;
 }
 
@@ -639,7 +893,7 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     }
     g->stream = (cudaStream_t)cuda_stream;
     for (int a = 0; a < 5; ++a) g->w[a] = (double*)(g->ws + L.w[a]);
-    for (int a = 0; a < 4; ++a) g->wt[a] = precision != ET_F64 ? (void*)(g->ws + L.wt[a]) : nullptr;
+    for (int a = 0; a < 5; ++a) g->wt[a] = precision != ET_F64 ? (void*)(g->ws + L.wt[a]) : nullptr;
     for (int v = 0; v < 6; ++v) g->vec[v] = (void*)(g->ws + L.vec[v]);
     g->stage = (double*)(g->ws + L.stage);
     g->partial = (double*)(g->ws + L.partial);
@@ -788,6 +1042,43 @@ et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, dou
     if (ws_used) *ws_used = g->L.total;
     if (rmax) *rmax = g->coeffs_set ? g->rmax : 0.0;
     return ET_OK;
+}
+
+size_t et_vjp_workspace_bytes(const et_grid* g, double tau, int nsteps, int checkpoint_every) {
+    if (!g || !g->coeffs_set || nsteps < 1 || checkpoint_every < 1) return 0;
+    Schedule S;
+    if (schedule_for(g, tau, &S) != ET_OK) return 0;
+    AdjLayout A;
+    adj_layout(g, S, nsteps, std::min(checkpoint_every, nsteps), &A);
+    return A.total;
+}
+
+et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int checkpoint_every,
+                 const double* ubar_final, double* ubar0, double* grad_rho, double* grad_dscale,
+                 void* workspace, size_t workspace_bytes) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    if (g->prec == ET_DF64) return fail(g, ET_ERR_UNSUPPORTED, "the adjoint is provided for ET_F64 and ET_F32");
+    if (!u0 || !ubar_final || !ubar0 || !aligned8(u0) || !aligned8(ubar_final) || !aligned8(ubar0))
+        return fail(g, ET_ERR_ARG, "u0, ubar_final and ubar0 must be 8-byte aligned device pointers");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(g, ET_ERR_ARG, "tau must be finite and > 0");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(g, ET_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0)
+        return fail(g, ET_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+    Schedule S;
+    if (schedule_for(g, tau, &S) != ET_OK) return fail(g, ET_ERR_ARG, "no (s, m) for tau = %g", tau);
+    const int ck = std::min(checkpoint_every, nsteps);
+    AdjLayout A;
+    adj_layout(g, S, nsteps, ck, &A);
+    if (workspace_bytes < A.total)
+        return fail(g, ET_ERR_ARG, "adjoint workspace has %zu bytes, %zu needed", workspace_bytes, A.total);
+    clear_graphs(g);  // the forward steps below run without graphs
+    if (g->prec == ET_F64)
+        return vjp_impl<double>(g, u0, tau, nsteps, ck, ubar_final, ubar0, grad_rho, grad_dscale,
+                                (char*)workspace, A, S);
+    return vjp_impl<float>(g, u0, tau, nsteps, ck, ubar_final, ubar0, grad_rho, grad_dscale, (char*)workspace,
+                           A, S);
 }
 
 void et_destroy(et_grid* g) {

@@ -100,6 +100,28 @@ struct TermArgs {
     double* u;       // non-null on the last term of the step: u += gamma * sum
 };
 
+// Arguments of one reverse Taylor-term launch (et_adjoint.cu).
+template <typename T>
+struct AdjTermArgs {
+    const T* wsrc;       // w / wscale, read with a one-voxel halo
+    T wscale;
+    const T* dt;         // diagonal of A^ (as in the forward pass)
+    const T* negR;       // minus the row sums of L, times 1/nu
+    const T* ybar_next;  // cotangent of the sub-step result; Sbar = gamma * ybar_next
+    T gamma;
+    T g;                 // coefficient of Sbar in the output
+    T f;                 // factor of the forward term on A^ (1, or 1/nu on the first term)
+    T inv_nu;
+    const T* x;          // forward input of this term
+    int has_beta;
+    T beta;
+    T* bbar;             // cotangent of b (accumulated)
+    T* cbar;             // cotangent of the diagonal rho(1 - 2u) (accumulated)
+    double* sbar_acc;    // per-voxel cotangent of the D scale (accumulated)
+    int out_to_bbar;     // the output adds to bbar instead of zbar_out
+    T* zbar_out;
+};
+
 // Kernel launchers (et_kernels.cu).  All enqueue on `stream` and return the
 // launch error.
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op,
@@ -124,6 +146,20 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const 
                         cudaStream_t stream);
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
+// Adjoint launchers (et_adjoint.cu).
+template <typename T>
+cudaError_t launch_adj_term(const Geom& G, et_operator op, Weights<T> W, const AdjTermArgs<T>& a,
+                            cudaStream_t stream);
+template <typename T>
+cudaError_t launch_adj_step(const Geom& G, et_operator op, Weights<double> W, const double* u, const T* bbar,
+                            const T* cbar, const double* ubar_next, double rho, et_scheme scheme, double* ubar,
+                            double* sbar_acc, double* rbar_acc, cudaStream_t stream);
+// Deterministic sum of v[0..n) into *out; partial holds sum_partials_bytes().
+size_t sum_partials_bytes();
+cudaError_t launch_sum(long long n, const double* v, double* partial, double* out, cudaStream_t stream);
+// dst[p] = (float)(src[p] * scale)
+cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);
+
 // Looks up launch limits (resident blocks per SM) before any stream capture.
 cudaError_t prime_launch_limits();
 cudaError_t prime_launch_limits_df64();

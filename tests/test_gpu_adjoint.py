@@ -1,0 +1,141 @@
+"""The GPU adjoint (et_vjp, discrete reverse mode with checkpointing) against the
+oracle's own adjoint, against central finite differences of the GPU forward map,
+and through torch.autograd.  GPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_02273_gb300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_02273_gb300 as et
+    et.load()
+    return et, torch
+
+
+def _problem(shape, seed=3):
+    D, u0 = phantom.case(shape, seed=seed, noise=0.1)
+    tgt = 0.5 * phantom.uniform(seed, 11, D.size).reshape(shape)
+    return D, u0, tgt
+
+
+@pytest.mark.parametrize("op", ["conservative", "literal"])
+@pytest.mark.parametrize("scheme", ["rosenbrock", "expeuler"])
+def test_vjp_matches_oracle_adjoint(env, op, scheme):
+    et, torch = env
+    shape, tau, K = (18, 20, 22), 7.3, 4
+    D, u0, tgt = _problem(shape)
+    P = oracle.Problem(D, op=op, scheme=scheme)
+    uK, _ = P.run(u0, tau, K)
+    o_ub, o_rho, o_ds = oracle.vjp(P, u0, tau, K, uK - tgt)
+    g = et.Grid(shape)
+    g.set_coeffs(torch.from_numpy(D).cuda(), op=op, scheme=scheme)
+    u0d = torch.from_numpy(u0.copy()).cuda()
+    ubarK = torch.from_numpy((uK - tgt).copy()).cuda()
+    ub, g_rho, g_ds = g.vjp(u0d, tau, K, ubarK, checkpoint_every=3)
+    ub = ub.cpu().numpy().reshape(shape)
+    assert np.abs(ub - o_ub).max() <= 1e-9 * np.abs(o_ub).max()
+    assert g_rho == pytest.approx(o_rho, rel=1e-9)
+    assert g_ds == pytest.approx(o_ds, rel=1e-9)
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient(env):
+    et, torch = env
+    shape, tau, K = (16, 16, 16), 7.3, 7
+    D, u0, tgt = _problem(shape, seed=5)
+    g = et.Grid(shape)
+    g.set_coeffs(torch.from_numpy(D).cuda())
+    u0d = torch.from_numpy(u0.copy()).cuda()
+    ubarK = torch.from_numpy(tgt.copy()).cuda()
+    ref = g.vjp(u0d, tau, K, ubarK, checkpoint_every=1)
+    for ck in (2, 3, 7, 50):
+        got = g.vjp(u0d, tau, K, ubarK, checkpoint_every=ck)
+        assert torch.equal(got[0], ref[0]) and got[1] == ref[1] and got[2] == ref[2]
+
+
+def test_fp32_adjoint_error_is_small(env):
+    et, torch = env
+    shape, tau, K = (18, 20, 22), 7.3, 4
+    D, u0, tgt = _problem(shape)
+    P = oracle.Problem(D)
+    uK, _ = P.run(u0, tau, K)
+    o_ub, o_rho, o_ds = oracle.vjp(P, u0, tau, K, uK - tgt)
+    g = et.Grid(shape, precision="f32")
+    g.set_coeffs(torch.from_numpy(D).cuda())
+    ub, g_rho, g_ds = g.vjp(torch.from_numpy(u0.copy()).cuda(), tau, K,
+                            torch.from_numpy((uK - tgt).copy()).cuda(), checkpoint_every=2)
+    ub = ub.cpu().numpy().reshape(shape)
+    err = np.abs(ub - o_ub).max() / np.abs(o_ub).max()
+    print(f"FP32 adjoint vs oracle: u0 {err:.2e}, rho {abs(g_rho / o_rho - 1):.2e}, "
+          f"D scale {abs(g_ds / o_ds - 1):.2e}")
+    assert err <= 1e-4
+    assert g_rho == pytest.approx(o_rho, rel=1e-4)
+    assert g_ds == pytest.approx(o_ds, rel=1e-4)
+
+
+def test_config4_128cubed_50_steps_against_central_differences(env):
+    """128^3, 50 steps, checkpoints every 10; target from the forward model with
+    rho x 1.1, D scale x 1.1 and the seed shifted by 2 voxels; gradients in rho, the D
+    scale and a random direction of u0 against central differences (eps 1e-6)."""
+    et, torch = env
+    shape, tau, K = (128, 128, 128), 7.3, 50
+    D, u0 = phantom.case(shape, seed=0, noise=0.1)
+    cx, cy, cz = phantom.seed_centre(shape)
+    u0_tgt = phantom.gaussian_blob(shape, (cx + 2.0, cy, cz))
+    Dd = torch.from_numpy(D).cuda()
+    g = et.Grid(shape)
+
+    def forward(u_init, rho, ds):
+        g.set_coeffs(Dd * ds, rho=rho)
+        u = torch.from_numpy(np.ascontiguousarray(u_init)).cuda() if isinstance(u_init, np.ndarray) else u_init.clone()
+        g.run(u, tau, K)
+        g.sync_info()
+        return u
+
+    tgt = forward(u0_tgt, 0.025 * 1.1, 1.1)
+    loss = lambda u: 0.5 * float(((u - tgt) ** 2).sum())
+    rho, ds = 0.025, 1.0
+    uK = forward(u0, rho, ds)
+    g.set_coeffs(Dd, rho=rho)
+    u0d = torch.from_numpy(u0.copy()).cuda()
+    ub, g_rho, g_ds = g.vjp(u0d, tau, K, uK - tgt, checkpoint_every=10)
+    eps = 1e-6
+    fd_rho = (loss(forward(u0, rho + eps, ds)) - loss(forward(u0, rho - eps, ds))) / (2 * eps)
+    fd_ds = (loss(forward(u0, rho, ds + eps)) - loss(forward(u0, rho, ds - eps))) / (2 * eps)
+    v = phantom.uniform(9, 9, D.size).reshape(shape) - 0.5
+    v *= (u0 > 1e-3)  # a direction inside the seed
+    fd_u = (loss(forward(u0 + eps * v, rho, ds)) - loss(forward(u0 - eps * v, rho, ds))) / (2 * eps)
+    ad_u = float((ub.cpu() * torch.from_numpy(v)).sum())
+    print(f"config 4: rho {g_rho:.6e} vs fd {fd_rho:.6e}; D scale {g_ds:.6e} vs {fd_ds:.6e}; "
+          f"u0 dir {ad_u:.6e} vs {fd_u:.6e}")
+    assert g_rho == pytest.approx(fd_rho, rel=1e-5)
+    assert g_ds == pytest.approx(fd_ds, rel=1e-5)
+    assert ad_u == pytest.approx(fd_u, rel=1e-5)
+
+
+def test_autograd_function_gradients(env):
+    et, torch = env
+    shape, tau, K = (10, 11, 12), 7.3, 3
+    D, u0, tgt = _problem(shape, seed=8)
+    D0 = torch.from_numpy(D).cuda()
+    u0d = torch.from_numpy(u0.copy()).cuda().requires_grad_(True)
+    rho = torch.tensor(0.03, dtype=torch.float64, requires_grad=True)
+    ds = torch.tensor(1.2, dtype=torch.float64, requires_grad=True)
+    tg = torch.from_numpy(tgt.copy()).cuda()
+    uK = et.tumour_run(u0d, rho, ds, D0, tau, K, checkpoint_every=2)
+    loss = 0.5 * ((uK - tg) ** 2).sum()
+    loss.backward()
+    # the oracle's gradient at the same point (D = 1.2 D0, rho = 0.03)
+    P = oracle.Problem(1.2 * D, rho=0.03)
+    oK, _ = P.run(u0, tau, K)
+    o_ub, o_rho, o_ds = oracle.vjp(P, u0, tau, K, oK - tgt)
+    assert np.abs(u0d.grad.cpu().numpy() - o_ub).max() <= 1e-9 * np.abs(o_ub).max()
+    assert rho.grad.item() == pytest.approx(o_rho, rel=1e-9)
+    assert ds.grad.item() == pytest.approx(o_ds / 1.2, rel=1e-9)

@@ -47,6 +47,8 @@ TERM_FLOPS = {"f64": 17, "df64": 139, "f32": 17}
 # changed after the capture.
 TERM_TRAFFIC = {"f64": None, "df64": None, "f32": 59.5e6}
 L2_FLUSH_BYTES = 256 << 20
+ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
+ADJ_CK = 10
 
 
 def parse():
@@ -58,6 +60,7 @@ def parse():
     ap.add_argument("--grid", type=int, default=N_GRID)
     ap.add_argument("--nsteps", type=int, default=NSTEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint form")
     ap.add_argument("--no-forms", action="store_true", help="time the plain FP64 form only")
     ap.add_argument("--forms", default="f64,df64,f32",
                     help="comma-separated precision forms to time (the first one is the headline)")
@@ -314,6 +317,35 @@ def main():
         del g
         torch.cuda.empty_cache()
 
+    # adjoint form: one gradient = forward run of ADJ_STEPS steps + et_vjp with
+    # checkpoints every ADJ_CK steps (the misfit cotangent u_K - u_target is the
+    # caller's, computed with one torch subtraction)
+    adjoint = {}
+    if not args.no_adjoint and not args.no_forms:
+        for prec in ("f64", "f32"):
+            g = et.Grid(D.shape, precision=prec, stream=stream)
+            g.set_coeffs(torch.from_numpy(D).to("cuda"), rho=RHO)
+            u0d = torch.from_numpy(u0).to("cuda")
+            tgt = u0d * 0.5
+            u = torch.empty_like(u0d)
+
+            def adj_step():
+                u.copy_(u0d)
+                g.run(u, TAU, ADJ_STEPS)
+                g.vjp(u0d, TAU, ADJ_STEPS, u - tgt, ADJ_CK)
+                flush.add_(1)
+
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    adj_step()
+            ms, clocks = timed(adj_step)
+            adjoint[prec] = {"value": whole_job_rate(world, n, ADJ_STEPS, ms), "unit": UNIT,
+                             "ms_per_gradient": ms, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CK,
+                             "note": "voxel-steps of the forward run per second of forward + adjoint",
+                             "clocks": clocks}
+            del g
+            torch.cuda.empty_cache()
+
     # end to end through the public API with host buffers (pinned): H2D of D and
     # u0, coefficient setup, the 100-step run, D2H of u and of the last record
     e2e = None
@@ -362,6 +394,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": base,
             "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+            "adjoint": adjoint,
             "forms": {p: {"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
                           "dtype": p, "s": results[p]["info"]["s"], "m": results[p]["info"]["m"],
                           "roofline": results[p]["roofline"], "clocks": results[p]["clocks"]}

@@ -35,17 +35,25 @@ NOISE = 0.1
 METRIC = "exp-integrator Mvoxel-steps/s at 128^3 (plain vs chosen form), % HBM roofline"
 UNIT = "Mvoxel-steps/s"
 WORKLOAD = "128^3 head phantom, D noise 10%, rho 0.025/d, 100 steps x tau 7.3 d (2 years), zero-flux"
-# Algorithmic bytes and flops per voxel per Taylor-term launch (shifted scaled
-# recurrence, conservative operator): read z 8, write z 8, three face-weight
-# fields 24, diagonal 8, residual 8, read+write of the sub-step sum 16 (FP64 and
-# DF64 pairs); half of that for FP32.  FP64 / FP32: 8 FMA + 1 MUL = 17 flops;
-# DF64: the compensated 8-term dot product and the pair update, 139 FP32 flops.
+# Algorithmic bytes and flops per voxel of one Taylor-term launch (conservative
+# operator).  Sub-step 0 is evaluated by Horner's rule: read z 8, write z 8,
+# three face-weight fields 24, diagonal 8, residual 8 = 56 B (FP64 and DF64
+# pairs; 28 B in FP32), 7 FMA + 1 MUL = 15 flops (DF64: the compensated 8-term
+# dot product, 118 FP32 flops).  Terms of later sub-steps also read and write
+# the running sum: 72 B (36 B), 17 flops (DF64 139).
+HORNER_BYTES = {"f64": 56, "df64": 56, "f32": 28}
+HORNER_FLOPS = {"f64": 15, "df64": 118, "f32": 15}
 TERM_BYTES = {"f64": 72, "df64": 72, "f32": 36}
 TERM_FLOPS = {"f64": 17, "df64": 139, "f32": 17}
+
+
+def per_launch(table_h, table_t, prec, s, m):
+    """Average over the s*m - 1 launches of a step: m - 1 Horner terms, (s-1) m others."""
+    return (table_h[prec] * (m - 1) + table_t[prec] * (s - 1) * m) / (s * m - 1)
 # DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of the current kernels (cold cache); None where the kernel
 # changed after the capture.
-TERM_TRAFFIC = {"f64": None, "df64": None, "f32": 59.5e6}
+TERM_TRAFFIC = {"f64": None, "df64": None, "f32": None}
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
@@ -290,8 +298,9 @@ def main():
         term_ms, term_launches, other_launches = g.timing()  # last run of the timed region
         rec = g.sync_info()
         avg_launch_ms = term_ms / max(term_launches, 1)
-        bytes_per_launch = TERM_BYTES[prec] * n
-        flops_per_launch = TERM_FLOPS[prec] * n
+        s_, m_ = info["s"], info["m"]
+        bytes_per_launch = per_launch(HORNER_BYTES, TERM_BYTES, prec, s_, m_) * n
+        flops_per_launch = per_launch(HORNER_FLOPS, TERM_FLOPS, prec, s_, m_) * n
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         value = whole_job_rate(world, n, args.nsteps, ms)

@@ -245,7 +245,9 @@ struct PlannedTerm {
     double base_scale;  // base_mode 1: the first term's weight h on b
     int base_mode;      // 0: running sum; 1: h b; 2: y_k
     bool last;          // last term of its sub-step
-    bool zscale_on;     // stencil part scaled by 1/nu (first term, normalised forms)
+    bool zscale_on;     // stencil part scaled by zscale_val (first term of sub-step 0)
+    bool horner;        // a Horner step of sub-step 0
+    double zscale_val;
 };
 
 struct ChainPlan {
@@ -265,36 +267,60 @@ ChainPlan plan_chain(const et_grid* g, const Schedule& S, double hstep) {
     P.inv_nu = 1.0 / nu;
     double ak = 1.0;  // augmented scalar at the start of sub-step k
     for (int k = 0; k < s; ++k) {
-        double pw = 1.0;  // (-mu)^j / nu^{j+1} (normalised) or (-mu)^j
-        double gj = 1.0;  // weight of term j
-        int j0 = 0;
         if (k == 0) {
-            // y_0 = 0, so the first term is a_0 b: no launch for it
-            pw = -mu / nu;
-            gj = hw;
-            j0 = 1;
-        }
-        if (normalised) pw /= nu;
-        for (int j = j0; j < m; ++j) {
-            PlannedTerm t;
-            t.k = k;
-            t.j = j;
-            t.beta = ak * pw;
-            t.gnext = gj * hw / (j + 1);
-            t.base_scale = 0.0;
-            if (k == 0 && j == 1) {
-                t.base_mode = 1;
-                t.base_scale = hstep;  // first term h b
-            } else if (k > 0 && j == 0) {
-                t.base_mode = 2;  // y_k, read as the centre of z_0
-            } else {
-                t.base_mode = 0;
+            // Sub-step 0 starts from y_0 = 0, so its result is gamma P(A^) b with
+            //   P(x) = sum_{j=1..m} g_j q_j(x),  q_1 = 1/nu,  q_{j+1}(x) = x q_j(x) + beta_j,
+            // evaluated by Horner's rule: v = p_{m-1} b, v <- A^ v + p_i b (i = m-2..0).
+            // FP64 uses the monic form (coefficients divided by p_{m-1}, folded into
+            // the final factor); FP32 / DF64 keep p_{m-1} as a scale on the first
+            // stencil so their vectors stay inside the FP32 range.
+            std::vector<double> q(1, 1.0 / nu), pc(m, 0.0);
+            double pw = 1.0;  // (-mu)^j
+            double gj = 1.0;
+            for (int j = 1; j <= m; ++j) {
+                gj *= hw / j;
+                for (size_t i = 0; i < q.size(); ++i) pc[i] += gj * q[i];
+                if (j == m) break;
+                pw *= -mu;
+                const double beta = ak * pw / (normalised ? std::pow(nu, j + 1) : 1.0);
+                q.insert(q.begin(), 0.0);  // x q_j
+                q[0] += beta;
             }
-            t.last = (j + 1 == m);
-            t.zscale_on = normalised && k == 0 && j == 1;
-            P.terms.push_back(t);
-            pw *= -mu / nu;
-            gj = t.gnext;
+            const double lead = pc[m - 1];
+            for (int idx = 0; idx + 1 < m; ++idx) {
+                const int i = m - 2 - idx;
+                PlannedTerm t;
+                t.k = 0;
+                t.j = idx + 1;
+                t.horner = true;
+                t.beta = normalised ? pc[i] : pc[i] / lead;
+                t.zscale_on = normalised && idx == 0;
+                t.zscale_val = normalised ? lead : 1.0;
+                t.last = (idx + 2 == m);
+                t.gnext = t.last ? (normalised ? 1.0 : lead) : 0.0;  // final factor gamma * gnext
+                t.base_scale = 0.0;
+                t.base_mode = 0;
+                P.terms.push_back(t);
+            }
+        } else {
+            double pw = normalised ? 1.0 / nu : 1.0;  // (-mu)^j / nu^{j+1} (normalised) or (-mu)^j
+            double gj = 1.0;                          // weight of term j
+            for (int j = 0; j < m; ++j) {
+                PlannedTerm t;
+                t.k = k;
+                t.j = j;
+                t.horner = false;
+                t.beta = ak * pw;
+                t.gnext = gj * hw / (j + 1);
+                t.base_scale = 0.0;
+                t.base_mode = (j == 0) ? 2 : 0;  // y_k, read as the centre of z_0
+                t.last = (j + 1 == m);
+                t.zscale_on = false;
+                t.zscale_val = 1.0;
+                P.terms.push_back(t);
+                pw *= -mu / nu;
+                gj = t.gnext;
+            }
         }
         // augmented scalar after the sub-step: e^{mu h} * sum_j a_k (-mu h)^j / j!
         double sum = 0.0, tt = 1.0;
@@ -347,14 +373,15 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.b = B.b;
         a.beta = Scalar<T>::make(t.beta);
         a.has_beta = t.beta != 0.0;
-        a.zscale = Scalar<T>::make(P.inv_nu);
+        a.zscale = Scalar<T>::make(t.zscale_val);
         a.has_zscale = t.zscale_on;
         a.dt = B.dt;
         a.g = Scalar<T>::make(t.gnext);
-        a.gamma = Scalar<T>::make(t.last ? P.gamma : 1.0);
+        a.gamma = Scalar<T>::make(t.last ? P.gamma * (t.horner ? t.gnext : 1.0) : 1.0);
         a.base_scale = Scalar<T>::make(t.base_scale);
         a.base_mode = t.base_mode;
         a.last = t.last;
+        a.horner = t.horner;
         a.yacc = yacc;
         a.u = (t.last && k == s - 1 && !rec) ? u : nullptr;
         a.zout = t.last ? nullptr : (rec ? rec->z(k, j + 1) : B.Z[zi]);
@@ -673,12 +700,13 @@ et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, cons
         a.ybar_next = ynext;
         a.gamma = Scalar<T>::make(P.gamma);
         // coefficient of the forward input in the sub-step sum
+        // (Horner steps: the input enters the result only through the polynomial)
         double gin;
-        if (into_b) gin = t.base_scale;
+        if (t.horner) gin = 0.0;
         else if (into_y) gin = 1.0;
         else gin = P.terms[idx - 1].gnext;
         a.g = Scalar<T>::make(gin);
-        a.f = Scalar<T>::make(t.zscale_on ? P.inv_nu : 1.0);
+        a.f = Scalar<T>::make(t.zscale_on ? t.zscale_val : 1.0);
         a.inv_nu = Scalar<T>::make(P.inv_nu);
         a.x = into_b ? B.b : (into_y ? rec.y(k) : rec.z(k, j));
         a.has_beta = t.beta != 0.0;

@@ -105,8 +105,8 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
     float2* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
     const float2 zero = make_float2(0.f, 0.f);
-    const bool need_b = a.has_beta || a.base_mode == 1;
-    const bool need_y = a.base_mode == 0;
+    const bool need_b = a.has_beta || (!a.horner && a.base_mode == 1);
+    const bool need_y = !a.horner && a.base_mode == 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x;
         const int rest = t / tiles_x;
@@ -163,18 +163,28 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
                 acc = df_mul(a.zscale, dot_result(A));
                 if (a.has_beta) acc = df_fma(a.beta, cur.bb, acc);
             }
-            float2 base;
-            if (a.base_mode == 0) base = cur.yy;
-            else if (a.base_mode == 1) base = df_mul(a.base_scale, cur.bb);
-            else base = zc;
-            float2 sum = df_fma(a.g, acc, base);
-            if (!a.last) {
-                zout[p] = acc;
-                yacc[p] = sum;
+            if (a.horner) {
+                if (!a.last) {
+                    zout[p] = acc;
+                } else {
+                    const float2 r = df_mul(a.gamma, acc);
+                    if (u) u[p] += (double)r.x + (double)r.y;
+                    else yacc[p] = r;
+                }
             } else {
-                sum = df_mul(a.gamma, sum);
-                if (u) u[p] += (double)sum.x + (double)sum.y;
-                else yacc[p] = sum;
+                float2 base;
+                if (a.base_mode == 0) base = cur.yy;
+                else if (a.base_mode == 1) base = df_mul(a.base_scale, cur.bb);
+                else base = zc;
+                float2 sum = df_fma(a.g, acc, base);
+                if (!a.last) {
+                    zout[p] = acc;
+                    yacc[p] = sum;
+                } else {
+                    sum = df_mul(a.gamma, sum);
+                    if (u) u[p] += (double)sum.x + (double)sum.y;
+                    else yacc[p] = sum;
+                }
             }
             zm = zc;
             zc = cur.zp;

@@ -96,6 +96,7 @@ struct TermArgs {
     T g;             // weight of z_{j+1} in the sub-step sum
     T gamma;         // e^{mu h}, applied on the last term (1 otherwise)
     int last;        // last term of the sub-step
+    int horner;      // Horner step of sub-step 0: output acc itself (no running sum)
     T* yacc;         // sub-step sum (read when base_mode == 0, written unless finishing)
     double* u;       // non-null on the last term of the step: u += gamma * sum
 };

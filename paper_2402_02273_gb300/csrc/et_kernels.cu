@@ -238,18 +238,24 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
                 if (a.has_zscale) acc *= a.zscale;  // only the normalised (FP32) chain scales
             }
             if (a.has_beta) acc = fma(a.beta, bv[p], acc);
-            T base;
-            if (a.base_mode == 0) base = yacc[p];
-            else if (a.base_mode == 1) base = a.base_scale * bv[p];
-            else base = zc;
-            T sum = fma(a.g, acc, base);
-            if (!a.last) {
-                zout[p] = acc;
-                yacc[p] = sum;
-            } else if (u) {
-                u[p] += (double)(sum * a.gamma);
+            if (a.horner) {
+                if (!a.last) zout[p] = acc;
+                else if (u) u[p] += (double)(acc * a.gamma);
+                else yacc[p] = acc * a.gamma;
             } else {
-                yacc[p] = sum * a.gamma;
+                T base;
+                if (a.base_mode == 0) base = yacc[p];
+                else if (a.base_mode == 1) base = a.base_scale * bv[p];
+                else base = zc;
+                T sum = fma(a.g, acc, base);
+                if (!a.last) {
+                    zout[p] = acc;
+                    yacc[p] = sum;
+                } else if (u) {
+                    u[p] += (double)(sum * a.gamma);
+                } else {
+                    yacc[p] = sum * a.gamma;
+                }
             }
             zm = zc;
             zc = zp;
@@ -279,6 +285,13 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
     acc = fma(W.w[2][p], (k + 1 < G.nz) ? z[p + G.sz] : 0.0, acc);
     acc = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? z[p - G.sz] : 0.0, acc);
     if (a.has_beta) acc = fma(a.beta, a.b[p], acc);
+    if (a.horner) {
+        // sub-step 0 by Horner's rule: no running sum to read or write
+        if (!a.last) a.zout[p] = acc;
+        else if (a.u) a.u[p] += acc * a.gamma;
+        else a.yacc[p] = acc * a.gamma;
+        return;
+    }
     double base;
     if (a.base_mode == 0) base = a.yacc[p];
     else if (a.base_mode == 1) base = a.base_scale * a.b[p];

@@ -199,6 +199,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             a.has_beta = (ak * pw) != 0.0;
             a.zscale = 1.0;
             a.has_zscale = 0;
+            a.horner = 0;
             a.dt = dt;
             const double gnext = gj * hs / (j + 1);
             a.g = gnext;

@@ -57,6 +57,7 @@ TERM_TRAFFIC = {"f64": 107.5e6, "df64": 107.9e6, "f32": 50.4e6}
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
+BATCH_COUNT = 64  # the many-patient workload: 64 grids of {96..160}^3, 100 steps each
 
 
 def parse():
@@ -70,6 +71,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint form")
     ap.add_argument("--no-forms", action="store_true", help="time the plain FP64 form only")
+    ap.add_argument("--no-batch", action="store_true", help="skip timing the batched many-grid form")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
+    ap.add_argument("--batch-runs", type=int, default=1, help="timed runs of the batched form (one warm-up run)")
+    ap.add_argument("--batch-forms", default="f64,df64,f32")
     ap.add_argument("--forms", default="f64,df64,f32",
                     help="comma-separated precision forms to time (the first one is the headline)")
     return ap.parse_args()
@@ -355,6 +360,74 @@ def main():
             del g
             torch.cuda.empty_cache()
 
+    # batched form: BATCH_COUNT uneven grids (phantom.batch_case, seeds 1000 + i,
+    # offset per rank) in one CUDA graph of batched launches, 100 steps; one
+    # warm-up run (autotune + graph capture), then --batch-runs timed runs
+    batch = {}
+    if not args.no_batch and not args.no_forms:
+        cases = [phantom.batch_case(i, base_seed=1000 + rank * args.batch_count) for i in range(args.batch_count)]
+        shapes = [c["D"].shape for c in cases]
+        rhos = [c["rho"] for c in cases]
+        Dcat = torch.from_numpy(np.concatenate([c["D"].ravel() for c in cases])).to("cuda")
+        ucat0 = torch.from_numpy(np.concatenate([c["u0"].ravel() for c in cases])).to("cuda")
+        nb = int(Dcat.numel())
+        del cases
+        for prec in [f for f in args.batch_forms.split(",") if f]:
+            B = et.Batch(shapes, precision=prec, stream=stream)
+            t0 = time.perf_counter()
+            B.set_coeffs(Dcat, rhos)
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            variant, tune_us = B.autotune(TAU)
+            s_list, m_list = B.schedule(TAU)
+            u = torch.empty_like(ucat0)
+
+            def batch_step():
+                u.copy_(ucat0)
+                B.run(u, TAU, args.nsteps)
+
+            with torch.cuda.stream(stream):
+                batch_step()
+            B.sync_info()
+            torch.cuda.synchronize()
+            ksave = args.steps
+            args.steps = args.batch_runs
+            ms, clocks = timed(batch_step)
+            args.steps = ksave
+            recs = B.sync_info()
+            sizes = [int(np.prod(sh)) for sh in shapes]
+            # algorithmic bytes of the term launches over the whole run, per
+            # grid (m-1 Horner terms, (s-1) m later terms per step)
+            term_bytes = sum(n_i * (HORNER_BYTES[prec] * (m_i - 1) + TERM_BYTES[prec] * (s_i - 1) * m_i)
+                             for n_i, s_i, m_i in zip(sizes, s_list, m_list)) * args.nsteps
+            gbs = term_bytes / (ms * 1e-3) / 1e9
+            # the autotuner's timing of the chosen variant on the first term
+            # launch (a Horner term of every grid), cold L2 between repeats not
+            # enforced: the launch streams ~4-8 GB, far above L2
+            t_us = tune_us[variant]
+            if prec == "f64":
+                ach = HORNER_FLOPS[prec] * nb / (t_us * 1e-6) / 1e12
+                broof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": ach / fp64_peak}
+            else:
+                ach = HORNER_BYTES[prec] * nb / (t_us * 1e-6) / 1e9
+                broof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+            broof.update({"kernel": "batched term (first launch, all grids)", "avg_launch_us": t_us,
+                          "traffic": None})
+            batch[prec] = {"value": whole_job_rate(world, nb, args.nsteps, ms), "unit": UNIT,
+                           "ms_per_run": ms, "voxels": nb, "grids": len(shapes), "steps": args.nsteps,
+                           "setup_ms": setup_ms, "variant": variant, "autotune_us": tune_us,
+                           "s_range": [min(s_list), max(s_list)], "m_range": [min(m_list), max(m_list)],
+                           "roofline": broof, "term_gbs_whole_run": gbs, "term_hbm_frac_whole_run": gbs / hbm_peak,
+                           # per step: residual, max(s m) - 1 term launches, stats
+                           "launches_per_run": args.nsteps * (max(si * mi for si, mi in zip(s_list, m_list)) + 1),
+                           "max_final_umax": max(r["umax"] for r in recs),
+                           "timed_runs": args.batch_runs, "warmup_runs": 1, "clocks": clocks}
+            B.close()
+            del B, u
+            torch.cuda.empty_cache()
+        del Dcat, ucat0
+        torch.cuda.empty_cache()
+
     # end to end through the public API with host buffers (pinned): H2D of D and
     # u0, coefficient setup, the 100-step run, D2H of u and of the last record
     e2e = None
@@ -404,6 +477,7 @@ def main():
             "cpu_baseline": base,
             "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
             "adjoint": adjoint,
+            "batch": batch,
             "forms": {p: {"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
                           "dtype": p, "s": results[p]["info"]["s"], "m": results[p]["info"]["m"],
                           "roofline": results[p]["roofline"], "clocks": results[p]["clocks"]}

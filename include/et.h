@@ -218,6 +218,39 @@ ET_API et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, in
                         const double* ubar_final, double* ubar0, double* grad_rho, double* grad_dscale,
                         void* workspace, size_t workspace_bytes);
 
+/* ---- Batched form: many grids (patients, scenarios) advanced together ----
+ * Grids of different sizes, each with its own D, rho and (s, m) schedule, share
+ * one workspace with their fields concatenated in grid order.  Each step is one
+ * batched residual launch, one batched launch per Taylor-term index (covering
+ * every grid whose chain has that term) and one batched stats launch; a run is
+ * captured as one CUDA graph.  The term-launch kernel variant (planes per tile,
+ * looping or one-tile-per-block grids) is picked by timing the candidates on
+ * the batch (et_batch_autotune, or automatically on the first run).
+ *  dims: host array of 3*count ints (nx, ny, nz of grid i at 3i); count <= 1024.
+ *  D, u: device, the grids' fields concatenated in order (sum of n_i FP64).
+ *  rho: host array of count rates.  info: device array of nsteps*count records
+ *  (record of grid i after step t at t*count + i), or NULL. */
+typedef struct et_batch et_batch;
+ET_API size_t et_batch_workspace_bytes(int count, const int* dims, et_precision precision);
+ET_API et_status et_batch_create(int count, const int* dims, double h, et_precision precision, void* workspace,
+                                 size_t workspace_bytes, void* cuda_stream, et_batch** out);
+ET_API et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, et_operator op,
+                                     et_scheme scheme, const et_options* options);
+ET_API et_status et_batch_run(et_batch* b, double* u, double tau, int nsteps, et_step_info* info);
+/* Times every kernel variant on one term launch of this batch and keeps the
+ * fastest; us_per_variant (host, et_batch_variant_count entries) may be NULL. */
+ET_API et_status et_batch_autotune(et_batch* b, double tau, int* variant, double* us_per_variant);
+ET_API int et_batch_variant_count(et_precision precision);
+/* Uses kernel variant `variant` (0 .. et_batch_variant_count - 1) instead of the
+ * autotuner's choice until the next et_batch_set_coeffs or et_batch_autotune. */
+ET_API et_status et_batch_set_variant(et_batch* b, int variant);
+/* Synchronises; copies the latest record of every grid (count records). */
+ET_API et_status et_batch_sync_info(et_batch* b, et_step_info* host_out);
+ET_API et_status et_batch_get_schedule(const et_batch* b, double tau, int* s, int* m);
+ET_API et_status et_batch_set_stream(et_batch* b, void* cuda_stream);
+ET_API const char* et_batch_last_error(const et_batch* b);
+ET_API void et_batch_destroy(et_batch* b);
+
 /* One step that allocates nothing (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory at call time, e.g. code inside a
  * framework whose pool owns all device memory, or code run while a memory

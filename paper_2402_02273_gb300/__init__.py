@@ -78,6 +78,18 @@ _SIGS = {
     "et_destroy": ([_VP], None),
     "et_vjp_workspace_bytes": ([_VP, _D, _I, _I], ctypes.c_size_t),
     "et_vjp": ([_VP, _VP, _D, _I, _I, _VP, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP, ctypes.c_size_t], _I),
+    "et_batch_workspace_bytes": ([_I, _VP, _I], ctypes.c_size_t),
+    "et_batch_create": ([_I, _VP, _D, _I, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], _I),
+    "et_batch_set_coeffs": ([_VP, _VP, _VP, _I, _I, ctypes.POINTER(et_options)], _I),
+    "et_batch_run": ([_VP, _VP, _D, _I, _VP], _I),
+    "et_batch_autotune": ([_VP, _D, ctypes.POINTER(_I), _VP], _I),
+    "et_batch_variant_count": ([_I], _I),
+    "et_batch_set_variant": ([_VP, _I], _I),
+    "et_batch_sync_info": ([_VP, _VP], _I),
+    "et_batch_get_schedule": ([_VP, _D, _VP, _VP], _I),
+    "et_batch_set_stream": ([_VP, _VP], _I),
+    "et_batch_last_error": ([_VP], ctypes.c_char_p),
+    "et_batch_destroy": ([_VP], None),
     "et_step_static": ([_I, _I, _I, _D, _VP, _D, _I, _I, _VP, _D, _VP, ctypes.c_char_p, ctypes.c_size_t], _I),
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
@@ -301,6 +313,105 @@ def probe_alu(stream=None):
     f64, f32 = _D(), _D()
     _check(lib.et_probe_alu(buf.data_ptr(), nbytes, st.cuda_stream, ctypes.byref(f64), ctypes.byref(f32)))
     return f64.value, f32.value
+
+
+class Batch:
+    """Many grids of different sizes advanced together (the et_batch_* ABI).
+
+    shapes: list of (nz, ny, nx); fields (D, u) are the grids' arrays flattened
+    and concatenated in order (float64 CUDA tensors of sum(n_i) values).
+    """
+
+    def __init__(self, shapes, h=1.0, precision="f64", stream=None, device=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load()
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.count = len(self.shapes)
+        dims = []
+        for nz, ny, nx in self.shapes:
+            dims += [nx, ny, nz]
+        self._dims = (ctypes.c_int * len(dims))(*dims)
+        self.sizes = [nx * ny * nz for nz, ny, nx in self.shapes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = self.lib.et_batch_workspace_bytes(self.count, self._dims, PRECISIONS[precision])
+        if nbytes == 0:
+            raise EtError(ET_ERR_ARG, "invalid batch")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            ws = (self.workspace.data_ptr() + 255) // 256 * 256
+            handle = _VP()
+            rc = self.lib.et_batch_create(self.count, self._dims, float(h), PRECISIONS[precision], ws, nbytes,
+                                          self.stream.cuda_stream, ctypes.byref(handle))
+            if rc != ET_OK:
+                raise EtError(rc, self.lib.et_batch_last_error(None).decode())
+        self.handle = handle
+
+    def _chk(self, rc):
+        if rc != ET_OK:
+            raise EtError(rc, self.lib.et_batch_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.et_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, t, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float64 \
+                or not t.is_contiguous() or t.numel() != self.n:
+            raise EtError(ET_ERR_ARG, f"{name} must be a contiguous float64 tensor of {self.n} values")
+        return t.data_ptr()
+
+    def set_coeffs(self, D, rho, op="conservative", scheme="rosenbrock", **opts):
+        r = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (self.count,)))
+        self._rho = r
+        o = make_options(**opts)
+        self._chk(self.lib.et_batch_set_coeffs(self.handle, self._dev(D, "D"), r.ctypes.data, OPS[op],
+                                               SCHEMES[scheme], ctypes.byref(o)))
+
+    def run(self, u, tau, nsteps, info=None):
+        self._chk(self.lib.et_batch_run(self.handle, self._dev(u, "u"), float(tau), int(nsteps),
+                                        None if info is None else info.data_ptr()))
+
+    def info_buffer(self, nsteps):
+        return self._torch.zeros(40 * int(nsteps) * self.count, dtype=self._torch.uint8, device=self.device)
+
+    def autotune(self, tau):
+        nv = self.lib.et_batch_variant_count(PRECISIONS[self.precision])
+        us = (ctypes.c_double * nv)()
+        v = _I()
+        self._chk(self.lib.et_batch_autotune(self.handle, float(tau), ctypes.byref(v), us))
+        return v.value, list(us)
+
+    def set_variant(self, v):
+        self._chk(self.lib.et_batch_set_variant(self.handle, int(v)))
+
+    def sync_info(self):
+        recs = (et_step_info * self.count)()
+        self._chk(self.lib.et_batch_sync_info(self.handle, recs))
+        return [_rec_dict(r) for r in recs]
+
+    def schedule(self, tau):
+        s = (ctypes.c_int * self.count)()
+        m = (ctypes.c_int * self.count)()
+        self._chk(self.lib.et_batch_get_schedule(self.handle, float(tau), s, m))
+        return list(s), list(m)
+
+    def split(self, t):
+        """Views of a concatenated tensor, one per grid, shaped (nz, ny, nx)."""
+        return [t[self.offsets[i]:self.offsets[i + 1]].view(self.shapes[i]) for i in range(self.count)]
 
 
 def _rec_dict(rec):

@@ -1,0 +1,682 @@
+// Batched form of the C ABI (include/et.h, et_batch_*): many grids of
+// different sizes, each with its own diffusion field, proliferation rate and
+// (s, m) schedule, advanced together.  Every step is one batched residual
+// launch, one batched launch per Taylor-term index (covering every grid that
+// has that term) and one batched stats launch; the whole run is captured as
+// one CUDA graph.  The kernel variant of the term launches (planes per tile,
+// looping blocks or one tile per block) is chosen by timing the candidates on
+// the batch itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "et.h"
+#include "et_internal.h"
+#include "et_plan.h"
+
+using namespace et;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxBatch = 1024;
+constexpr int kMaxTermLaunches = 1024;  // per step
+thread_local char g_batch_error[512] = "";
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
+// flags, per-grid rmax bits, tickets and step counters, per-grid step records
+size_t misc_bytes(int count) { return 128ull * count + 1024; }
+
+size_t desc_bytes_per_instance(et_precision prec) {
+    const size_t term = prec == ET_F64 ? sizeof(BatchTerm<double>)
+                                       : (prec == ET_F32 ? sizeof(BatchTerm<float>) : sizeof(BatchTerm<float2>));
+    const size_t res = prec == ET_F64 ? sizeof(BatchResidual<double>)
+                                      : (prec == ET_F32 ? sizeof(BatchResidual<float>) : sizeof(BatchResidual<float2>));
+    return (size_t)kMaxTermLaunches * term + res + sizeof(BatchStats);
+}
+
+struct BatchLayout {
+    size_t w[5], wt[5], vec[6], stage, partial, desc, tune_desc, misc;
+    size_t total;
+    long long ntot;
+};
+
+bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L, std::vector<long long>* offs) {
+    if (count < 1 || count > kMaxBatch || !dims) return false;
+    long long ntot = 0;
+    offs->assign(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+        if (nx <= 0 || ny <= 0 || nz <= 0) return false;
+        const long long n = (long long)nx * ny * nz;
+        (*offs)[i] = ntot;
+        ntot += n;
+    }
+    (*offs)[count] = ntot;
+    if (ntot >= (1ll << 40)) return false;
+    L->ntot = ntot;
+    const size_t vb = value_bytes(prec);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * ntot);
+    for (int a = 0; a < 5; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * ntot) : SIZE_MAX;
+    for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * ntot);
+    L->stage = take(8ull * ntot);
+    L->partial = take(3ull * 8ull * kStatsBlocks * count);
+    L->desc = take(desc_bytes_per_instance(prec) * count);
+    L->tune_desc = take(desc_bytes_per_instance(prec) / kMaxTermLaunches * count + 256);
+    L->misc = take(misc_bytes(count));
+    L->total = off;
+    return true;
+}
+
+struct Sched {
+    int s = 0, m = 0;
+    double mu = 0.0, theta = 0.0;
+};
+
+}  // namespace
+
+struct et_batch {
+    int count;
+    std::vector<int> dims;
+    std::vector<long long> offs;
+    long long ntot;
+    double h;
+    et_precision prec;
+    int device, sms;
+    char* ws;
+    size_t ws_bytes;
+    BatchLayout L;
+    cudaStream_t stream, capture;
+    // model
+    bool coeffs_set;
+    et_operator op;
+    et_scheme scheme;
+    std::vector<double> rho, rmax, nu;
+    et_options opt;
+    bool opt_set;
+    // tables and graph
+    double table_tau;
+    int table_variant;
+    int nlaunch;                         // term launches per step
+    std::vector<long long> launch_tiles; // tiles per term launch
+    std::vector<int> launch_count;       // descriptors per term launch
+    long long res_tiles;
+    double graph_tau;
+    int graph_steps;
+    double* graph_u;
+    et_step_info* graph_info;
+    int graph_variant;
+    cudaGraphExec_t exec;
+    int variant;  // autotuned kernel variant (-1: not tuned yet)
+    char err[512];
+};
+
+namespace {
+
+et_status bfail(et_batch* b, et_status st, const char* fmt, ...) {
+    char* dst = b ? b->err : g_batch_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define BT_CUDA(b, call)                                                                        \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return bfail((b), ET_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+struct BDeviceGuard {
+    int prev = -1;
+    explicit BDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~BDeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+Geom geom_of(const et_batch* b, int i) {
+    Geom G;
+    G.nx = b->dims[3 * i];
+    G.ny = b->dims[3 * i + 1];
+    G.nz = b->dims[3 * i + 2];
+    G.n = (long long)G.nx * G.ny * G.nz;
+    G.sy = G.nx;
+    G.sz = (long long)G.nx * G.ny;
+    G.nblocks = (unsigned)(((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) * G.nz);
+    G.sms = b->sms;
+    return G;
+}
+
+long long tiles_of(const Geom& G, int tz) {
+    return (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) * ((G.nz + tz - 1) / tz);
+}
+
+char* misc(et_batch* b) { return b->ws + b->L.misc; }
+unsigned* flags_of(et_batch* b) { return (unsigned*)(misc(b) + 0); }
+unsigned long long* rmax_bits_of(et_batch* b, int i) { return (unsigned long long*)(misc(b) + 64 + 8ull * i); }
+unsigned* ticket_of(et_batch* b, int i) { return (unsigned*)(misc(b) + 64 + 8ull * b->count + 8ull * i); }
+unsigned* counter_of(et_batch* b, int i) { return ticket_of(b, i) + 1; }
+et_step_info* slot_of(et_batch* b, int i) {
+    return (et_step_info*)(misc(b) + align_up(64 + 16ull * b->count) + 64ull * i);
+}
+
+template <typename T>
+T* field(et_batch* b, size_t region, int i) {
+    return (T*)(b->ws + region) + b->offs[i];
+}
+
+et_status sched_of(const et_batch* b, int i, double tau, Sched* S) {
+    const et_status rc = et_select_schedule(tau, b->rmax[i], b->rho[i], b->scheme, b->prec,
+                                            b->opt_set ? &b->opt : nullptr, &S->s, &S->m, &S->mu, &S->theta);
+    return rc;
+}
+
+template <typename T>
+Weights<T> typed_weights(et_batch* b, int i) {
+    Weights<T> W;
+    for (int a = 0; a < 5; ++a)
+        W.w[a] = b->prec == ET_F64 ? (const T*)field<double>(b, b->L.w[a], i) : field<T>(b, b->L.wt[a], i);
+    return W;
+}
+
+// Host-side tables of one step: the residual descriptors, then for every term
+// index t the descriptors of the grids whose chain has a term t.  u_override
+// (non-null): the last term writes there instead of u (autotuning).
+template <typename T>
+et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vector<char>& bytes, bool tuning) {
+    const int C = b->count;
+    const int tz = batch_variant(b->prec, variant).tile_z;
+    std::vector<Sched> S(C);
+    std::vector<ChainPlan> plans(C);
+    int nl = 0;
+    for (int i = 0; i < C; ++i) {
+        if (sched_of(b, i, tau, &S[i]) != ET_OK)
+            return bfail(b, ET_ERR_ARG, "no (s, m) meets the tolerance for grid %d at tau = %g", i, tau);
+        plans[i] = plan_chain(b->prec, b->nu[i], S[i].s, S[i].m, S[i].mu, tau / S[i].s);
+        nl = std::max(nl, (int)plans[i].terms.size());
+    }
+    if (nl > kMaxTermLaunches) return bfail(b, ET_ERR_UNSUPPORTED, "more than %d terms per step", kMaxTermLaunches);
+    b->nlaunch = nl;
+    b->launch_tiles.assign(nl, 0);
+    b->launch_count.assign(nl, 0);
+    // residual descriptors
+    std::vector<BatchResidual<T>> res(C);
+    long long rt = 0;
+    for (int i = 0; i < C; ++i) {
+        BatchResidual<T>& r = res[i];
+        r.G = geom_of(b, i);
+        r.u = u + b->offs[i];
+        for (int a = 0; a < 5; ++a) r.W.w[a] = field<double>(b, b->L.w[a], i);
+        r.rho = b->rho[i];
+        r.dt_shift = (b->scheme == ET_SCHEME_ROSENBROCK ? b->rho[i] : 0.0) - S[i].mu;
+        r.dt_scale = b->prec == ET_F64 ? 1.0 : 1.0 / b->nu[i];
+        r.b = field<T>(b, b->L.vec[0], i);
+        r.dt = field<T>(b, b->L.vec[1], i);
+        r.tile_begin = rt;
+        rt += tiles_of(r.G, 1);
+    }
+    b->res_tiles = rt;
+    // term descriptors, launch by launch; each grid runs its own chain
+    std::vector<BatchTerm<T>> terms;
+    std::vector<int> zi(C, 0);
+    std::vector<const T*> zin(C, nullptr);
+    for (int t = 0; t < nl; ++t) {
+        long long tiles = 0;
+        int cnt = 0;
+        for (int i = 0; i < C; ++i) {
+            if (t >= (int)plans[i].terms.size()) continue;
+            const ChainPlan& P = plans[i];
+            const PlannedTerm& pt = P.terms[t];
+            const int k = pt.k, j = pt.j;
+            T* Y[2] = {field<T>(b, b->L.vec[2], i), field<T>(b, b->L.vec[3], i)};
+            T* Z[2] = {field<T>(b, b->L.vec[4], i), field<T>(b, b->L.vec[5], i)};
+            const T* bv = field<T>(b, b->L.vec[0], i);
+            if (k == 0 && j == 1) zin[i] = bv;
+            if (k > 0 && j == 0) zin[i] = Y[k & 1];
+            BatchTerm<T> d;
+            std::memset(&d, 0, sizeof(d));
+            d.G = geom_of(b, i);
+            d.W = typed_weights<T>(b, i);
+            TermArgs<T>& a = d.a;
+            a.zin = zin[i];
+            a.b = bv;
+            a.beta = Scalar<T>::make(pt.beta);
+            a.has_beta = pt.beta != 0.0;
+            a.zscale = Scalar<T>::make(pt.zscale_val);
+            a.has_zscale = pt.zscale_on;
+            a.dt = field<T>(b, b->L.vec[1], i);
+            a.g = Scalar<T>::make(pt.gnext);
+            a.gamma = Scalar<T>::make(pt.last ? P.gamma * (pt.horner ? pt.gnext : 1.0) : 1.0);
+            a.base_scale = Scalar<T>::make(pt.base_scale);
+            a.base_mode = pt.base_mode;
+            a.last = pt.last;
+            a.horner = pt.horner;
+            a.yacc = Y[(k + 1) & 1];
+            const bool finish = pt.last && k == S[i].s - 1;
+            a.u = finish ? (tuning ? field<double>(b, b->L.stage, i) : u + b->offs[i]) : nullptr;
+            a.zout = pt.last ? nullptr : Z[zi[i]];
+            if (!pt.last) {
+                zin[i] = a.zout;
+                zi[i] ^= 1;
+            }
+            d.tile_begin = tiles;
+            tiles += tiles_of(d.G, tz);
+            terms.push_back(d);
+            ++cnt;
+        }
+        b->launch_tiles[t] = tiles;
+        b->launch_count[t] = cnt;
+    }
+    // stats descriptors
+    std::vector<BatchStats> st(C);
+    for (int i = 0; i < C; ++i) {
+        st[i].n = geom_of(b, i).n;
+        st[i].u = u + b->offs[i];
+        StatsSink& s = st[i].sink;
+        s.partial = (double*)(b->ws + b->L.partial) + 3ull * kStatsBlocks * i;
+        s.ticket = ticket_of(b, i);
+        s.step_counter = counter_of(b, i);
+        s.flags = flags_of(b);
+        s.info = nullptr;  // set per run
+        s.info_stride = 0;
+        s.last = slot_of(b, i);
+        s.s = S[i].s;
+        s.m = S[i].m;
+    }
+    bytes.resize(sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C + sizeof(BatchTerm<T>) * terms.size());
+    char* p = bytes.data();
+    std::memcpy(p, res.data(), sizeof(BatchResidual<T>) * C);
+    p += sizeof(BatchResidual<T>) * C;
+    std::memcpy(p, st.data(), sizeof(BatchStats) * C);
+    p += sizeof(BatchStats) * C;
+    std::memcpy(p, terms.data(), sizeof(BatchTerm<T>) * terms.size());
+    return ET_OK;
+}
+
+template <typename T>
+et_status enqueue_batch_step(et_batch* b, char* dtab, cudaStream_t st) {
+    const int C = b->count;
+    const BatchResidual<T>* res = (const BatchResidual<T>*)dtab;
+    const BatchStats* sts = (const BatchStats*)(dtab + sizeof(BatchResidual<T>) * C);
+    const BatchTerm<T>* terms = (const BatchTerm<T>*)(dtab + sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C);
+    cudaError_t e = launch_batch_residual<T>(b->op, (int)b->scheme, res, C, b->res_tiles, flags_of(b), st);
+    if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched residual: %s", cudaGetErrorString(e));
+    long long off = 0;
+    for (int t = 0; t < b->nlaunch; ++t) {
+        e = launch_batch_term(b->op, b->table_variant, terms + off, b->launch_count[t], b->launch_tiles[t], b->sms, st);
+        if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched term: %s", cudaGetErrorString(e));
+        off += b->launch_count[t];
+    }
+    e = launch_batch_stats(sts, C, st);
+    if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched stats: %s", cudaGetErrorString(e));
+    return ET_OK;
+}
+
+template <typename T>
+et_status upload_tables(et_batch* b, double* u, double tau, int variant, et_step_info* info, bool tuning) {
+    std::vector<char> bytes;
+    et_status rc = build_tables<T>(b, u, tau, variant, bytes, tuning);
+    if (rc != ET_OK) return rc;
+    // the per-run info destination goes into the stats descriptors
+    BatchStats* st = (BatchStats*)(bytes.data() + sizeof(BatchResidual<T>) * b->count);
+    for (int i = 0; i < b->count; ++i) {
+        st[i].sink.info = info ? info + i : slot_of(b, i);
+        st[i].sink.info_stride = info ? b->count : 0;
+    }
+    char* dst = b->ws + b->L.desc;
+    BT_CUDA(b, cudaMemcpyAsync(dst, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, b->stream));
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));  // bytes is a pageable host vector
+    b->table_tau = tau;
+    b->table_variant = variant;
+    return ET_OK;
+}
+
+// Times one launch of the first (largest) term index for every kernel variant
+// and keeps the fastest.
+template <typename T>
+et_status autotune(et_batch* b, double tau, double* us_out) {
+    const int nv = batch_variant_count(b->prec);
+    cudaEvent_t e0, e1;
+    BT_CUDA(b, cudaEventCreate(&e0));
+    BT_CUDA(b, cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_v = 0;
+    for (int v = 0; v < nv; ++v) {
+        // tables of the first term launch only, with u redirected to the staging field
+        std::vector<char> bytes;
+        et_status rc = build_tables<T>(b, field<double>(b, b->L.stage, 0), tau, v, bytes, true);
+        if (rc != ET_OK) break;
+        const int C = b->count;
+        const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
+        const size_t n0 = sizeof(BatchTerm<T>) * b->launch_count[0];
+        char* dst = b->ws + b->L.tune_desc;
+        cudaError_t ce = cudaMemcpyAsync(dst, bytes.data() + head, n0, cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+        const BatchTerm<T>* d = (const BatchTerm<T>*)dst;
+        float ms = 0.f;
+        for (int r = 0; r < 4 && ce == cudaSuccess; ++r) {  // one warm-up launch, then three timed
+            if (r == 1) ce = cudaEventRecord(e0, b->stream);
+            if (ce == cudaSuccess)
+                ce = launch_batch_term(b->op, v, d, b->launch_count[0], b->launch_tiles[0], b->sms, b->stream);
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
+        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bfail(b, ET_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        const double us = ms * 1e3 / 3.0;
+        if (us_out) us_out[v] = us;
+        if (us < best) {
+            best = us;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->variant = best_v;
+    b->table_tau = -1.0;  // tables must be rebuilt for the chosen variant
+    return ET_OK;
+}
+
+void clear_graph(et_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+template <typename T>
+et_status run_impl(et_batch* b, double* u, double tau, int nsteps, et_step_info* info) {
+    if (b->variant < 0) {
+        et_status rc = autotune<T>(b, tau, nullptr);
+        if (rc != ET_OK) return rc;
+    }
+    const bool same = b->exec && b->graph_tau == tau && b->graph_steps == nsteps && b->graph_u == u &&
+                      b->graph_info == info && b->graph_variant == b->variant;
+    if (same) {
+        BT_CUDA(b, cudaGraphLaunch(b->exec, b->stream));
+        return ET_OK;
+    }
+    clear_graph(b);
+    et_status rc = upload_tables<T>(b, u, tau, b->variant, info, false);
+    if (rc != ET_OK) return rc;
+    BT_CUDA(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    rc = ET_OK;
+    for (int i = 0; i < b->count && rc == ET_OK; ++i)
+        if (cudaMemsetAsync(counter_of(b, i), 0, sizeof(unsigned), b->capture) != cudaSuccess) rc = ET_ERR_CUDA;
+    for (int t = 0; t < nsteps && rc == ET_OK; ++t) rc = enqueue_batch_step<T>(b, b->ws + b->L.desc, b->capture);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
+    if (rc != ET_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc == ET_ERR_CUDA ? bfail(b, rc, "capture failed") : rc;
+    }
+    if (ce != cudaSuccess) return bfail(b, ET_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return bfail(b, ET_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    b->graph_tau = tau;
+    b->graph_steps = nsteps;
+    b->graph_u = u;
+    b->graph_info = info;
+    b->graph_variant = b->variant;
+    BT_CUDA(b, cudaGraphLaunch(b->exec, b->stream));
+    return ET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t et_batch_workspace_bytes(int count, const int* dims, et_precision precision) {
+    if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64) return 0;
+    BatchLayout L;
+    std::vector<long long> offs;
+    if (!batch_layout(count, dims, precision, &L, &offs)) return 0;
+    return L.total;
+}
+
+et_status et_batch_create(int count, const int* dims, double h, et_precision precision, void* workspace,
+                          size_t workspace_bytes, void* cuda_stream, et_batch** out) {
+    if (!out) return bfail(nullptr, ET_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64)
+        return bfail(nullptr, ET_ERR_ARG, "unknown precision");
+    BatchLayout L;
+    std::vector<long long> offs;
+    if (!batch_layout(count, dims, precision, &L, &offs))
+        return bfail(nullptr, ET_ERR_ARG, "batch of %d grids is empty, too large or has an empty grid", count);
+    for (int i = 0; i < count; ++i)
+        if (dims[3 * i + 2] > 65535 || (long long)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2] >= (1ll << 31))
+            return bfail(nullptr, ET_ERR_ARG, "grid %d is too large", i);
+    if (!(h > 0.0) || !std::isfinite(h)) return bfail(nullptr, ET_ERR_ARG, "h must be finite and > 0");
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0)
+        return bfail(nullptr, ET_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < L.total)
+        return bfail(nullptr, ET_ERR_ARG, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bfail(nullptr, ET_ERR_CUDA, "device query failed");
+    et_batch* b = new (std::nothrow) et_batch();
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "out of host memory");
+    b->count = count;
+    b->dims.assign(dims, dims + 3 * count);
+    b->offs = offs;
+    b->ntot = L.ntot;
+    b->h = h;
+    b->prec = precision;
+    b->device = dev;
+    b->sms = sms;
+    b->ws = (char*)workspace;
+    b->ws_bytes = workspace_bytes;
+    b->L = L;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->coeffs_set = false;
+    b->opt_set = false;
+    std::memset(&b->opt, 0, sizeof(b->opt));
+    b->rho.assign(count, 0.0);
+    b->rmax.assign(count, 0.0);
+    b->nu.assign(count, 1.0);
+    b->table_tau = -1.0;
+    b->table_variant = -1;
+    b->nlaunch = 0;
+    b->res_tiles = 0;
+    b->graph_tau = -1.0;
+    b->graph_steps = 0;
+    b->graph_u = nullptr;
+    b->graph_info = nullptr;
+    b->graph_variant = -1;
+    b->exec = nullptr;
+    b->variant = -1;
+    b->err[0] = 0;
+    if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
+        prime_launch_limits() != cudaSuccess ||
+        cudaMemsetAsync(b->ws + L.misc, 0, misc_bytes(count), b->stream) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, ET_ERR_CUDA, "batch set-up failed");
+    }
+    *out = b;
+    return ET_OK;
+}
+
+et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, et_operator op, et_scheme scheme,
+                              const et_options* options) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (!D || ((uintptr_t)D & 7u) || !rho) return bfail(b, ET_ERR_ARG, "D (device) and rho (host) must be given");
+    if (op != ET_OP_CONSERVATIVE && op != ET_OP_LITERAL) return bfail(b, ET_ERR_ARG, "unknown operator");
+    if (scheme != ET_SCHEME_ROSENBROCK && scheme != ET_SCHEME_EXPEULER) return bfail(b, ET_ERR_ARG, "unknown scheme");
+    for (int i = 0; i < b->count; ++i)
+        if (!(rho[i] >= 0.0) || !std::isfinite(rho[i])) return bfail(b, ET_ERR_ARG, "rho[%d] must be finite and >= 0", i);
+    if (options) {
+        if (options->tol < 0 || !std::isfinite(options->tol)) return bfail(b, ET_ERR_ARG, "options.tol must be >= 0");
+        if (options->theta_max < 0 || !std::isfinite(options->theta_max))
+            return bfail(b, ET_ERR_ARG, "options.theta_max must be >= 0");
+        if (options->force_m == 1) return bfail(b, ET_ERR_ARG, "options.force_m must be 0 or >= 2");
+        if (options->force_s < 0 || options->force_m < 0) return bfail(b, ET_ERR_ARG, "forced s, m must be >= 0");
+    }
+    BDeviceGuard dg(b->device);
+    clear_graph(b);
+    b->coeffs_set = false;
+    b->table_tau = -1.0;
+    const double inv_h2 = 1.0 / (b->h * b->h);
+    BT_CUDA(b, cudaMemsetAsync(misc(b), 0, misc_bytes(b->count), b->stream));
+    for (int i = 0; i < b->count; ++i) {
+        double* w[5];
+        for (int a = 0; a < 5; ++a) w[a] = field<double>(b, b->L.w[a], i);
+        const cudaError_t e =
+            launch_coeffs(geom_of(b, i), D + b->offs[i], inv_h2, op, w, rmax_bits_of(b, i), flags_of(b), b->stream);
+        if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
+    }
+    std::vector<unsigned long long> bits(b->count);
+    unsigned flags = 0;
+    BT_CUDA(b, cudaMemcpyAsync(bits.data(), rmax_bits_of(b, 0), 8ull * b->count, cudaMemcpyDeviceToHost, b->stream));
+    BT_CUDA(b, cudaMemcpyAsync(&flags, flags_of(b), sizeof(flags), cudaMemcpyDeviceToHost, b->stream));
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    BT_CUDA(b, cudaMemsetAsync(flags_of(b), 0, sizeof(unsigned), b->stream));
+    if (flags & ET_FLAG_D_INVALID) return bfail(b, ET_ERR_NUMERIC, "D has negative or non-finite values");
+    b->op = op;
+    b->scheme = scheme;
+    b->opt_set = options != nullptr;
+    if (options) b->opt = *options;
+    const bool shift = !(options && options->shift == 0);
+    for (int i = 0; i < b->count; ++i) {
+        std::memcpy(&b->rmax[i], &bits[i], sizeof(double));
+        b->rho[i] = rho[i];
+        const double rho_c = scheme == ET_SCHEME_ROSENBROCK ? rho[i] * (1.0 + 2.0 * kRangeSlack) : 0.0;
+        const double nu = shift ? b->rmax[i] + rho_c : 2.0 * b->rmax[i] + rho_c;
+        b->nu[i] = nu > 0.0 ? nu : 1.0;
+        if (b->prec != ET_F64) {
+            const Geom G = geom_of(b, i);
+            const double* src[4];
+            for (int a = 0; a < 4; ++a) src[a] = field<double>(b, b->L.w[a], i);
+            cudaError_t e;
+            if (b->prec == ET_F32) {
+                float* dst[4];
+                for (int a = 0; a < 4; ++a) dst[a] = field<float>(b, b->L.wt[a], i);
+                e = launch_convert_weights(G, src, dst, 1.0 / b->nu[i], b->stream);
+                if (e == cudaSuccess)
+                    e = launch_cast(G.n, field<double>(b, b->L.w[4], i), 1.0 / b->nu[i], field<float>(b, b->L.wt[4], i),
+                                    b->stream);
+            } else {
+                float2* dst[4];
+                for (int a = 0; a < 4; ++a) dst[a] = field<float2>(b, b->L.wt[a], i);
+                e = launch_convert_weights(G, src, dst, 1.0 / b->nu[i], b->stream);
+            }
+            if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
+        }
+    }
+    b->coeffs_set = true;
+    b->variant = -1;
+    return ET_OK;
+}
+
+et_status et_batch_run(et_batch* b, double* u, double tau, int nsteps, et_step_info* info) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (!b->coeffs_set) return bfail(b, ET_ERR_STATE, "et_batch_set_coeffs has not been called");
+    if (!u || ((uintptr_t)u & 7u)) return bfail(b, ET_ERR_ARG, "u must be an 8-byte aligned device pointer");
+    if (info && ((uintptr_t)info & 7u)) return bfail(b, ET_ERR_ARG, "info must be 8-byte aligned");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return bfail(b, ET_ERR_ARG, "tau must be finite and > 0");
+    if (nsteps < 1) return bfail(b, ET_ERR_ARG, "nsteps must be >= 1");
+    BDeviceGuard dg(b->device);
+    if (b->prec == ET_F64) return run_impl<double>(b, u, tau, nsteps, info);
+    if (b->prec == ET_F32) return run_impl<float>(b, u, tau, nsteps, info);
+    return run_impl<float2>(b, u, tau, nsteps, info);
+}
+
+et_status et_batch_autotune(et_batch* b, double tau, int* variant, double* us_per_variant) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (!b->coeffs_set) return bfail(b, ET_ERR_STATE, "et_batch_set_coeffs has not been called");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return bfail(b, ET_ERR_ARG, "tau must be finite and > 0");
+    BDeviceGuard dg(b->device);
+    clear_graph(b);
+    et_status rc;
+    if (b->prec == ET_F64) rc = autotune<double>(b, tau, us_per_variant);
+    else if (b->prec == ET_F32) rc = autotune<float>(b, tau, us_per_variant);
+    else rc = autotune<float2>(b, tau, us_per_variant);
+    if (rc == ET_OK && variant) *variant = b->variant;
+    return rc;
+}
+
+et_status et_batch_set_variant(et_batch* b, int variant) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (variant < 0 || variant >= batch_variant_count(b->prec)) return bfail(b, ET_ERR_ARG, "no variant %d", variant);
+    BDeviceGuard dg(b->device);
+    clear_graph(b);
+    b->variant = variant;
+    b->table_tau = -1.0;
+    return ET_OK;
+}
+
+int et_batch_variant_count(et_precision precision) {
+    if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64) return 0;
+    return batch_variant_count(precision);
+}
+
+et_status et_batch_sync_info(et_batch* b, et_step_info* host_out) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    BDeviceGuard dg(b->device);
+    std::vector<et_step_info> rec(b->count);
+    unsigned flags = 0;
+    for (int i = 0; i < b->count; ++i)
+        BT_CUDA(b, cudaMemcpyAsync(&rec[i], slot_of(b, i), sizeof(et_step_info), cudaMemcpyDeviceToHost, b->stream));
+    BT_CUDA(b, cudaMemcpyAsync(&flags, flags_of(b), sizeof(flags), cudaMemcpyDeviceToHost, b->stream));
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    BT_CUDA(b, cudaMemsetAsync(flags_of(b), 0, sizeof(unsigned), b->stream));
+    if (host_out) std::memcpy(host_out, rec.data(), sizeof(et_step_info) * b->count);
+    if (flags & ET_FLAG_NONFINITE) return bfail(b, ET_ERR_NUMERIC, "non-finite density met");
+    if (flags & ET_FLAG_RANGE_IN) return bfail(b, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3)");
+    return ET_OK;
+}
+
+et_status et_batch_get_schedule(const et_batch* b, double tau, int* s, int* m) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (!b->coeffs_set) return bfail(const_cast<et_batch*>(b), ET_ERR_STATE, "et_batch_set_coeffs has not been called");
+    for (int i = 0; i < b->count; ++i) {
+        Sched S;
+        if (sched_of(b, i, tau, &S) != ET_OK) return bfail(const_cast<et_batch*>(b), ET_ERR_ARG, "no (s, m) for grid %d", i);
+        if (s) s[i] = S.s;
+        if (m) m[i] = S.m;
+    }
+    return ET_OK;
+}
+
+et_status et_batch_set_stream(et_batch* b, void* cuda_stream) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    b->stream = (cudaStream_t)cuda_stream;
+    return ET_OK;
+}
+
+const char* et_batch_last_error(const et_batch* b) { return b ? b->err : g_batch_error; }
+
+void et_batch_destroy(et_batch* b) {
+    if (!b) return;
+    {
+        BDeviceGuard dg(b->device);
+        clear_graph(b);
+        if (b->capture) cudaStreamDestroy(b->capture);
+    }
+    delete b;
+}
+
+}  // extern "C"

@@ -81,17 +81,13 @@ struct PlaneDF {
     float2 dt, wxp, wxm, wyp, wym, zxp, zxm, zyp, zym, zp, wzp, bb, yy, w3;
 };
 
-// Same tiling and recurrence as term_kernel in et_kernels.cu, in pair
-// arithmetic.  The z-march is software-pipelined: the loads of plane k+1 are
-// issued before plane k is computed, so each thread keeps a whole plane of
-// loads in flight while the FP32 pipes work.
-template <int OP>
-__global__ void __launch_bounds__(kThreads, 3)
-term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
-    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
-    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
-    const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
-    const int ntiles = tiles_x * tiles_y * tiles_z;
+// One (i, j) column of kTileZ planes of a term in pair arithmetic.  The z-march
+// is software-pipelined: the loads of plane k+1 are issued before plane k is
+// computed, so each thread keeps a whole plane of loads in flight while the
+// FP32 pipes work.
+template <int OP, int TZ>
+__device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<float2>& W,
+                                                 const TermArgs<float2>& a, int i, int j, int tz) {
     // restrict-qualified locals: the stores of one plane do not alias the loads of
     // the next, so those loads may be issued before the stores
     const float2* __restrict__ z = a.zin;
@@ -107,6 +103,96 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
     const float2 zero = make_float2(0.f, 0.f);
     const bool need_b = a.has_beta || (!a.horner && a.base_mode == 1);
     const bool need_y = !a.horner && a.base_mode == 0;
+    const bool xp = i + 1 < G.nx, xm = i > 0, yp = j + 1 < G.ny, ym = j > 0;
+    const int k0 = tz * TZ;
+    const int k1 = min(k0 + TZ, G.nz);
+    auto load = [&](PlaneDF& L, long long q, int k) {
+        L.dt = dtv[q];
+        L.wxp = w0[q];
+        L.wyp = w1[q];
+        L.wzp = w2[q];
+        L.w3 = (OP == ET_OP_LITERAL) ? w3[q] : zero;
+        L.wxm = (OP == ET_OP_CONSERVATIVE && xm) ? w0[q - 1] : zero;
+        L.wym = (OP == ET_OP_CONSERVATIVE && ym) ? w1[q - G.sy] : zero;
+        L.zxp = xp ? z[q + 1] : zero;
+        L.zxm = xm ? z[q - 1] : zero;
+        L.zyp = yp ? z[q + G.sy] : zero;
+        L.zym = ym ? z[q - G.sy] : zero;
+        L.zp = (k + 1 < G.nz) ? z[q + G.sz] : zero;
+        L.bb = need_b ? bv[q] : zero;
+        L.yy = need_y ? yacc[q] : zero;
+    };
+    long long p = i + G.sy * j + G.sz * k0;
+    float2 zm = (k0 > 0) ? z[p - G.sz] : zero;
+    float2 wzm_c = (OP == ET_OP_CONSERVATIVE && k0 > 0) ? w2[p - G.sz] : zero;
+    float2 zc = z[p];
+    PlaneDF cur;
+    load(cur, p, k0);
+    for (int k = k0; k < k1; ++k, p += G.sz) {
+        PlaneDF nxt;
+        if (k + 1 < k1) load(nxt, p + G.sz, k + 1);
+        // literal: the -e weight of every axis is w3[p] (0 on the near wall)
+        const float2 wxm = (OP == ET_OP_CONSERVATIVE) ? cur.wxm : (xm ? cur.w3 : zero);
+        const float2 wym = (OP == ET_OP_CONSERVATIVE) ? cur.wym : (ym ? cur.w3 : zero);
+        const float2 wzm = (OP == ET_OP_CONSERVATIVE) ? wzm_c : ((k > 0) ? cur.w3 : zero);
+        DotAcc A;
+        dot_first(A, cur.dt, zc);
+        dot_add(A, cur.wxp, cur.zxp);
+        dot_add(A, wxm, cur.zxm);
+        dot_add(A, cur.wyp, cur.zyp);
+        dot_add(A, wym, cur.zym);
+        dot_add(A, cur.wzp, cur.zp);
+        dot_add(A, wzm, zm);
+        float2 acc;
+        if (!a.has_zscale) {
+            if (a.has_beta) dot_add(A, a.beta, cur.bb);
+            acc = dot_result(A);
+        } else {
+            acc = df_mul(a.zscale, dot_result(A));
+            if (a.has_beta) acc = df_fma(a.beta, cur.bb, acc);
+        }
+        if (a.horner) {
+            if (!a.last) {
+                zout[p] = acc;
+            } else {
+                const float2 r = df_mul(a.gamma, acc);
+                if (u) u[p] += (double)r.x + (double)r.y;
+                else yacc[p] = r;
+            }
+        } else {
+            float2 base;
+            if (a.base_mode == 0) base = cur.yy;
+            else if (a.base_mode == 1) base = df_mul(a.base_scale, cur.bb);
+            else base = zc;
+            float2 sum = df_fma(a.g, acc, base);
+            if (!a.last) {
+                zout[p] = acc;
+                yacc[p] = sum;
+            } else {
+                sum = df_mul(a.gamma, sum);
+                if (u) u[p] += (double)sum.x + (double)sum.y;
+                else yacc[p] = sum;
+            }
+        }
+        zm = zc;
+        zc = cur.zp;
+        wzm_c = cur.wzp;
+        cur = nxt;
+    }
+}
+
+// Same tiling and recurrence as term_kernel in et_kernels.cu, in pair arithmetic.
+// The parameters are __grid_constant__: the column code takes them by
+// reference, which otherwise makes a local copy (32-64 B of stack at 80
+// registers).
+template <int OP>
+__global__ void __launch_bounds__(kThreads, 3)
+term_kernel_df64(const __grid_constant__ Geom G, const __grid_constant__ Weights<float2> W,
+                 const __grid_constant__ TermArgs<float2> a) {
+    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
+    const int tiles_z = (G.nz + kTileZ - 1) / kTileZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x;
         const int rest = t / tiles_x;
@@ -115,83 +201,59 @@ term_kernel_df64(Geom G, Weights<float2> W, TermArgs<float2> a) {
         const int i = tx * kBlockX + threadIdx.x;
         const int j = ty * kBlockY + threadIdx.y;
         if (i >= G.nx || j >= G.ny) continue;
-        const int k0 = tz * kTileZ;
-        const int k1 = min(k0 + kTileZ, G.nz);
-        const bool xp = i + 1 < G.nx, xm = i > 0, yp = j + 1 < G.ny, ym = j > 0;
-        auto load = [&](PlaneDF& L, long long q, int k) {
-            L.dt = dtv[q];
-            L.wxp = w0[q];
-            L.wyp = w1[q];
-            L.wzp = w2[q];
-            L.w3 = (OP == ET_OP_LITERAL) ? w3[q] : zero;
-            L.wxm = (OP == ET_OP_CONSERVATIVE && xm) ? w0[q - 1] : zero;
-            L.wym = (OP == ET_OP_CONSERVATIVE && ym) ? w1[q - G.sy] : zero;
-            L.zxp = xp ? z[q + 1] : zero;
-            L.zxm = xm ? z[q - 1] : zero;
-            L.zyp = yp ? z[q + G.sy] : zero;
-            L.zym = ym ? z[q - G.sy] : zero;
-            L.zp = (k + 1 < G.nz) ? z[q + G.sz] : zero;
-            L.bb = need_b ? bv[q] : zero;
-            L.yy = need_y ? yacc[q] : zero;
-        };
-        long long p = i + G.sy * j + G.sz * k0;
-        float2 zm = (k0 > 0) ? z[p - G.sz] : zero;
-        float2 wzm_c = (OP == ET_OP_CONSERVATIVE && k0 > 0) ? w2[p - G.sz] : zero;
-        float2 zc = z[p];
-        PlaneDF cur;
-        load(cur, p, k0);
-        for (int k = k0; k < k1; ++k, p += G.sz) {
-            PlaneDF nxt;
-            if (k + 1 < k1) load(nxt, p + G.sz, k + 1);
-            // literal: the -e weight of every axis is w3[p] (0 on the near wall)
-            const float2 wxm = (OP == ET_OP_CONSERVATIVE) ? cur.wxm : (xm ? cur.w3 : zero);
-            const float2 wym = (OP == ET_OP_CONSERVATIVE) ? cur.wym : (ym ? cur.w3 : zero);
-            const float2 wzm = (OP == ET_OP_CONSERVATIVE) ? wzm_c : ((k > 0) ? cur.w3 : zero);
-            DotAcc A;
-            dot_first(A, cur.dt, zc);
-            dot_add(A, cur.wxp, cur.zxp);
-            dot_add(A, wxm, cur.zxm);
-            dot_add(A, cur.wyp, cur.zyp);
-            dot_add(A, wym, cur.zym);
-            dot_add(A, cur.wzp, cur.zp);
-            dot_add(A, wzm, zm);
-            float2 acc;
-            if (!a.has_zscale) {
-                if (a.has_beta) dot_add(A, a.beta, cur.bb);
-                acc = dot_result(A);
-            } else {
-                acc = df_mul(a.zscale, dot_result(A));
-                if (a.has_beta) acc = df_fma(a.beta, cur.bb, acc);
-            }
-            if (a.horner) {
-                if (!a.last) {
-                    zout[p] = acc;
-                } else {
-                    const float2 r = df_mul(a.gamma, acc);
-                    if (u) u[p] += (double)r.x + (double)r.y;
-                    else yacc[p] = r;
-                }
-            } else {
-                float2 base;
-                if (a.base_mode == 0) base = cur.yy;
-                else if (a.base_mode == 1) base = df_mul(a.base_scale, cur.bb);
-                else base = zc;
-                float2 sum = df_fma(a.g, acc, base);
-                if (!a.last) {
-                    zout[p] = acc;
-                    yacc[p] = sum;
-                } else {
-                    sum = df_mul(a.gamma, sum);
-                    if (u) u[p] += (double)sum.x + (double)sum.y;
-                    else yacc[p] = sum;
-                }
-            }
-            zm = zc;
-            zc = cur.zp;
-            wzm_c = cur.wzp;
-            cur = nxt;
-        }
+        term_column_df64<OP, kTileZ>(G, W, a, i, j, tz);
     }
+}
+
+// Batched form: blocks loop over the tiles of all grids of the launch.
+template <int OP, int TZ>
+__global__ void __launch_bounds__(kThreads, 3)
+batch_term_df64_kernel(const BatchTerm<float2>* __restrict__ d, int count, long long tiles) {
+    __shared__ BatchTerm<float2> sd;
+    const int tid = threadIdx.x + kBlockX * threadIdx.y;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        __syncthreads();
+        const int* src = reinterpret_cast<const int*>(d + lo);
+        int* dst = reinterpret_cast<int*>(&sd);
+        for (int w = tid; w < (int)(sizeof(BatchTerm<float2>) / 4); w += kThreads) dst[w] = src[w];
+        __syncthreads();
+        const long long lt = tile - sd.tile_begin;
+        const int tiles_x = (sd.G.nx + kBlockX - 1) / kBlockX;
+        const int tiles_y = (sd.G.ny + kBlockY - 1) / kBlockY;
+        const int i = (int)(lt % tiles_x) * kBlockX + threadIdx.x;
+        const long long rest = lt / tiles_x;
+        const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
+        const int tz = (int)(rest / tiles_y);
+        if (i < sd.G.nx && j < sd.G.ny) term_column_df64<OP, TZ>(sd.G, sd.W, sd.a, i, j, tz);
+    }
+}
+
+template <int OP, int TZ>
+int batch_df64_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_term_df64_kernel<OP, TZ>, kThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+template <int OP, int TZ>
+cudaError_t launch_batch_df64(const BatchTerm<float2>* d, int count, long long tiles, int sms, cudaStream_t stream) {
+    const long long cap = (long long)(sms > 0 ? sms : 1) * batch_df64_blocks_per_sm<OP, TZ>();
+    batch_term_df64_kernel<OP, TZ><<<(unsigned)(tiles < cap ? tiles : cap), dim3(kBlockX, kBlockY, 1), 0, stream>>>(
+        d, count, tiles);
+    return cudaGetLastError();
 }
 
 template <int OP>
@@ -213,6 +275,16 @@ cudaError_t prime_launch_limits_df64() {
     df64_blocks_per_sm<ET_OP_CONSERVATIVE>();
     df64_blocks_per_sm<ET_OP_LITERAL>();
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_term(et_operator op, int variant, const BatchTerm<float2>* d, int count, long long tiles,
+                              int sms, cudaStream_t stream) {
+    const BatchVariant v = batch_variant(ET_DF64, variant);
+    if (op == ET_OP_CONSERVATIVE)
+        return v.tile_z == 2 ? launch_batch_df64<ET_OP_CONSERVATIVE, 2>(d, count, tiles, sms, stream)
+                             : launch_batch_df64<ET_OP_CONSERVATIVE, 4>(d, count, tiles, sms, stream);
+    return v.tile_z == 2 ? launch_batch_df64<ET_OP_LITERAL, 2>(d, count, tiles, sms, stream)
+                         : launch_batch_df64<ET_OP_LITERAL, 4>(d, count, tiles, sms, stream);
 }
 
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const TermArgs<float2>& a,

@@ -55,7 +55,7 @@ struct StatsSink {
     unsigned* step_counter; // step index within the current run
     unsigned* flags;        // ET_FLAG_* word
     et_step_info* info;     // destination base
-    int info_stride;        // 1: info[step], 0: info[0]
+    int info_stride;        // records step t at info[t * info_stride] (0: always info[0])
     et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
     int s, m;               // recorded in the info
 };
@@ -122,6 +122,54 @@ struct AdjTermArgs {
     int out_to_bbar;     // the output adds to bbar instead of zbar_out
     T* zbar_out;
 };
+
+// Batched form: one launch covers many grids.  Each grid's part of a launch is
+// a descriptor in device memory (fields already offset to the grid's slice of
+// the concatenated workspace) with the index of its first tile; blocks find
+// their grid by binary search over tile_begin.
+template <typename T>
+struct BatchTerm {
+    Geom G;
+    Weights<T> W;
+    TermArgs<T> a;
+    long long tile_begin;
+};
+
+template <typename T>
+struct BatchResidual {
+    Geom G;
+    const double* u;
+    Weights<double> W;
+    double rho, dt_shift, dt_scale;
+    T* b;
+    T* dt;
+    long long tile_begin;
+};
+
+struct BatchStats {
+    long long n;
+    const double* u;
+    StatsSink sink;
+};
+
+// Kernel variants of the batched term launch, chosen by the autotuner:
+// planes per tile and whether blocks loop over tiles.
+struct BatchVariant {
+    int tile_z;
+    int persistent;
+};
+int batch_variant_count(et_precision prec);
+BatchVariant batch_variant(et_precision prec, int v);
+
+template <typename T>
+cudaError_t launch_batch_term(et_operator op, int variant, const BatchTerm<T>* d, int count, long long tiles,
+                              int sms, cudaStream_t stream);
+cudaError_t launch_batch_term(et_operator op, int variant, const BatchTerm<float2>* d, int count, long long tiles,
+                              int sms, cudaStream_t stream);
+template <typename T>
+cudaError_t launch_batch_residual(et_operator op, int scheme, const BatchResidual<T>* d, int count, long long tiles,
+                                  unsigned* flags, cudaStream_t stream);
+cudaError_t launch_batch_stats(const BatchStats* d, int count, cudaStream_t stream);
 
 // Kernel launchers (et_kernels.cu).  All enqueue on `stream` and return the
 // launch error.

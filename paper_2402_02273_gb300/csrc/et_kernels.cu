@@ -148,13 +148,10 @@ __device__ __forceinline__ T minus_weight(const Weights<T>& W, int axis, long lo
 // L u = sum_e w_e u_e - R u_p with R from the coefficient pass: 12 FP64
 // operations per voxel; the range test on u runs on the integer bits.
 template <int OP, typename T>
-__global__ void __launch_bounds__(kThreads)
-residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double dt_shift,
-                double dt_scale, int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= G.nx || j >= G.ny) return;
+__device__ __forceinline__ void residual_point(const Geom& G, const double* __restrict__ u, const Weights<double>& W,
+                                               double rho, double dt_shift, double dt_scale, int scheme,
+                                               T* __restrict__ b, T* __restrict__ dt, unsigned* flags, int i, int j,
+                                               int k) {
     const long long p = i + G.sy * j + G.sz * k;
     const double up = u[p];
     const double negR = W.w[4][p];
@@ -182,19 +179,22 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
     }
 }
 
-// ---------------------------------------------------------------------------
-// term: z^_{j+1} = A~ z^_j + beta b;  sum = base + g z^_{j+1};
-// last term: sum *= gamma and either stored as the next y or added to u.
-// Each thread marches over kTileZ planes, carrying the z-neighbours (and, for
-// the conservative operator, the -z face weight) in registers; blocks loop over
-// tiles so the grid matches the resident-block capacity of the device.
-template <int OP, typename T, int TZ>
+template <int OP, typename T>
 __global__ void __launch_bounds__(kThreads)
-term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
-    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
-    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
-    const int tiles_z = (G.nz + TZ - 1) / TZ;
-    const int ntiles = tiles_x * tiles_y * tiles_z;
+residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double dt_shift,
+                double dt_scale, int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= G.nx || j >= G.ny) return;
+    residual_point<OP, T>(G, u, W, rho, dt_shift, dt_scale, scheme, b, dt, flags, i, j, k);
+}
+
+// One (i, j) column of TZ planes of a term, marching in z with the z-neighbours
+// (and, for the conservative operator, the -z face weight) carried in registers.
+template <int OP, typename T, int TZ>
+__device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, const TermArgs<T>& a, int i, int j,
+                                            int tz) {
     // restrict-qualified locals: the stores of one plane do not alias the loads of
     // the next, so the compiler may issue those loads early
     const T* __restrict__ z = a.zin;
@@ -207,6 +207,65 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
     T* __restrict__ zout = a.zout;
     T* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
+    const int k0 = tz * TZ;
+    const int k1 = min(k0 + TZ, G.nz);
+    long long p = i + G.sy * j + G.sz * k0;
+    T zm = (k0 > 0) ? z[p - G.sz] : T(0);
+    T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : T(0);
+    T zc = z[p];
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k, p += G.sz) {
+        const bool has_zp = k + 1 < G.nz;
+        const T zp = has_zp ? z[p + G.sz] : T(0);
+        const T wzp = w2[p];
+        T acc = dtv[p] * zc;
+        acc = fma(w0[p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
+        acc = fma((i > 0) ? (OP == ET_OP_CONSERVATIVE ? w0[p - 1] : w3[p]) : T(0), (i > 0) ? z[p - 1] : T(0), acc);
+        acc = fma(w1[p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
+        acc = fma((j > 0) ? (OP == ET_OP_CONSERVATIVE ? w1[p - G.sy] : w3[p]) : T(0), (j > 0) ? z[p - G.sy] : T(0),
+                  acc);
+        acc = fma(wzp, zp, acc);
+        acc = fma(wzm, zm, acc);
+        if constexpr (!std::is_same<T, double>::value) {
+            if (a.has_zscale) acc *= a.zscale;  // only the normalised (FP32) chain scales
+        }
+        if (a.has_beta) acc = fma(a.beta, bv[p], acc);
+        if (a.horner) {
+            if (!a.last) zout[p] = acc;
+            else if (u) u[p] += (double)(acc * a.gamma);
+            else yacc[p] = acc * a.gamma;
+        } else {
+            T base;
+            if (a.base_mode == 0) base = yacc[p];
+            else if (a.base_mode == 1) base = a.base_scale * bv[p];
+            else base = zc;
+            T sum = fma(a.g, acc, base);
+            if (!a.last) {
+                zout[p] = acc;
+                yacc[p] = sum;
+            } else if (u) {
+                u[p] += (double)(sum * a.gamma);
+            } else {
+                yacc[p] = sum * a.gamma;
+            }
+        }
+        zm = zc;
+        zc = zp;
+        wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : T(0));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// term: z^_{j+1} = A~ z^_j + beta b;  sum = base + g z^_{j+1};
+// last term: sum *= gamma and either stored as the next y or added to u.
+// Blocks loop over tiles so the grid matches the resident-block capacity.
+template <int OP, typename T, int TZ>
+__global__ void __launch_bounds__(kThreads)
+term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
+    const int tiles_x = (G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (G.ny + kBlockY - 1) / kBlockY;
+    const int tiles_z = (G.nz + TZ - 1) / TZ;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x;
         const int rest = t / tiles_x;
@@ -215,52 +274,7 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
         const int i = tx * kBlockX + threadIdx.x;
         const int j = ty * kBlockY + threadIdx.y;
         if (i >= G.nx || j >= G.ny) continue;
-        const int k0 = tz * TZ;
-        const int k1 = min(k0 + TZ, G.nz);
-        long long p = i + G.sy * j + G.sz * k0;
-        T zm = (k0 > 0) ? z[p - G.sz] : T(0);
-        T wzm = (k0 > 0) ? (OP == ET_OP_CONSERVATIVE ? w2[p - G.sz] : w3[p]) : T(0);
-        T zc = z[p];
-#pragma unroll 2
-        for (int k = k0; k < k1; ++k, p += G.sz) {
-            const bool has_zp = k + 1 < G.nz;
-            const T zp = has_zp ? z[p + G.sz] : T(0);
-            const T wzp = w2[p];
-            T acc = dtv[p] * zc;
-            acc = fma(w0[p], (i + 1 < G.nx) ? z[p + 1] : T(0), acc);
-            acc = fma((i > 0) ? (OP == ET_OP_CONSERVATIVE ? w0[p - 1] : w3[p]) : T(0), (i > 0) ? z[p - 1] : T(0), acc);
-            acc = fma(w1[p], (j + 1 < G.ny) ? z[p + G.sy] : T(0), acc);
-            acc = fma((j > 0) ? (OP == ET_OP_CONSERVATIVE ? w1[p - G.sy] : w3[p]) : T(0), (j > 0) ? z[p - G.sy] : T(0),
-                      acc);
-            acc = fma(wzp, zp, acc);
-            acc = fma(wzm, zm, acc);
-            if constexpr (!std::is_same<T, double>::value) {
-                if (a.has_zscale) acc *= a.zscale;  // only the normalised (FP32) chain scales
-            }
-            if (a.has_beta) acc = fma(a.beta, bv[p], acc);
-            if (a.horner) {
-                if (!a.last) zout[p] = acc;
-                else if (u) u[p] += (double)(acc * a.gamma);
-                else yacc[p] = acc * a.gamma;
-            } else {
-                T base;
-                if (a.base_mode == 0) base = yacc[p];
-                else if (a.base_mode == 1) base = a.base_scale * bv[p];
-                else base = zc;
-                T sum = fma(a.g, acc, base);
-                if (!a.last) {
-                    zout[p] = acc;
-                    yacc[p] = sum;
-                } else if (u) {
-                    u[p] += (double)(sum * a.gamma);
-                } else {
-                    yacc[p] = sum * a.gamma;
-                }
-            }
-            zm = zc;
-            zc = zp;
-            wzm = (OP == ET_OP_CONSERVATIVE) ? wzp : (has_zp ? w3[p + G.sz] : T(0));
-        }
+        term_column<OP, T, TZ>(G, W, a, i, j, tz);
     }
 }
 
@@ -268,12 +282,8 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
 // kernel is bound by the FP64 pipe, so it is kept lean for full occupancy
 // (no plane loop, operands straight from the kernel parameters).
 template <int OP>
-__global__ void __launch_bounds__(kThreads)
-term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= G.nx || j >= G.ny) return;
+__device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<double>& W, const TermArgs<double>& a,
+                                               int i, int j, int k) {
     const long long p = i + G.sy * j + G.sz * k;
     const double* __restrict__ z = a.zin;
     const double zc = z[p];
@@ -307,12 +317,22 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
     }
 }
 
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= G.nx || j >= G.ny) return;
+    term_point_f64<OP>(G, W, a, i, j, k);
+}
+
 // ---------------------------------------------------------------------------
 // stats: sum, min and max of u (min/max through integer order keys, one FP64
 // add per voxel), the non-finite flag, then the step record.  A fixed grid of
 // kStatsBlocks blocks fixes every summation order (bitwise reproducible).
-__global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const double* __restrict__ u,
-                                                              StatsSink s) {
+// Block `blk` (of kStatsBlocks) of the reduction over u[0..n).
+__device__ __forceinline__ void stats_body(long long n, const double* __restrict__ u, const StatsSink& s, int blk) {
     constexpr int kWarps = kStatsThreads / 32;
     __shared__ double ssum[kWarps];
     __shared__ unsigned long long smin[kWarps], smax[kWarps];
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const
     double sum = 0.0;
     unsigned long long kmin = ~0ull, kmax = 0ull;
     bool bad = false;
-    for (long long p = blockIdx.x * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
+    for (long long p = blk * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
         const double v = u[p];
         sum += v;
         const unsigned long long key = order_key(v);
@@ -350,9 +370,9 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const
             kmin = smin[w] < kmin ? smin[w] : kmin;
             kmax = smax[w] > kmax ? smax[w] : kmax;
         }
-        s.partial[3 * blockIdx.x + 0] = sum;
-        s.partial[3 * blockIdx.x + 1] = __longlong_as_double((long long)kmin);
-        s.partial[3 * blockIdx.x + 2] = __longlong_as_double((long long)kmax);
+        s.partial[3 * blk + 0] = sum;
+        s.partial[3 * blk + 1] = __longlong_as_double((long long)kmin);
+        s.partial[3 * blk + 2] = __longlong_as_double((long long)kmax);
         __threadfence();
         const unsigned ticket = atomicAdd(s.ticket, 1u);
         is_last = (ticket == kStatsBlocks - 1);
@@ -399,12 +419,125 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const
         rec.m = s.m;
         rec.flags = atomicOr(s.flags, 0u);
         rec.step = step;
-        s.info[s.info_stride ? step : 0u] = rec;
+        s.info[(size_t)step * (unsigned)s.info_stride] = rec;
         *s.last = rec;
         *s.step_counter = step + 1;
         *s.ticket = 0u;
         __threadfence();
     }
+}
+
+__global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const double* __restrict__ u,
+                                                              StatsSink s) {
+    stats_body(n, u, s, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: the descriptor of the block's grid is copied to shared
+// memory once per tile, then the single-grid device functions run on it.
+
+template <typename D>
+__device__ __forceinline__ int find_desc(const D* __restrict__ d, int count, long long tile) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename D>
+__device__ __forceinline__ void copy_desc(D& dst, const D* __restrict__ src) {
+    static_assert(sizeof(D) % 4 == 0, "descriptor size");
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int* s = reinterpret_cast<const int*>(src);
+    int* t = reinterpret_cast<int*>(&dst);
+    for (int w = tid; w < (int)(sizeof(D) / 4); w += blockDim.x * blockDim.y) t[w] = s[w];
+}
+
+template <int OP, typename T>
+__global__ void __launch_bounds__(kThreads)
+batch_residual_kernel(const BatchResidual<T>* __restrict__ d, int count, int scheme, unsigned* flags) {
+    __shared__ BatchResidual<T> sd;
+    const long long tile = blockIdx.x;
+    const int di = find_desc(d, count, tile);
+    copy_desc(sd, d + di);
+    __syncthreads();
+    const long long lt = tile - sd.tile_begin;
+    const int tiles_x = (sd.G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (sd.G.ny + kBlockY - 1) / kBlockY;
+    const int i = (int)(lt % tiles_x) * kBlockX + threadIdx.x;
+    const long long rest = lt / tiles_x;
+    const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
+    const int k = (int)(rest / tiles_y);
+    if (i >= sd.G.nx || j >= sd.G.ny) return;
+    residual_point<OP, T>(sd.G, sd.u, sd.W, sd.rho, sd.dt_shift, sd.dt_scale, scheme, sd.b, sd.dt, flags, i, j, k);
+}
+
+// FP64, one tile (32 x 8 x 1) per block.
+template <int OP>
+__global__ void __launch_bounds__(kThreads) batch_term_f64_kernel(const BatchTerm<double>* __restrict__ d, int count) {
+    __shared__ BatchTerm<double> sd;
+    const long long tile = blockIdx.x;
+    const int di = find_desc(d, count, tile);
+    copy_desc(sd, d + di);
+    __syncthreads();
+    const long long lt = tile - sd.tile_begin;
+    const int tiles_x = (sd.G.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (sd.G.ny + kBlockY - 1) / kBlockY;
+    const int i = (int)(lt % tiles_x) * kBlockX + threadIdx.x;
+    const long long rest = lt / tiles_x;
+    const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
+    const int k = (int)(rest / tiles_y);
+    if (i >= sd.G.nx || j >= sd.G.ny) return;
+    term_point_f64<OP>(sd.G, sd.W, sd.a, i, j, k);
+}
+
+// Blocks loop over tiles of TZ planes (grid = resident capacity).
+template <int OP, typename T, int TZ>
+__global__ void __launch_bounds__(kThreads)
+batch_term_kernel(const BatchTerm<T>* __restrict__ d, int count, long long tiles) {
+    __shared__ BatchTerm<T> sd;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int di = find_desc(d, count, tile);
+        __syncthreads();
+        copy_desc(sd, d + di);
+        __syncthreads();
+        const long long lt = tile - sd.tile_begin;
+        const int tiles_x = (sd.G.nx + kBlockX - 1) / kBlockX;
+        const int tiles_y = (sd.G.ny + kBlockY - 1) / kBlockY;
+        const int i = (int)(lt % tiles_x) * kBlockX + threadIdx.x;
+        const long long rest = lt / tiles_x;
+        const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
+        const int tz = (int)(rest / tiles_y);
+        if (i < sd.G.nx && j < sd.G.ny) term_column<OP, T, TZ>(sd.G, sd.W, sd.a, i, j, tz);
+    }
+}
+
+__global__ void __launch_bounds__(kStatsThreads) batch_stats_kernel(const BatchStats* __restrict__ d) {
+    __shared__ BatchStats sd;
+    const int di = blockIdx.x / kStatsBlocks;
+    const int tid = threadIdx.x;
+    const int* s = reinterpret_cast<const int*>(d + di);
+    int* t = reinterpret_cast<int*>(&sd);
+    for (int w = tid; w < (int)(sizeof(BatchStats) / 4); w += kStatsThreads) t[w] = s[w];
+    __syncthreads();
+    stats_body(sd.n, sd.u, sd.sink, blockIdx.x % kStatsBlocks);
+}
+
+template <int OP, typename T, int TZ>
+int batch_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_term_kernel<OP, T, TZ>, kThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
 }
 
 // Resident blocks per SM of a term-kernel instantiation (looked up once).
@@ -513,6 +646,81 @@ cudaError_t prime_launch_limits() {
     prime_launch_limits_df64();
     return cudaGetLastError();
 }
+
+int batch_variant_count(et_precision prec) { return prec == ET_F64 ? 3 : (prec == ET_F32 ? 4 : 2); }
+
+BatchVariant batch_variant(et_precision prec, int v) {
+    if (prec == ET_F64) {
+        static const BatchVariant t[3] = {{1, 0}, {1, 1}, {2, 1}};
+        return t[v];
+    }
+    if (prec == ET_F32) {
+        static const BatchVariant t[4] = {{4, 1}, {2, 1}, {8, 1}, {1, 1}};
+        return t[v];
+    }
+    static const BatchVariant t[2] = {{4, 1}, {2, 1}};
+    return t[v];
+}
+
+template <int OP, typename T, int TZ>
+cudaError_t launch_batch_persistent(const BatchTerm<T>* d, int count, long long tiles, int sms, cudaStream_t stream) {
+    const long long cap = (long long)(sms > 0 ? sms : 1) * batch_blocks_per_sm<OP, T, TZ>();
+    batch_term_kernel<OP, T, TZ><<<(unsigned)(tiles < cap ? tiles : cap), dim3(kBlockX, kBlockY, 1), 0, stream>>>(
+        d, count, tiles);
+    return cudaGetLastError();
+}
+
+template <int OP, typename T>
+cudaError_t launch_batch_term_op(int variant, const BatchTerm<T>* d, int count, long long tiles, int sms,
+                                 cudaStream_t stream) {
+    const BatchVariant v = batch_variant(std::is_same<T, double>::value ? ET_F64 : ET_F32, variant);
+    if (std::is_same<T, double>::value && !v.persistent) {
+        if constexpr (std::is_same<T, double>::value)
+            batch_term_f64_kernel<OP><<<(unsigned)tiles, dim3(kBlockX, kBlockY, 1), 0, stream>>>(d, count);
+        return cudaGetLastError();
+    }
+    switch (v.tile_z) {
+        case 1: return launch_batch_persistent<OP, T, 1>(d, count, tiles, sms, stream);
+        case 2: return launch_batch_persistent<OP, T, 2>(d, count, tiles, sms, stream);
+        case 4: return launch_batch_persistent<OP, T, 4>(d, count, tiles, sms, stream);
+        default: return launch_batch_persistent<OP, T, 8>(d, count, tiles, sms, stream);
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch_term(et_operator op, int variant, const BatchTerm<T>* d, int count, long long tiles, int sms,
+                              cudaStream_t stream) {
+    if (op == ET_OP_CONSERVATIVE) return launch_batch_term_op<ET_OP_CONSERVATIVE, T>(variant, d, count, tiles, sms, stream);
+    return launch_batch_term_op<ET_OP_LITERAL, T>(variant, d, count, tiles, sms, stream);
+}
+
+template <typename T>
+cudaError_t launch_batch_residual(et_operator op, int scheme, const BatchResidual<T>* d, int count, long long tiles,
+                                  unsigned* flags, cudaStream_t stream) {
+    if (op == ET_OP_CONSERVATIVE)
+        batch_residual_kernel<ET_OP_CONSERVATIVE, T><<<(unsigned)tiles, dim3(kBlockX, kBlockY, 1), 0, stream>>>(
+            d, count, scheme, flags);
+    else
+        batch_residual_kernel<ET_OP_LITERAL, T><<<(unsigned)tiles, dim3(kBlockX, kBlockY, 1), 0, stream>>>(
+            d, count, scheme, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stats(const BatchStats* d, int count, cudaStream_t stream) {
+    batch_stats_kernel<<<(unsigned)(count * kStatsBlocks), kStatsThreads, 0, stream>>>(d);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_term<double>(et_operator, int, const BatchTerm<double>*, int, long long, int,
+                                               cudaStream_t);
+template cudaError_t launch_batch_term<float>(et_operator, int, const BatchTerm<float>*, int, long long, int,
+                                              cudaStream_t);
+template cudaError_t launch_batch_residual<double>(et_operator, int, const BatchResidual<double>*, int, long long,
+                                                   unsigned*, cudaStream_t);
+template cudaError_t launch_batch_residual<float>(et_operator, int, const BatchResidual<float>*, int, long long,
+                                                  unsigned*, cudaStream_t);
+template cudaError_t launch_batch_residual<float2>(et_operator, int, const BatchResidual<float2>*, int, long long,
+                                                   unsigned*, cudaStream_t);
 
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream) {
     stats_kernel<<<kStatsBlocks, kStatsThreads, 0, stream>>>(G.n, u, sink);

@@ -53,10 +53,16 @@ def uniform(seed: int, stream: int, n: int) -> np.ndarray:
     return (bits >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def _ellipsoid(shape, centre, radii):
+def _axes(shape):
+    """Voxel-centre coordinates z, y, x as broadcastable (nz,1,1), (1,ny,1), (1,1,nx) arrays."""
     nz, ny, nx = shape
-    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
-                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return (np.arange(nz, dtype=np.float64).reshape(nz, 1, 1),
+            np.arange(ny, dtype=np.float64).reshape(1, ny, 1),
+            np.arange(nx, dtype=np.float64).reshape(1, 1, nx))
+
+
+def _ellipsoid(shape, centre, radii):
+    z, y, x = _axes(shape)
     q = ((x - centre[0]) / radii[0]) ** 2 + ((y - centre[1]) / radii[1]) ** 2 \
         + ((z - centre[2]) / radii[2]) ** 2
     return q <= 1.0
@@ -111,9 +117,7 @@ def diffusion_field(labels: np.ndarray, seed: int = 0, d_white: float = D_WHITE,
 
 def gaussian_blob(shape, centre, peak: float = 0.8, sigma: float = 2.0) -> np.ndarray:
     """peak * exp(-|x - centre|^2 / (2 sigma^2)) on voxel centres (float64)."""
-    nz, ny, nx = shape
-    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
-                          np.arange(nx, dtype=np.float64), indexing="ij")
+    z, y, x = _axes(shape)
     r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
     return peak * np.exp(-r2 / (2.0 * sigma * sigma))
 

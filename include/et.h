@@ -102,6 +102,10 @@ typedef struct {
     int force_m;      /* > 0: use this many Taylor terms per sub-step (>= 2) */
     int use_graph;    /* 1 (default): replay et_run / et_step as CUDA graphs;
                          -1: launch kernels directly */
+    int single_terms; /* 1: one Taylor term per launch; 0 (default): the F32 and
+                         DF64 forms evaluate two consecutive terms of a
+                         sub-step per launch (same arithmetic per voxel, about
+                         half the memory traffic); F64 always runs one */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */
@@ -117,6 +121,8 @@ typedef struct {
 #define ET_FLAG_RANGE_IN  2u /* u^n outside [-1e-3, 1 + 1e-3] in the folded scheme:
                                 the a-priori bound behind (s, m) did not hold */
 #define ET_FLAG_D_INVALID 4u /* D < 0 or not finite (et_set_coeffs) */
+#define ET_FLAG_TIMEOUT   8u /* a bounded device-side wait ran out (a TMA load
+                                that never completed); the step is not valid */
 
 /* Bytes of device workspace a grid of this size needs (256-byte aligned
  * start required).  Returns 0 for non-positive sizes. */

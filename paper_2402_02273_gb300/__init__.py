@@ -28,7 +28,7 @@ ET_OK, ET_ERR_ARG, ET_ERR_STATE, ET_ERR_CUDA, ET_ERR_NUMERIC, ET_ERR_TIMEOUT, ET
 ET_F64, ET_F32, ET_DF64 = 0, 1, 2
 ET_OP_CONSERVATIVE, ET_OP_LITERAL = 0, 1
 ET_SCHEME_ROSENBROCK, ET_SCHEME_EXPEULER = 0, 1
-ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID = 1, 2, 4
+ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID, ET_FLAG_TIMEOUT = 1, 2, 4, 8
 
 PRECISIONS = {"f64": ET_F64, "f32": ET_F32, "df64": ET_DF64}
 OPS = {"conservative": ET_OP_CONSERVATIVE, "literal": ET_OP_LITERAL}
@@ -37,7 +37,8 @@ SCHEMES = {"rosenbrock": ET_SCHEME_ROSENBROCK, "expeuler": ET_SCHEME_EXPEULER}
 
 class et_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("theta_max", ctypes.c_double), ("shift", ctypes.c_int),
-                ("force_s", ctypes.c_int), ("force_m", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("force_s", ctypes.c_int), ("force_m", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("single_terms", ctypes.c_int)]
 
 
 class et_step_info(ctypes.Structure):
@@ -140,9 +141,9 @@ def _check(rc: int, handle=None):
         raise EtError(rc, msg or lib.et_status_string(rc).decode())
 
 
-def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True):
+def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True, single_terms=False):
     return et_options(float(tol), float(theta_max), int(shift), int(force_s), int(force_m),
-                      1 if use_graph else -1)
+                      1 if use_graph else -1, 1 if single_terms else 0)
 
 
 def select_schedule(tau, rmax, rho, scheme="rosenbrock", precision="f64", **opts):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libet.so")
-SOURCES = ["et_api.cu", "et_batch_api.cu", "et_kernels.cu", "et_df64.cu", "et_adjoint.cu", "et_probe.cu",
+SOURCES = ["et_api.cu", "et_batch_api.cu", "et_kernels.cu", "et_df64.cu", "et_adjoint.cu", "et_fused.cu", "et_probe.cu",
            "et_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

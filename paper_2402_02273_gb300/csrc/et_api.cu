@@ -6,13 +6,13 @@
 
 #include <algorithm>
 #include <cmath>
-#include <type_traits>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "et.h"
@@ -89,7 +89,7 @@ struct Schedule {
 
 struct ResolvedOptions {
     double tol, theta_max;
-    int shift, force_s, force_m, use_graph;
+    int shift, force_s, force_m, use_graph, single_terms;
 };
 
 ResolvedOptions resolve(const et_options* o, et_precision prec) {
@@ -106,6 +106,7 @@ ResolvedOptions resolve(const et_options* o, et_precision prec) {
     r.force_s = (o && o->force_s > 0) ? o->force_s : 0;
     r.force_m = (o && o->force_m > 0) ? o->force_m : 0;
     r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
+    r.single_terms = (o && o->single_terms > 0) ? 1 : 0;
     return r;
 }
 
@@ -129,6 +130,7 @@ struct et_grid {
     void* vec[6];
     double* stage;
     double* partial;
+    PairPlan* pair;  // tensor maps of the two-term kernel (F32 / DF64), or nullptr
     unsigned long long* rmax_bits;
     unsigned* flags;
     unsigned* ticket;
@@ -269,11 +271,14 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                           cudaStream_t st, long long* launches, const ChainRecord<T>* rec = nullptr) {
     const ChainPlan P = plan_chain(g, S, hstep);
     const int s = S.s;
+    // F32 / DF64 without a recorded chain: consecutive terms of a sub-step go in
+    // pairs, one launch each (et_fused.cu)
+    const bool pairs = !std::is_same<T, double>::value && !rec && g->pair &&
+                       !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
     int zi = 0;  // next z buffer to write
     const T* zin = nullptr;
-    for (const PlannedTerm& t : P.terms) {
+    auto args_of = [&](const PlannedTerm& t) {
         const int k = t.k, j = t.j;
-        T* yacc = rec ? rec->y(k + 1) : B.Y[(k + 1) & 1];
         if (k == 0 && j == 1) zin = B.b;
         if (k > 0 && j == 0) zin = rec ? rec->y(k) : B.Y[k & 1];
         TermArgs<T> a;
@@ -290,10 +295,29 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.base_mode = t.base_mode;
         a.last = t.last;
         a.horner = t.horner;
-        a.yacc = yacc;
+        a.yacc = rec ? rec->y(k + 1) : B.Y[(k + 1) & 1];
         a.u = (t.last && k == s - 1 && !rec) ? u : nullptr;
         a.zout = t.last ? nullptr : (rec ? rec->z(k, j + 1) : B.Z[zi]);
-        cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
+        return a;
+    };
+    for (size_t ti = 0; ti < P.terms.size(); ++ti) {
+        const PlannedTerm& t = P.terms[ti];
+        cudaError_t e;
+        if (pairs && !t.last && ti + 1 < P.terms.size() && P.terms[ti + 1].k == t.k) {
+            const TermArgs<T> a1 = args_of(t);  // its outputs stay on chip
+            const TermArgs<T> a2 = args_of(P.terms[ti + 1]);
+            e = launch_term_pair(g->pair, g->G, g->op, a1, a2, g->flags, st);
+            ++ti;
+            if (e != cudaSuccess) return e;
+            ++*launches;
+            if (!a2.last) {
+                zin = a2.zout;
+                zi ^= 1;
+            }
+            continue;
+        }
+        const TermArgs<T> a = args_of(t);
+        e = launch_term(g->G, g->op, B.W, a, st);
         if (e != cudaSuccess) return e;
         ++*launches;
         if (!t.last) {
@@ -833,6 +857,12 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     for (int v = 0; v < 6; ++v) g->vec[v] = (void*)(g->ws + L.vec[v]);
     g->stage = (double*)(g->ws + L.stage);
     g->partial = (double*)(g->ws + L.partial);
+    g->pair = nullptr;
+    if (precision != ET_F64) {
+        const void* wt4[4] = {g->wt[0], g->wt[1], g->wt[2], g->wt[3]};
+        const void* yz[4] = {g->vec[2], g->vec[3], g->vec[4], g->vec[5]};
+        g->pair = pair_plan_create(g->G, precision, wt4, g->vec[0], g->vec[1], yz);  // nullptr: one term per launch
+    }
     char* misc = g->ws + L.misc;
     g->rmax_bits = (unsigned long long*)(misc + 0);
     g->flags = (unsigned*)(misc + 8);
@@ -852,12 +882,14 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->err[0] = 0;
     e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        pair_plan_destroy(g->pair);
         delete g;
         return fail(nullptr, ET_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
     e = cudaMemsetAsync(misc, 0, kMiscBytes, g->stream);
     if (e != cudaSuccess) {
         cudaStreamDestroy(g->capture);
+        pair_plan_destroy(g->pair);
         delete g;
         return fail(nullptr, ET_ERR_CUDA, "workspace clear: %s", cudaGetErrorString(e));
     }
@@ -918,6 +950,7 @@ et_status et_sync_info(et_grid* g, et_step_info* host_out) {
     ET_CUDA(g, cudaStreamSynchronize(g->stream));
     ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
     if (host_out) *host_out = rec;
+    if (flags & ET_FLAG_TIMEOUT) return fail(g, ET_ERR_TIMEOUT, "a device-side wait ran out; the run is not valid");
     if (flags & ET_FLAG_NONFINITE) return fail(g, ET_ERR_NUMERIC, "non-finite density met");
     if (flags & ET_FLAG_RANGE_IN)
         return fail(g, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3): the step bound does not hold");
@@ -1025,6 +1058,7 @@ void et_destroy(et_grid* g) {
         clear_events(g);
         if (g->capture) cudaStreamDestroy(g->capture);
     }
+    pair_plan_destroy(g->pair);
     delete g;
 }
 

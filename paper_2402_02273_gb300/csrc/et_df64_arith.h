@@ -1,0 +1,70 @@
+// Double-float (DF64) pair arithmetic shared by the DF64 Taylor-term kernels
+// (et_df64.cu, et_fused.cu).  A value is hi + lo in two FP32 numbers (48-bit
+// significand).  Error-free transformations: TwoSum (Knuth) and the FMA-based
+// TwoProduct; sums of products are compensated dot products in the manner of
+// Ogita, Rump and Oishi (2005): high parts added with TwoSum, every rounding
+// error and every hi*lo cross product collected in one FP32 correction, one
+// renormalisation at the end; lo*lo products (relative size 2^-48) dropped.
+// Intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn) keep the compiler from
+// contracting or reassociating any step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace et {
+namespace df64 {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated accumulator of a sum of pair products.
+struct DotAcc {
+    float s, c;
+};
+
+__device__ __forceinline__ void dot_first(DotAcc& A, float2 a, float2 b) {
+    A.s = __fmul_rn(a.x, b.x);
+    float c = __fmaf_rn(a.x, b.x, -A.s);
+    c = __fmaf_rn(a.x, b.y, c);
+    A.c = __fmaf_rn(a.y, b.x, c);
+}
+
+__device__ __forceinline__ void dot_add(DotAcc& A, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float ep = __fmaf_rn(a.x, b.x, -p);
+    float s, es;
+    two_sum(A.s, p, s, es);
+    A.s = s;
+    float c = __fmaf_rn(a.x, b.y, A.c);
+    c = __fmaf_rn(a.y, b.x, c);
+    A.c = __fadd_rn(c, __fadd_rn(ep, es));
+}
+
+__device__ __forceinline__ float2 dot_result(const DotAcc& A) {
+    float s, e;
+    two_sum(A.s, A.c, s, e);
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    DotAcc A;
+    dot_first(A, a, b);
+    return dot_result(A);
+}
+
+// a * b + c as one compensated sum.
+__device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
+    DotAcc A;
+    dot_first(A, a, b);
+    float s, es;
+    two_sum(A.s, c.x, s, es);
+    A.s = s;
+    A.c = __fadd_rn(__fadd_rn(A.c, c.y), es);
+    return dot_result(A);
+}
+
+}  // namespace df64
+}  // namespace et

@@ -1,0 +1,598 @@
+// Two consecutive Taylor terms in one launch (temporal blocking) for the FP32
+// and DF64 forms on sm_103a, fed by TMA.
+//
+// Terms j and j+1 of one sub-step are
+//     z_a = A~ z_j + beta_1 b,          z_b = A~ z_a + beta_2 b,
+// (with the running sums  S_a = base + g_1 z_a,  S_b = S_a + g_2 z_b  outside
+// the Horner sub-step).  A block owns a 32 x 8 column of the grid and marches
+// through a segment of its z-range.  For every plane q one thread issues TMA
+// tile loads (cp.async.bulk.tensor) of z_j with a two-voxel halo (box 36 x 12
+// for DF64, 40 x 12 for FP32, whose x origin is moved to a 16-byte boundary)
+// and of the weights, the diagonal and b with a one-voxel halo into a ring of
+// shared-memory stages completed by an mbarrier; loads run one plane ahead of
+// the arithmetic.  The TMA unit fills voxels outside the grid with zeros, so
+// the zero-flux walls need no branches: every weight of an outside voxel and
+// every outside value reads as 0, exactly the terms the unfused kernels skip.
+// The first term is evaluated on the one-voxel halo of the plane (34 x 10, one
+// voxel per thread of an 11-warp block) into a four-plane shared ring, the
+// second on the interior (8 warps) two planes behind, so the two need only the
+// one barrier per plane; the plane-below values of the first term are carried
+// in registers.  z_a never reaches memory: a pair of terms moves about
+// the bytes of one unfused term.  The per-voxel arithmetic (order of the
+// multiply-adds, pair arithmetic for DF64) is that of the unfused kernels, so
+// both give identical numbers.
+//
+// Eligible grids: rows of a 16-byte multiple (nx even for DF64, a multiple of
+// 4 for FP32), as TMA requires of the global strides; other grids and the
+// adjoint's recorded chains run one term per launch.
+//
+// Every mbarrier wait is bounded; a wait that runs out sets ET_FLAG_TIMEOUT,
+// waits (bounded) for the block's copies still in flight and ends the block.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "et_df64_arith.h"
+#include "et_internal.h"
+
+namespace et {
+
+struct PairPlan {
+    CUtensorMap zj[5];       // 12-row boxes of b, Y0, Y1, Z0, Z1
+    const void* zj_ptr[5];
+    CUtensorMap w0, w1, w2, dt, b, w3;  // w1: 11 rows; the others 10
+};
+
+namespace {
+
+// Tensor maps of one launch (kernel parameter).
+struct PairMaps {
+    CUtensorMap zj, w0, w1, w2, dt, b, w3;
+};
+
+constexpr int kPairThreads = 352;       // 11 warps: one per voxel of the 34 x 10 halo plane
+constexpr int kHaloX = kBlockX + 2;     // 34
+constexpr int kHaloY = kBlockY + 2;     // 10
+constexpr int kHalo = kHaloX * kHaloY;  // 340
+constexpr int kPrefetch = 1;            // stages loaded ahead of the one consumed
+constexpr int kStages = kPrefetch + 4;  // + planes L - 3 (second term), L - 1, L (first term), L - 2
+constexpr int kRing = 4;                // z_a planes kept: the second term's three and the one being written
+constexpr int kWaitTries = 1 << 20;
+
+template <typename T>
+struct Shape {
+    static constexpr int ES = sizeof(T);
+    static constexpr int BX = ES == 8 ? 36 : 40;  // box width (x origin x0 - XO, 16-byte aligned)
+    static constexpr int XO = ES == 8 ? 2 : 4;
+    __host__ __device__ static constexpr int box(int rows) { return rows * BX * ES; }
+    __host__ __device__ static constexpr int pad(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int kZj = 0;                        // 12 rows from y0 - 2
+    static constexpr int kW1 = pad(box(12));             // 11 rows from y0 - 2
+    static constexpr int kW0 = kW1 + pad(box(11));       // 10 rows from y0 - 1 (also w2, dt, b, w3)
+    static constexpr int kW2 = kW0 + pad(box(10));
+    static constexpr int kDt = kW2 + pad(box(10));
+    static constexpr int kB = kDt + pad(box(10));
+    static constexpr int kW3 = kB + pad(box(10));
+    __host__ __device__ static constexpr int stage_bytes(bool literal) { return kW3 + (literal ? pad(box(10)) : 0); }
+    __host__ __device__ static constexpr unsigned tx_bytes(bool literal) {
+        return box(12) + box(11) + 4 * box(10) + (literal ? box(10) : 0);
+    }
+    __host__ __device__ static constexpr int smem_bytes(bool literal) {
+        return 128 + kStages * stage_bytes(literal) + kRing * kHalo * ES + kStages * 8;
+    }
+};
+
+// Per-voxel arithmetic of one term, identical to the unfused kernels.  ZS: the
+// stencil part is scaled by zscale (first term of an FP32 / DF64 chain).
+template <typename T>
+struct Arith;
+
+template <>
+struct Arith<float> {
+    template <bool ZS>
+    static __device__ __forceinline__ float stencil(float dt, float zc, float wxp, float zxp, float wxm, float zxm,
+                                                    float wyp, float zyp, float wym, float zym, float wzp, float zp,
+                                                    float wzm, float zm, float zscale, bool has_beta, float beta,
+                                                    float bval) {
+        float acc = dt * zc;
+        acc = fmaf(wxp, zxp, acc);
+        acc = fmaf(wxm, zxm, acc);
+        acc = fmaf(wyp, zyp, acc);
+        acc = fmaf(wym, zym, acc);
+        acc = fmaf(wzp, zp, acc);
+        acc = fmaf(wzm, zm, acc);
+        if (ZS) acc *= zscale;
+        if (has_beta) acc = fmaf(beta, bval, acc);
+        return acc;
+    }
+    static __device__ __forceinline__ float axpy(float g, float x, float base) { return fmaf(g, x, base); }
+    static __device__ __forceinline__ float scale(float g, float x) { return x * g; }
+    static __device__ __forceinline__ double widen(float x) { return (double)x; }
+    static __device__ __forceinline__ float zero() { return 0.f; }
+};
+
+template <>
+struct Arith<float2> {
+    template <bool ZS>
+    static __device__ __forceinline__ float2 stencil(float2 dt, float2 zc, float2 wxp, float2 zxp, float2 wxm,
+                                                     float2 zxm, float2 wyp, float2 zyp, float2 wym, float2 zym,
+                                                     float2 wzp, float2 zp, float2 wzm, float2 zm, float2 zscale,
+                                                     bool has_beta, float2 beta, float2 bval) {
+        using namespace df64;
+        DotAcc A;
+        dot_first(A, dt, zc);
+        dot_add(A, wxp, zxp);
+        dot_add(A, wxm, zxm);
+        dot_add(A, wyp, zyp);
+        dot_add(A, wym, zym);
+        dot_add(A, wzp, zp);
+        dot_add(A, wzm, zm);
+        float2 acc;
+        if (!ZS) {
+            if (has_beta) dot_add(A, beta, bval);
+            acc = dot_result(A);
+        } else {
+            acc = df_mul(zscale, dot_result(A));
+            if (has_beta) acc = df_fma(beta, bval, acc);
+        }
+        return acc;
+    }
+    static __device__ __forceinline__ float2 axpy(float2 g, float2 x, float2 base) { return df64::df_fma(g, x, base); }
+    static __device__ __forceinline__ float2 scale(float2 g, float2 x) { return df64::df_mul(g, x); }
+    static __device__ __forceinline__ double widen(float2 x) { return (double)x.x + (double)x.y; }
+    static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+};
+
+// Kernel variants: Horner pair (sub-step 0) or running-sum pair; the first
+// term scaled by zscale; the sum's base read from z_j itself (first term of a
+// later sub-step) instead of the running sum.
+enum : int { kModeHorner = 1, kModeZscale = 2, kModeBaseZ = 4 };
+
+// ---- mbarrier and TMA (inline PTX) -----------------------------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- the kernel --------------------------------------------------------------
+
+// FP32: 4 blocks per SM fit the shared memory (46 registers a thread); DF64: 2.
+template <int OP, typename T, int MODE>
+__global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 4 : 2)
+term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
+             const __grid_constant__ TermArgs<T> a1, const __grid_constant__ TermArgs<T> a2, int tz,
+             unsigned* flags) {
+    using S = Shape<T>;
+    using A = Arith<T>;
+    constexpr bool kLit = OP == ET_OP_LITERAL;
+    constexpr bool kHorner = (MODE & kModeHorner) != 0;
+    constexpr bool kZs = (MODE & kModeZscale) != 0;
+    constexpr bool kBaseZ = (MODE & kModeBaseZ) != 0;
+    constexpr int BX = S::BX, XO = S::XO;
+    constexpr int kStageBytes = S::stage_bytes(kLit);
+    constexpr unsigned kTx = S::tx_bytes(kLit);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* const base = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+    T* const za = reinterpret_cast<T*>(base + kStages * kStageBytes);  // [kRing][kHalo], slot = plane & 3
+    uint64_t* const full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes + kRing * kHalo * sizeof(T));
+    const int t = threadIdx.x;
+    if (t == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // everything the loop needs from the parameters, in registers
+    const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
+    const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
+    const T* const ysrc = a1.yacc;
+    T* const zout = a2.zout;
+    T* const yout = a2.yacc;
+    double* const uout = a2.u;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const long long sy = G.sy, sz = G.sz;
+    const T zero = A::zero();
+
+    // first-term voxel of this thread on the halo plane, second-term voxel inside
+    const bool has_b = t < kHalo;
+    const int hx = t % kHaloX, hy = t / kHaloX;
+    const int bz = (hy + 1) * BX + hx - 1 + XO;   // in a 12-row box
+    const int b10 = hy * BX + hx - 1 + XO;        // in a 10-row box
+    const int b11 = (hy + 1) * BX + hx - 1 + XO;  // in the 11-row box
+    const bool has_c = t < kThreads;
+    const int cx = t % kBlockX, cy = t / kBlockX;
+    const int c10 = (cy + 1) * BX + cx + XO;
+    const int c11 = (cy + 2) * BX + cx + XO;
+    const int c12 = (cy + 2) * BX + cx + XO;
+    const int ca = (cy + 1) * kHaloX + cx + 1;
+
+    // ring bookkeeping, the same on every thread
+    unsigned issued = 0, waited = 0;
+    int islot = 0, wslot = 0;
+    unsigned wpar = 0;
+    const unsigned char *s3 = nullptr, *s2 = nullptr, *sp = nullptr, *sc = nullptr;  // planes L - 3 .. L
+
+    const int tiles_x = (nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (ny + kBlockY - 1) / kBlockY;
+    const int ntiles = tiles_x * tiles_y * ((nz + tz - 1) / tz);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * kBlockX;
+        const int rest = tile / tiles_x;
+        const int y0 = (rest % tiles_y) * kBlockY;
+        const int k0 = (rest / tiles_y) * tz;
+        const int k1 = min(k0 + tz, nz);
+        const int Llast = k1 + 1;  // planes k0 - 2 .. k1 + 1 are loaded
+        const int gx = x0 + cx, gy = y0 + cy;
+        const bool store_c = has_c && gx < nx && gy < ny;
+        const long long pc = gx + sy * gy;  // column offset of the second-term voxel
+
+        auto issue = [&](int q) {
+            if (t == 0) {
+                unsigned char* st = base + islot * kStageBytes;
+                uint64_t* bar = &full[islot];
+                mbar_expect_tx(bar, kTx);
+                tma_load(st + S::kZj, &M.zj, x0 - XO, y0 - 2, q, bar);
+                tma_load(st + S::kW1, &M.w1, x0 - XO, y0 - 2, q, bar);
+                tma_load(st + S::kW0, &M.w0, x0 - XO, y0 - 1, q, bar);
+                tma_load(st + S::kW2, &M.w2, x0 - XO, y0 - 1, q, bar);
+                tma_load(st + S::kDt, &M.dt, x0 - XO, y0 - 1, q, bar);
+                tma_load(st + S::kB, &M.b, x0 - XO, y0 - 1, q, bar);
+                if (kLit) tma_load(st + S::kW3, &M.w3, x0 - XO, y0 - 1, q, bar);
+            }
+            ++issued;
+            if (++islot == kStages) islot = 0;
+        };
+        // next plane L: issue the load kPrefetch planes ahead, wait for plane L
+        auto advance = [&](int L) -> bool {
+            if (L + kPrefetch <= Llast) issue(L + kPrefetch);
+            s3 = s2;
+            s2 = sp;
+            sp = sc;
+            sc = base + wslot * kStageBytes;
+            const bool ok = mbar_wait(&full[wslot], wpar);
+            ++waited;
+            if (++wslot == kStages) {
+                wslot = 0;
+                wpar ^= 1u;
+            }
+            return ok;
+        };
+        // true (for every thread) if some wait ran out: record it, let the
+        // copies in flight land, and stop
+        auto timed_out = [&](bool ok) -> bool {
+            if (!__syncthreads_or(!ok)) return false;
+            if (t == 0) atomicOr(flags, ET_FLAG_TIMEOUT);
+            for (unsigned m = waited - 1; m < issued; ++m) mbar_wait(&full[m % kStages], (m / kStages) & 1u);
+            return true;
+        };
+
+        T b_zm = zero, b_w2m = zero;  // z_j and w2 of the plane below, at the halo voxel
+        T c_w2m = zero;               // w2 of the plane below, at the interior voxel
+
+        // first term on plane q = L - 1 from stages sp (q) and sc (q + 1)
+        auto first = [&](int q) {
+            if (!has_b) return;
+            const T* Zp = reinterpret_cast<const T*>(sp + S::kZj);
+            const T* Zc = reinterpret_cast<const T*>(sc + S::kZj);
+            const T* W0 = reinterpret_cast<const T*>(sp + S::kW0);
+            const T* W1 = reinterpret_cast<const T*>(sp + S::kW1);
+            const T* W2 = reinterpret_cast<const T*>(sp + S::kW2);
+            const T* DT = reinterpret_cast<const T*>(sp + S::kDt);
+            const T zc = Zp[bz];
+            T wxm, wym, wzm;
+            if (kLit) {
+                const T w3 = reinterpret_cast<const T*>(sp + S::kW3)[b10];
+                wxm = w3;
+                wym = w3;
+                wzm = w3;
+            } else {
+                wxm = W0[b10 - 1];
+                wym = W1[b11 - BX];
+                wzm = b_w2m;
+            }
+            const T bval = hb1 ? reinterpret_cast<const T*>(sp + S::kB)[b10] : zero;
+            const T wzp = W2[b10];
+            za[(q & 3) * kHalo + t] =
+                A::template stencil<kZs>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11], Zp[bz + BX],
+                                         wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1, beta1, bval);
+            b_zm = zc;
+            b_w2m = wzp;
+        };
+        // second term on plane q = L - 3 from stage s3 (q) and the z_a ring
+        auto second = [&](int q) {
+            if (!has_c) return;
+            const T wzp = reinterpret_cast<const T*>(s3 + S::kW2)[c10];
+            if (store_c) {
+                const T* Ac = za + (q & 3) * kHalo;
+                const T* Ap = za + ((q + 1) & 3) * kHalo;
+                const T* Am = za + ((q - 1) & 3) * kHalo;
+                const T* W0 = reinterpret_cast<const T*>(s3 + S::kW0);
+                const T* W1 = reinterpret_cast<const T*>(s3 + S::kW1);
+                const T* DT = reinterpret_cast<const T*>(s3 + S::kDt);
+                const T acen = Ac[ca];
+                T wxm, wym, wzm;
+                if (kLit) {
+                    const T w3 = reinterpret_cast<const T*>(s3 + S::kW3)[c10];
+                    wxm = w3;
+                    wym = w3;
+                    wzm = w3;
+                } else {
+                    wxm = W0[c10 - 1];
+                    wym = W1[c11 - BX];
+                    wzm = c_w2m;
+                }
+                const T bval = hb2 ? reinterpret_cast<const T*>(s3 + S::kB)[c10] : zero;
+                const T zb = A::template stencil<false>(DT[c10], acen, W0[c10], Ac[ca + 1], wxm, Ac[ca - 1], W1[c11],
+                                                        Ac[ca + kHaloX], wym, Ac[ca - kHaloX], wzp, Ap[ca], wzm, Am[ca],
+                                                        zero, hb2, beta2, bval);
+                const long long p = pc + sz * q;
+                if (kHorner) {
+                    if (!last2) {
+                        zout[p] = zb;
+                    } else {
+                        const T r = A::scale(gamma2, zb);
+                        if (uout) uout[p] += A::widen(r);
+                        else yout[p] = r;
+                    }
+                } else {
+                    const T sb0 = kBaseZ ? reinterpret_cast<const T*>(s3 + S::kZj)[c12] : ysrc[p];
+                    const T sa = A::axpy(g1, acen, sb0);
+                    T sb = A::axpy(g2, zb, sa);
+                    if (!last2) {
+                        zout[p] = zb;
+                        yout[p] = sb;
+                    } else {
+                        sb = A::scale(gamma2, sb);
+                        if (uout) uout[p] += A::widen(sb);
+                        else yout[p] = sb;
+                    }
+                }
+            }
+            c_w2m = wzp;
+        };
+
+        for (int d = 0; d < kPrefetch; ++d) issue(k0 - 2 + d);
+        // Plane L arrives: the first term runs on plane L - 1, the second on
+        // plane L - 3, whose z_a neighbours were all written in earlier
+        // iterations, so one barrier per plane separates the two.  Planes
+        // k0 - 2 .. k0 + 2 fill the carries and the z_a ring.
+        if (timed_out(advance(k0 - 2))) return;
+        bool ok = advance(k0 - 1);
+        if (ok && has_b) {
+            b_zm = reinterpret_cast<const T*>(sp + S::kZj)[bz];
+            b_w2m = reinterpret_cast<const T*>(sp + S::kW2)[b10];
+        }
+        if (timed_out(ok)) return;
+        ok = advance(k0);
+        if (ok) first(k0 - 1);
+        if (timed_out(ok)) return;
+        ok = advance(k0 + 1);
+        if (ok) first(k0);
+        if (timed_out(ok)) return;
+        ok = advance(k0 + 2);
+        if (ok) first(k0 + 1);
+        if (has_c) c_w2m = reinterpret_cast<const T*>(s3 + S::kW2)[c10];  // plane k0 - 1
+        if (timed_out(ok)) return;
+        for (int L = k0 + 3; L <= Llast; ++L) {
+            ok = advance(L);
+            if (ok) first(L - 1);
+            second(L - 3);
+            if (timed_out(ok)) return;
+        }
+        // plane k1 - 1: its z_a neighbours are complete
+        s3 = s2;
+        second(k1 - 1);
+        __syncthreads();
+    }
+}
+
+template <int OP, typename T, int MODE>
+int pair_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int b = 0;
+        const int smem = Shape<T>::smem_bytes(OP == ET_OP_LITERAL);
+        if (cudaFuncSetAttribute(term2_kernel<OP, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term2_kernel<OP, T, MODE>, kPairThreads, smem) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+// Planes per column segment: fewest waves of segments times the planes a
+// segment costs (its own plus about 3 of pipeline fill), over 4..64.
+int choose_tz(const Geom& G, long long capacity) {
+    const long long cols = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY);
+    int best = 4;
+    double best_cost = 1e300;
+    for (int tz = 4; tz <= 64; ++tz) {
+        const long long tiles = cols * ((G.nz + tz - 1) / tz);
+        const long long waves = (tiles + capacity - 1) / capacity;
+        const double cost = (double)waves * (tz + 3.0);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = tz;
+        }
+        if (tz >= G.nz) break;
+    }
+    return best;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool encode(CUtensorMap* m, const void* ptr, const Geom& G, int es, int bx, int rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+    if (!fn || !ptr || (reinterpret_cast<uintptr_t>(ptr) & 15u)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)G.nx * es, (cuuint64_t)G.nx * G.ny * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType type = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return fn(m, type, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int OP, typename T, int MODE>
+cudaError_t launch_pair_mode(const PairMaps& M, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
+                             unsigned* flags, cudaStream_t stream) {
+    const long long cap = (long long)(G.sms > 0 ? G.sms : 1) * pair_blocks_per_sm<OP, T, MODE>();
+    const int tz = choose_tz(G, cap);
+    const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
+                            ((G.nz + tz - 1) / tz);
+    const int smem = Shape<T>::smem_bytes(OP == ET_OP_LITERAL);
+    term2_kernel<OP, T, MODE><<<(unsigned)(tiles < cap ? tiles : cap), kPairThreads, smem, stream>>>(M, G, a1, a2,
+                                                                                                    tz, flags);
+    return cudaGetLastError();
+}
+
+template <int OP, typename T>
+cudaError_t launch_pair_op(const PairPlan* P, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
+                           unsigned* flags, cudaStream_t stream) {
+    // the pair kernel covers the term shapes the chain planner emits
+    if (a1.last || a2.has_zscale || a1.horner != a2.horner) return cudaErrorInvalidValue;
+    if (!a1.horner && (a2.base_mode != 0 || (a1.base_mode != 0 && a1.base_mode != 2))) return cudaErrorInvalidValue;
+    PairMaps M;
+    int zi = -1;
+    for (int i = 0; i < 5; ++i)
+        if (P->zj_ptr[i] == static_cast<const void*>(a1.zin)) zi = i;
+    if (zi < 0) return cudaErrorInvalidValue;
+    M.zj = P->zj[zi];
+    M.w0 = P->w0;
+    M.w1 = P->w1;
+    M.w2 = P->w2;
+    M.dt = P->dt;
+    M.b = P->b;
+    M.w3 = P->w3;
+    if (a1.horner) {
+        if (a1.has_zscale) return launch_pair_mode<OP, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream);
+        return launch_pair_mode<OP, T, kModeHorner>(M, G, a1, a2, flags, stream);
+    }
+    if (a1.has_zscale) {
+        if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeZscale | kModeBaseZ>(M, G, a1, a2, flags, stream);
+        return launch_pair_mode<OP, T, kModeZscale>(M, G, a1, a2, flags, stream);
+    }
+    if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeBaseZ>(M, G, a1, a2, flags, stream);
+    return launch_pair_mode<OP, T, 0>(M, G, a1, a2, flags, stream);
+}
+
+template <int OP, typename T>
+void prime_pair() {
+    pair_blocks_per_sm<OP, T, kModeHorner>();
+    pair_blocks_per_sm<OP, T, kModeHorner | kModeZscale>();
+    pair_blocks_per_sm<OP, T, kModeZscale | kModeBaseZ>();
+    pair_blocks_per_sm<OP, T, kModeZscale>();
+    pair_blocks_per_sm<OP, T, kModeBaseZ>();
+    pair_blocks_per_sm<OP, T, 0>();
+}
+
+}  // namespace
+
+PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const wt[4], const void* b, const void* dt,
+                           const void* const yz[4]) {
+    if (prec == ET_F64) return nullptr;
+    const int es = prec == ET_F32 ? 4 : 8;
+    if (((long long)G.nx * es) % 16 != 0) return nullptr;
+    const int bx = es == 8 ? Shape<float2>::BX : Shape<float>::BX;
+    PairPlan* P = new (std::nothrow) PairPlan();
+    if (!P) return nullptr;
+    const void* zsrc[5] = {b, yz[0], yz[1], yz[2], yz[3]};
+    bool ok = true;
+    for (int i = 0; i < 5; ++i) {
+        ok = ok && encode(&P->zj[i], zsrc[i], G, es, bx, 12);
+        P->zj_ptr[i] = zsrc[i];
+    }
+    ok = ok && encode(&P->w1, wt[1], G, es, bx, 11);
+    ok = ok && encode(&P->w0, wt[0], G, es, bx, 10);
+    ok = ok && encode(&P->w2, wt[2], G, es, bx, 10);
+    ok = ok && encode(&P->w3, wt[3], G, es, bx, 10);
+    ok = ok && encode(&P->dt, dt, G, es, bx, 10);
+    ok = ok && encode(&P->b, b, G, es, bx, 10);
+    if (!ok) {
+        delete P;
+        return nullptr;
+    }
+    return P;
+}
+
+void pair_plan_destroy(PairPlan* P) { delete P; }
+
+template <typename T>
+cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
+                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream) {
+    if (!P) return cudaErrorInvalidValue;
+    if (op == ET_OP_CONSERVATIVE) return launch_pair_op<ET_OP_CONSERVATIVE, T>(P, G, a1, a2, flags, stream);
+    return launch_pair_op<ET_OP_LITERAL, T>(P, G, a1, a2, flags, stream);
+}
+
+cudaError_t prime_launch_limits_pair() {
+    prime_pair<ET_OP_CONSERVATIVE, float>();
+    prime_pair<ET_OP_LITERAL, float>();
+    prime_pair<ET_OP_CONSERVATIVE, float2>();
+    prime_pair<ET_OP_LITERAL, float2>();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_term_pair<float>(const PairPlan*, const Geom&, et_operator, const TermArgs<float>&,
+                                             const TermArgs<float>&, unsigned*, cudaStream_t);
+template cudaError_t launch_term_pair<float2>(const PairPlan*, const Geom&, et_operator, const TermArgs<float2>&,
+                                              const TermArgs<float2>&, unsigned*, cudaStream_t);
+
+}  // namespace et

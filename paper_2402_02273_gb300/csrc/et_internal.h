@@ -193,6 +193,18 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermA
 // double-float form (et_df64.cu)
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const TermArgs<float2>& a,
                         cudaStream_t stream);
+// Two consecutive terms of one sub-step (a1 not last) in one TMA-fed launch
+// (et_fused.cu): a1's outputs are not written, a2's are.  The plan holds the
+// tensor maps of one grid's fields: typed weights wt[0..3], b, the diagonal
+// dt and the vectors Y0, Y1, Z0, Z1 (a1.zin must be b or one of these).
+// pair_plan_create returns nullptr where TMA cannot address the rows.
+struct PairPlan;
+PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const wt[4], const void* b, const void* dt,
+                           const void* const yz[4]);
+void pair_plan_destroy(PairPlan* P);
+template <typename T>
+cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
+                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
 // Adjoint launchers (et_adjoint.cu).
@@ -212,5 +224,6 @@ cudaError_t launch_cast(long long n, const double* src, double scale, float* dst
 // Looks up launch limits (resident blocks per SM) before any stream capture.
 cudaError_t prime_launch_limits();
 cudaError_t prime_launch_limits_df64();
+cudaError_t prime_launch_limits_pair();
 
 }  // namespace et

@@ -644,6 +644,7 @@ cudaError_t prime_launch_limits() {
     term_blocks_per_sm<ET_OP_CONSERVATIVE, float>();
     term_blocks_per_sm<ET_OP_LITERAL, float>();
     prime_launch_limits_df64();
+    prime_launch_limits_pair();
     return cudaGetLastError();
 }
 

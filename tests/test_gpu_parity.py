@@ -107,6 +107,47 @@ def test_unshifted_and_forced_schedules(et_mod, torch_cuda, shift, precision):
                         precision=precision)
 
 
+def _run_states(et, torch, D, u0, tau, nsteps, precision, **kw):
+    g = et.Grid(D.shape, precision=precision)
+    opts = {k: v for k, v in kw.items() if k not in ("rho", "op", "scheme")}
+    g.set_coeffs(torch.from_numpy(D.copy()).cuda(), rho=kw.get("rho", 0.025), op=kw.get("op", "conservative"),
+                 scheme=kw.get("scheme", "rosenbrock"), **opts)
+    u = torch.from_numpy(u0.copy()).cuda()
+    g.run(u, tau, nsteps)
+    rec = g.sync_info()
+    rec["term_launches"] = g.timing()[1]
+    return u.cpu().numpy().reshape(D.shape), rec
+
+
+@pytest.mark.parametrize("precision", ["f32", "df64"])
+@pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "rosenbrock"),
+                                       ("conservative", "expeuler")])
+@pytest.mark.parametrize("shape", [(5, 17, 33), (9, 8, 40), (1, 1, 45), (3, 70, 2), (40, 12, 36), (7, 19, 68),
+                                   (33, 9, 64), (2, 3, 8)])
+@pytest.mark.parametrize("sched", [{}, {"force_s": 3, "force_m": 5}, {"force_s": 2, "force_m": 4},
+                                   {"force_s": 1, "force_m": 2}])
+def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op, scheme, shape, sched):
+    """Two terms per launch (TMA-fed, on-chip first term) against one term per
+    launch: the per-voxel arithmetic is the same, so the results are identical.
+    Rows of a 16-byte multiple take the pair kernel (fewer launches), others run
+    one term per launch.  The schedules cover odd and even term counts per
+    sub-step, a lone trailing term, s = 1 (the pair finishes the step) and m = 2
+    (no pair); the shapes cover ragged y and z, several x tiles and z segments."""
+    D = (0.01 + 0.2 * phantom.uniform(5, 7, int(np.prod(shape)))).reshape(shape)
+    D = D.astype(np.float32).astype(np.float64)
+    u0 = 0.9 * phantom.uniform(5, 8, D.size).reshape(shape)
+    kw = dict(op=op, scheme=scheme, **sched)
+    fused, rf = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, **kw)
+    single, rs = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, single_terms=True, **kw)
+    assert (rf["s"], rf["m"]) == (rs["s"], rs["m"])
+    eligible = (shape[2] * (4 if precision == "f32" else 8)) % 16 == 0
+    if eligible and rf["m"] >= 3:
+        assert rf["term_launches"] < rs["term_launches"]
+    else:
+        assert rf["term_launches"] <= rs["term_launches"]
+    assert np.array_equal(fused, single), np.abs(fused - single).max()
+
+
 @pytest.mark.parametrize("precision", FP64_FORMS)
 def test_no_diffusion_and_no_growth_edge_cases(et_mod, torch_cuda, precision):
     shape = (6, 9, 35)

@@ -255,56 +255,77 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
     const int tiles_x = (nx + kBlockX - 1) / kBlockX;
     const int tiles_y = (ny + kBlockY - 1) / kBlockY;
     const int ntiles = tiles_x * tiles_y * ((nz + tz - 1) / tz);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * kBlockX;
+    auto tile_geom = [&](int tile, int& x0, int& y0, int& k0, int& k1) {
+        x0 = (tile % tiles_x) * kBlockX;
         const int rest = tile / tiles_x;
-        const int y0 = (rest % tiles_y) * kBlockY;
-        const int k0 = (rest / tiles_y) * tz;
-        const int k1 = min(k0 + tz, nz);
+        y0 = (rest % tiles_y) * kBlockY;
+        k0 = (rest / tiles_y) * tz;
+        k1 = min(k0 + tz, nz);
+    };
+    // The block's tiles (blockIdx.x, + gridDim.x, ...) form one stream of
+    // stages, planes k0 - 2 .. k1 + 1 of each; loads run kPrefetch stages ahead
+    // in that stream, across tile boundaries.
+    int itile = blockIdx.x, ix0 = 0, iy0 = 0, ik0 = 0, ik1 = 0, iq = 0;
+    if (itile < ntiles) {
+        tile_geom(itile, ix0, iy0, ik0, ik1);
+        iq = ik0 - 2;
+    }
+    auto issue_next = [&]() {
+        if (itile >= ntiles) return;
+        if (t == 0) {
+            unsigned char* st = base + islot * kStageBytes;
+            uint64_t* bar = &full[islot];
+            mbar_expect_tx(bar, kTx);
+            tma_load(st + S::kZj, &M.zj, ix0 - XO, iy0 - 2, iq, bar);
+            tma_load(st + S::kW1, &M.w1, ix0 - XO, iy0 - 2, iq, bar);
+            tma_load(st + S::kW0, &M.w0, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kW2, &M.w2, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kDt, &M.dt, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kB, &M.b, ix0 - XO, iy0 - 1, iq, bar);
+            if (kLit) tma_load(st + S::kW3, &M.w3, ix0 - XO, iy0 - 1, iq, bar);
+        }
+        ++issued;
+        if (++islot == kStages) islot = 0;
+        if (++iq > ik1 + 1) {
+            itile += gridDim.x;
+            if (itile < ntiles) {
+                tile_geom(itile, ix0, iy0, ik0, ik1);
+                iq = ik0 - 2;
+            }
+        }
+    };
+    // next plane: issue one more stage of the stream, wait for this one
+    auto advance = [&]() -> bool {
+        issue_next();
+        s3 = s2;
+        s2 = sp;
+        sp = sc;
+        sc = base + wslot * kStageBytes;
+        const bool ok = mbar_wait(&full[wslot], wpar);
+        ++waited;
+        if (++wslot == kStages) {
+            wslot = 0;
+            wpar ^= 1u;
+        }
+        return ok;
+    };
+    // true (for every thread) if some wait ran out: record it, let the copies
+    // in flight land, and stop
+    auto timed_out = [&](bool ok) -> bool {
+        if (!__syncthreads_or(!ok)) return false;
+        if (t == 0) atomicOr(flags, ET_FLAG_TIMEOUT);
+        for (unsigned m = waited - 1; m < issued; ++m) mbar_wait(&full[m % kStages], (m / kStages) & 1u);
+        return true;
+    };
+
+    for (int d = 0; d < kPrefetch; ++d) issue_next();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int x0, y0, k0, k1;
+        tile_geom(tile, x0, y0, k0, k1);
         const int Llast = k1 + 1;  // planes k0 - 2 .. k1 + 1 are loaded
         const int gx = x0 + cx, gy = y0 + cy;
         const bool store_c = has_c && gx < nx && gy < ny;
         const long long pc = gx + sy * gy;  // column offset of the second-term voxel
-
-        auto issue = [&](int q) {
-            if (t == 0) {
-                unsigned char* st = base + islot * kStageBytes;
-                uint64_t* bar = &full[islot];
-                mbar_expect_tx(bar, kTx);
-                tma_load(st + S::kZj, &M.zj, x0 - XO, y0 - 2, q, bar);
-                tma_load(st + S::kW1, &M.w1, x0 - XO, y0 - 2, q, bar);
-                tma_load(st + S::kW0, &M.w0, x0 - XO, y0 - 1, q, bar);
-                tma_load(st + S::kW2, &M.w2, x0 - XO, y0 - 1, q, bar);
-                tma_load(st + S::kDt, &M.dt, x0 - XO, y0 - 1, q, bar);
-                tma_load(st + S::kB, &M.b, x0 - XO, y0 - 1, q, bar);
-                if (kLit) tma_load(st + S::kW3, &M.w3, x0 - XO, y0 - 1, q, bar);
-            }
-            ++issued;
-            if (++islot == kStages) islot = 0;
-        };
-        // next plane L: issue the load kPrefetch planes ahead, wait for plane L
-        auto advance = [&](int L) -> bool {
-            if (L + kPrefetch <= Llast) issue(L + kPrefetch);
-            s3 = s2;
-            s2 = sp;
-            sp = sc;
-            sc = base + wslot * kStageBytes;
-            const bool ok = mbar_wait(&full[wslot], wpar);
-            ++waited;
-            if (++wslot == kStages) {
-                wslot = 0;
-                wpar ^= 1u;
-            }
-            return ok;
-        };
-        // true (for every thread) if some wait ran out: record it, let the
-        // copies in flight land, and stop
-        auto timed_out = [&](bool ok) -> bool {
-            if (!__syncthreads_or(!ok)) return false;
-            if (t == 0) atomicOr(flags, ET_FLAG_TIMEOUT);
-            for (unsigned m = waited - 1; m < issued; ++m) mbar_wait(&full[m % kStages], (m / kStages) & 1u);
-            return true;
-        };
 
         T b_zm = zero, b_w2m = zero;  // z_j and w2 of the plane below, at the halo voxel
         T c_w2m = zero;               // w2 of the plane below, at the interior voxel
@@ -391,30 +412,29 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
             c_w2m = wzp;
         };
 
-        for (int d = 0; d < kPrefetch; ++d) issue(k0 - 2 + d);
         // Plane L arrives: the first term runs on plane L - 1, the second on
         // plane L - 3, whose z_a neighbours were all written in earlier
         // iterations, so one barrier per plane separates the two.  Planes
         // k0 - 2 .. k0 + 2 fill the carries and the z_a ring.
-        if (timed_out(advance(k0 - 2))) return;
-        bool ok = advance(k0 - 1);
+        if (timed_out(advance())) return;
+        bool ok = advance();
         if (ok && has_b) {
             b_zm = reinterpret_cast<const T*>(sp + S::kZj)[bz];
             b_w2m = reinterpret_cast<const T*>(sp + S::kW2)[b10];
         }
         if (timed_out(ok)) return;
-        ok = advance(k0);
+        ok = advance();
         if (ok) first(k0 - 1);
         if (timed_out(ok)) return;
-        ok = advance(k0 + 1);
+        ok = advance();
         if (ok) first(k0);
         if (timed_out(ok)) return;
-        ok = advance(k0 + 2);
+        ok = advance();
         if (ok) first(k0 + 1);
         if (has_c) c_w2m = reinterpret_cast<const T*>(s3 + S::kW2)[c10];  // plane k0 - 1
         if (timed_out(ok)) return;
         for (int L = k0 + 3; L <= Llast; ++L) {
-            ok = advance(L);
+            ok = advance();
             if (ok) first(L - 1);
             second(L - 3);
             if (timed_out(ok)) return;
@@ -443,8 +463,11 @@ int pair_blocks_per_sm() {
     return cached;
 }
 
-// Planes per column segment: fewest waves of segments times the planes a
-// segment costs (its own plus about 3 of pipeline fill), over 4..64.
+// Planes per column segment: the fewest waves of segments over the resident
+// blocks times the planes a segment costs (its own plus about three: the
+// first term runs on two more planes than the second, and the pipeline
+// fills).  Measured on 128^3 grids, long segments win over balanced ones.
+// 4..64 planes.
 int choose_tz(const Geom& G, long long capacity) {
     const long long cols = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY);
     int best = 4;

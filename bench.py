@@ -413,31 +413,36 @@ def main():
             args.steps = ksave
             recs = B.sync_info()
             sizes = [int(np.prod(sh)) for sh in shapes]
-            # algorithmic bytes of the term launches over the whole run, per
-            # grid (m-1 Horner terms, (s-1) m later terms per step)
-            term_bytes = sum(n_i * (HORNER_BYTES[prec] * (m_i - 1) + TERM_BYTES[prec] * (s_i - 1) * m_i)
+            # the autotuned variant: two terms per launch in the first half of
+            # the index range (F32 / DF64)
+            pairs = prec != "f64" and variant < len(tune_us) // 2
+            # algorithmic bytes of the term launches over the whole run, per grid
+            term_bytes = sum(n_i * launch_mix(prec, s_i, m_i, pairs)[1]
                              for n_i, s_i, m_i in zip(sizes, s_list, m_list)) * args.nsteps
             gbs = term_bytes / (ms * 1e-3) / 1e9
-            # the autotuner's timing of the chosen variant on the first term
-            # launch (a Horner term of every grid), cold L2 between repeats not
-            # enforced: the launch streams ~4-8 GB, far above L2
+            # the autotuner's timing of the chosen variant on the first launch
+            # of every grid (Horner terms), per term; cold L2 is not enforced
+            # between its repeats: the launch streams 4-8 GB, far above L2
             t_us = tune_us[variant]
             if prec == "f64":
                 ach = HORNER_FLOPS[prec] * nb / (t_us * 1e-6) / 1e12
                 broof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": ach / fp64_peak}
             else:
-                ach = HORNER_BYTES[prec] * nb / (t_us * 1e-6) / 1e9
+                per_term = HORNER_BYTES[prec] / (2.0 if pairs else 1.0)
+                ach = per_term * nb / (t_us * 1e-6) / 1e9
                 broof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
-            broof.update({"kernel": "batched term (first launch, all grids)", "avg_launch_us": t_us,
-                          "traffic": None})
+            broof.update({"kernel": "batched " + ("two-term" if pairs else "one-term") + " launch (first, all grids)",
+                          "us_per_term": t_us, "traffic": None})
             batch[prec] = {"value": whole_job_rate(world, nb, args.nsteps, ms), "unit": UNIT,
                            "ms_per_run": ms, "voxels": nb, "grids": len(shapes), "steps": args.nsteps,
-                           "setup_ms": setup_ms, "variant": variant, "autotune_us": tune_us,
+                           "setup_ms": setup_ms, "variant": variant, "two_terms_per_launch": pairs,
+                           "autotune_us_per_term": tune_us,
                            "s_range": [min(s_list), max(s_list)], "m_range": [min(m_list), max(m_list)],
                            "roofline": broof, "term_gbs_whole_run": gbs, "term_hbm_frac_whole_run": gbs / hbm_peak,
-                           # per step: residual, max(s m) - 1 term launches, stats
-                           "launches_per_run": args.nsteps * (max(si * mi for si, mi in zip(s_list, m_list)) + 1),
+                           # per step: residual, the longest chain's launches, stats
+                           "launches_per_run": args.nsteps * (max(launch_mix(prec, si, mi, pairs)[0]
+                                                                  for si, mi in zip(s_list, m_list)) + 2),
                            "max_final_umax": max(r["umax"] for r in recs),
                            "timed_runs": args.batch_runs, "warmup_runs": 1, "clocks": clocks}
             B.close()

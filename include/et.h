@@ -243,8 +243,12 @@ ET_API et_status et_batch_create(int count, const int* dims, double h, et_precis
 ET_API et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, et_operator op,
                                      et_scheme scheme, const et_options* options);
 ET_API et_status et_batch_run(et_batch* b, double* u, double tau, int nsteps, et_step_info* info);
-/* Times every kernel variant on one term launch of this batch and keeps the
- * fastest; us_per_variant (host, et_batch_variant_count entries) may be NULL. */
+/* Times every kernel variant on the first launch of every grid's chain and
+ * keeps the fastest.  Variants: planes per tile and looping blocks of the
+ * one-term kernel, and for ET_F32 / ET_DF64 each of these with two terms of a
+ * sub-step per launch (the first half of the index range).  us_per_variant
+ * (host, et_batch_variant_count entries, may be NULL) receives microseconds
+ * per Taylor term of the whole batch. */
 ET_API et_status et_batch_autotune(et_batch* b, double tau, int* variant, double* us_per_variant);
 ET_API int et_batch_variant_count(et_precision precision);
 /* Uses kernel variant `variant` (0 .. et_batch_variant_count - 1) instead of the

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "et.h"
+#include "et_chain.h"
 #include "et_internal.h"
 #include "et_plan.h"
 
@@ -271,16 +272,31 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                           cudaStream_t st, long long* launches, const ChainRecord<T>* rec = nullptr) {
     const ChainPlan P = plan_chain(g, S, hstep);
     const int s = S.s;
-    // F32 / DF64 without a recorded chain: consecutive terms of a sub-step go in
-    // pairs, one launch each (et_fused.cu)
-    const bool pairs = !std::is_same<T, double>::value && !rec && g->pair &&
-                       !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
-    int zi = 0;  // next z buffer to write
+    if (!rec) {
+        // F32 / DF64: consecutive terms of a sub-step go in pairs (et_fused.cu)
+        const bool pairs = !std::is_same<T, double>::value && g->pair &&
+                           !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
+        T* const Y[2] = {B.Y[0], B.Y[1]};
+        T* const Z[2] = {B.Z[0], B.Z[1]};
+        for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs)) {
+            cudaError_t e;
+            if constexpr (std::is_same<T, double>::value) {
+                e = launch_term(g->G, g->op, B.W, op.a1, st);
+            } else {
+                e = op.pair ? launch_term_pair(g->pair, g->G, g->op, op.a1, op.a2, g->flags, st)
+                            : launch_term(g->G, g->op, B.W, op.a1, st);
+            }
+            if (e != cudaSuccess) return e;
+            ++*launches;
+        }
+        return cudaSuccess;
+    }
+    // recorded chain (adjoint): every term to its own buffer
     const T* zin = nullptr;
-    auto args_of = [&](const PlannedTerm& t) {
+    for (const PlannedTerm& t : P.terms) {
         const int k = t.k, j = t.j;
         if (k == 0 && j == 1) zin = B.b;
-        if (k > 0 && j == 0) zin = rec ? rec->y(k) : B.Y[k & 1];
+        if (k > 0 && j == 0) zin = rec->y(k);
         TermArgs<T> a;
         a.zin = zin;
         a.b = B.b;
@@ -295,35 +311,13 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.base_mode = t.base_mode;
         a.last = t.last;
         a.horner = t.horner;
-        a.yacc = rec ? rec->y(k + 1) : B.Y[(k + 1) & 1];
-        a.u = (t.last && k == s - 1 && !rec) ? u : nullptr;
-        a.zout = t.last ? nullptr : (rec ? rec->z(k, j + 1) : B.Z[zi]);
-        return a;
-    };
-    for (size_t ti = 0; ti < P.terms.size(); ++ti) {
-        const PlannedTerm& t = P.terms[ti];
-        cudaError_t e;
-        if (pairs && !t.last && ti + 1 < P.terms.size() && P.terms[ti + 1].k == t.k) {
-            const TermArgs<T> a1 = args_of(t);  // its outputs stay on chip
-            const TermArgs<T> a2 = args_of(P.terms[ti + 1]);
-            e = launch_term_pair(g->pair, g->G, g->op, a1, a2, g->flags, st);
-            ++ti;
-            if (e != cudaSuccess) return e;
-            ++*launches;
-            if (!a2.last) {
-                zin = a2.zout;
-                zi ^= 1;
-            }
-            continue;
-        }
-        const TermArgs<T> a = args_of(t);
-        e = launch_term(g->G, g->op, B.W, a, st);
+        a.yacc = rec->y(k + 1);
+        a.u = nullptr;
+        a.zout = t.last ? nullptr : rec->z(k, j + 1);
+        const cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
         if (e != cudaSuccess) return e;
         ++*launches;
-        if (!t.last) {
-            zin = a.zout;
-            if (!rec) zi ^= 1;
-        }
+        if (!t.last) zin = a.zout;
     }
     return cudaSuccess;
 }

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "et.h"
+#include "et_chain.h"
 #include "et_internal.h"
 #include "et_plan.h"
 
@@ -36,12 +37,20 @@ size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
 // flags, per-grid rmax bits, tickets and step counters, per-grid step records
 size_t misc_bytes(int count) { return 128ull * count + 1024; }
 
+size_t term_desc_bytes(et_precision prec) {
+    return prec == ET_F64 ? sizeof(BatchTerm<double>)
+                          : (prec == ET_F32 ? sizeof(BatchTerm<float>) : sizeof(BatchTerm<float2>));
+}
+size_t pair_desc_bytes(et_precision prec) {
+    return prec == ET_F64 ? 0 : (prec == ET_F32 ? sizeof(BatchPair<float>) : sizeof(BatchPair<float2>));
+}
+// Per grid: up to kMaxTermLaunches single terms, or half as many pairs, plus
+// its residual and stats descriptors.
 size_t desc_bytes_per_instance(et_precision prec) {
-    const size_t term = prec == ET_F64 ? sizeof(BatchTerm<double>)
-                                       : (prec == ET_F32 ? sizeof(BatchTerm<float>) : sizeof(BatchTerm<float2>));
     const size_t res = prec == ET_F64 ? sizeof(BatchResidual<double>)
                                       : (prec == ET_F32 ? sizeof(BatchResidual<float>) : sizeof(BatchResidual<float2>));
-    return (size_t)kMaxTermLaunches * term + res + sizeof(BatchStats);
+    return (size_t)kMaxTermLaunches * term_desc_bytes(prec) + (size_t)(kMaxTermLaunches / 2) * pair_desc_bytes(prec) +
+           res + sizeof(BatchStats) + 64;
 }
 
 struct BatchLayout {
@@ -77,7 +86,7 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
     L->stage = take(8ull * ntot);
     L->partial = take(3ull * 8ull * kStatsBlocks * count);
     L->desc = take(desc_bytes_per_instance(prec) * count);
-    L->tune_desc = take(desc_bytes_per_instance(prec) / kMaxTermLaunches * count + 256);
+    L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec)) * count + 256);
     L->misc = take(misc_bytes(count));
     L->total = off;
     return true;
@@ -113,8 +122,12 @@ struct et_batch {
     double table_tau;
     int table_variant;
     int nlaunch;                         // term launches per step
-    std::vector<long long> launch_tiles; // tiles per term launch
-    std::vector<int> launch_count;       // descriptors per term launch
+    // per launch index of a step: single-term descriptors (count, tiles, first)
+    // and two-term descriptors (count, tiles, first)
+    std::vector<int> single_count, pair_count;
+    std::vector<long long> single_tiles, pair_tiles, single_first, pair_first;
+    size_t pair_table_offset;              // byte offset of the two-term descriptors
+    std::vector<PairPlan*> pair_plans;     // per grid (F32 / DF64), nullptr: one term per launch
     long long res_tiles;
     double graph_tau;
     int graph_steps;
@@ -201,26 +214,35 @@ Weights<T> typed_weights(et_batch* b, int i) {
     return W;
 }
 
-// Host-side tables of one step: the residual descriptors, then for every term
-// index t the descriptors of the grids whose chain has a term t.  u_override
-// (non-null): the last term writes there instead of u (autotuning).
+// Kernel variants: the single-term variants of batch_variant (planes per tile,
+// looping blocks) and, for F32 / DF64, each of them again with two-term
+// launches (the first half of the index range).
+int total_variants(et_precision prec) {
+    return prec == ET_F64 ? batch_variant_count(prec) : 2 * batch_variant_count(prec);
+}
+bool variant_pairs(et_precision prec, int v) { return prec != ET_F64 && v < batch_variant_count(prec); }
+int single_variant(et_precision prec, int v) { return v % batch_variant_count(prec); }
+
+size_t align64(size_t x) { return (x + 63) / 64 * 64; }
+
+// Host-side tables of one step: the residual and stats descriptors of every
+// grid, then for every launch index l the single-term and the two-term
+// descriptors of the grids whose chain has an l-th launch.  tuning: the step
+// result goes to the staging field instead of u.
 template <typename T>
 et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vector<char>& bytes, bool tuning) {
     const int C = b->count;
-    const int tz = batch_variant(b->prec, variant).tile_z;
+    const int tz = batch_variant(b->prec, single_variant(b->prec, variant)).tile_z;
+    const bool want_pairs = variant_pairs(b->prec, variant) && !(b->opt_set && b->opt.single_terms > 0);
     std::vector<Sched> S(C);
     std::vector<ChainPlan> plans(C);
-    int nl = 0;
     for (int i = 0; i < C; ++i) {
         if (sched_of(b, i, tau, &S[i]) != ET_OK)
             return bfail(b, ET_ERR_ARG, "no (s, m) meets the tolerance for grid %d at tau = %g", i, tau);
         plans[i] = plan_chain(b->prec, b->nu[i], S[i].s, S[i].m, S[i].mu, tau / S[i].s);
-        nl = std::max(nl, (int)plans[i].terms.size());
+        if ((int)plans[i].terms.size() > kMaxTermLaunches)
+            return bfail(b, ET_ERR_UNSUPPORTED, "more than %d terms per step", kMaxTermLaunches);
     }
-    if (nl > kMaxTermLaunches) return bfail(b, ET_ERR_UNSUPPORTED, "more than %d terms per step", kMaxTermLaunches);
-    b->nlaunch = nl;
-    b->launch_tiles.assign(nl, 0);
-    b->launch_count.assign(nl, 0);
     // residual descriptors
     std::vector<BatchResidual<T>> res(C);
     long long rt = 0;
@@ -238,81 +260,105 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         rt += tiles_of(r.G, 1);
     }
     b->res_tiles = rt;
-    // term descriptors, launch by launch; each grid runs its own chain
-    std::vector<BatchTerm<T>> terms;
-    std::vector<int> zi(C, 0);
-    std::vector<const T*> zin(C, nullptr);
-    for (int t = 0; t < nl; ++t) {
-        long long tiles = 0;
-        int cnt = 0;
+    // every grid runs its own chain, launch by launch
+    std::vector<std::vector<ChainOp<T>>> ops(C);
+    int nl = 0;
+    for (int i = 0; i < C; ++i) {
+        T* const Y[2] = {field<T>(b, b->L.vec[2], i), field<T>(b, b->L.vec[3], i)};
+        T* const Z[2] = {field<T>(b, b->L.vec[4], i), field<T>(b, b->L.vec[5], i)};
+        double* ui = tuning ? field<double>(b, b->L.stage, i) : u + b->offs[i];
+        const bool pairs = want_pairs && b->pair_plans[i] != nullptr;
+        ops[i] = chain_ops<T>(plans[i], S[i].s, field<T>(b, b->L.vec[0], i), field<T>(b, b->L.vec[1], i), Y, Z, ui,
+                              pairs);
+        nl = std::max(nl, (int)ops[i].size());
+    }
+    b->nlaunch = nl;
+    b->single_count.assign(nl, 0);
+    b->pair_count.assign(nl, 0);
+    b->single_tiles.assign(nl, 0);
+    b->pair_tiles.assign(nl, 0);
+    b->single_first.assign(nl, 0);
+    b->pair_first.assign(nl, 0);
+    std::vector<BatchTerm<T>> singles;
+    std::vector<BatchPair<T>> pairs;
+    for (int l = 0; l < nl; ++l) {
+        b->single_first[l] = (long long)singles.size();
+        b->pair_first[l] = (long long)pairs.size();
+        long long st = 0, pt = 0;
         for (int i = 0; i < C; ++i) {
-            if (t >= (int)plans[i].terms.size()) continue;
-            const ChainPlan& P = plans[i];
-            const PlannedTerm& pt = P.terms[t];
-            const int k = pt.k, j = pt.j;
-            T* Y[2] = {field<T>(b, b->L.vec[2], i), field<T>(b, b->L.vec[3], i)};
-            T* Z[2] = {field<T>(b, b->L.vec[4], i), field<T>(b, b->L.vec[5], i)};
-            const T* bv = field<T>(b, b->L.vec[0], i);
-            if (k == 0 && j == 1) zin[i] = bv;
-            if (k > 0 && j == 0) zin[i] = Y[k & 1];
-            BatchTerm<T> d;
-            std::memset(&d, 0, sizeof(d));
-            d.G = geom_of(b, i);
-            d.W = typed_weights<T>(b, i);
-            TermArgs<T>& a = d.a;
-            a.zin = zin[i];
-            a.b = bv;
-            a.beta = Scalar<T>::make(pt.beta);
-            a.has_beta = pt.beta != 0.0;
-            a.zscale = Scalar<T>::make(pt.zscale_val);
-            a.has_zscale = pt.zscale_on;
-            a.dt = field<T>(b, b->L.vec[1], i);
-            a.g = Scalar<T>::make(pt.gnext);
-            a.gamma = Scalar<T>::make(pt.last ? P.gamma * (pt.horner ? pt.gnext : 1.0) : 1.0);
-            a.base_scale = Scalar<T>::make(pt.base_scale);
-            a.base_mode = pt.base_mode;
-            a.last = pt.last;
-            a.horner = pt.horner;
-            a.yacc = Y[(k + 1) & 1];
-            const bool finish = pt.last && k == S[i].s - 1;
-            a.u = finish ? (tuning ? field<double>(b, b->L.stage, i) : u + b->offs[i]) : nullptr;
-            a.zout = pt.last ? nullptr : Z[zi[i]];
-            if (!pt.last) {
-                zin[i] = a.zout;
-                zi[i] ^= 1;
+            if (l >= (int)ops[i].size()) continue;
+            const ChainOp<T>& op = ops[i][l];
+            if (op.pair) {
+                BatchPair<T> d;
+                std::memset(&d, 0, sizeof(d));
+                if (!pair_maps(b->pair_plans[i], op.a1.zin, &d.M))
+                    return bfail(b, ET_ERR_UNSUPPORTED, "grid %d: no tensor map for a two-term launch", i);
+                d.G = geom_of(b, i);
+                d.a1 = op.a1;
+                d.a2 = op.a2;
+                d.tz = batch_pair_tz(d.G);
+                d.tile_begin = pt;
+                pt += tiles_of(d.G, d.tz);
+                pairs.push_back(d);
+            } else {
+                BatchTerm<T> d;
+                std::memset(&d, 0, sizeof(d));
+                d.G = geom_of(b, i);
+                d.W = typed_weights<T>(b, i);
+                d.a = op.a1;
+                d.tile_begin = st;
+                st += tiles_of(d.G, tz);
+                singles.push_back(d);
             }
-            d.tile_begin = tiles;
-            tiles += tiles_of(d.G, tz);
-            terms.push_back(d);
-            ++cnt;
         }
-        b->launch_tiles[t] = tiles;
-        b->launch_count[t] = cnt;
+        b->single_count[l] = (int)((long long)singles.size() - b->single_first[l]);
+        b->pair_count[l] = (int)((long long)pairs.size() - b->pair_first[l]);
+        b->single_tiles[l] = st;
+        b->pair_tiles[l] = pt;
     }
     // stats descriptors
-    std::vector<BatchStats> st(C);
+    std::vector<BatchStats> stv(C);
     for (int i = 0; i < C; ++i) {
-        st[i].n = geom_of(b, i).n;
-        st[i].u = u + b->offs[i];
-        StatsSink& s = st[i].sink;
-        s.partial = (double*)(b->ws + b->L.partial) + 3ull * kStatsBlocks * i;
-        s.ticket = ticket_of(b, i);
-        s.step_counter = counter_of(b, i);
-        s.flags = flags_of(b);
-        s.info = nullptr;  // set per run
-        s.info_stride = 0;
-        s.last = slot_of(b, i);
-        s.s = S[i].s;
-        s.m = S[i].m;
+        stv[i].n = geom_of(b, i).n;
+        stv[i].u = u + b->offs[i];
+        StatsSink& sk = stv[i].sink;
+        sk.partial = (double*)(b->ws + b->L.partial) + 3ull * kStatsBlocks * i;
+        sk.ticket = ticket_of(b, i);
+        sk.step_counter = counter_of(b, i);
+        sk.flags = flags_of(b);
+        sk.info = nullptr;  // set per run
+        sk.info_stride = 0;
+        sk.last = slot_of(b, i);
+        sk.s = S[i].s;
+        sk.m = S[i].m;
     }
-    bytes.resize(sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C + sizeof(BatchTerm<T>) * terms.size());
+    // [residual x C][stats x C][single terms][pad to 64 bytes][two-term]
+    const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
+    b->pair_table_offset = align64(head + sizeof(BatchTerm<T>) * singles.size());
+    bytes.assign(b->pair_table_offset + sizeof(BatchPair<T>) * pairs.size(), 0);
     char* p = bytes.data();
     std::memcpy(p, res.data(), sizeof(BatchResidual<T>) * C);
-    p += sizeof(BatchResidual<T>) * C;
-    std::memcpy(p, st.data(), sizeof(BatchStats) * C);
-    p += sizeof(BatchStats) * C;
-    std::memcpy(p, terms.data(), sizeof(BatchTerm<T>) * terms.size());
+    std::memcpy(p + sizeof(BatchResidual<T>) * C, stv.data(), sizeof(BatchStats) * C);
+    if (!singles.empty()) std::memcpy(p + head, singles.data(), sizeof(BatchTerm<T>) * singles.size());
+    if (!pairs.empty()) std::memcpy(p + b->pair_table_offset, pairs.data(), sizeof(BatchPair<T>) * pairs.size());
     return ET_OK;
+}
+
+// The launches of launch index l from a table at dtab (single terms at
+// dtab + head, two-term descriptors at dtab + pair_table_offset).
+template <typename T>
+cudaError_t launch_index(et_batch* b, const char* dsingles, const char* dpairs, int l, int variant, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (b->single_count[l] > 0)
+        e = launch_batch_term(b->op, single_variant(b->prec, variant),
+                              reinterpret_cast<const BatchTerm<T>*>(dsingles) + b->single_first[l], b->single_count[l],
+                              b->single_tiles[l], b->sms, st);
+    if constexpr (!std::is_same<T, double>::value) {
+        if (e == cudaSuccess && b->pair_count[l] > 0)
+            e = launch_batch_term_pair<T>(b->op, reinterpret_cast<const BatchPair<T>*>(dpairs) + b->pair_first[l],
+                                          b->pair_count[l], b->pair_tiles[l], b->sms, flags_of(b), st);
+    }
+    return e;
 }
 
 template <typename T>
@@ -320,14 +366,13 @@ et_status enqueue_batch_step(et_batch* b, char* dtab, cudaStream_t st) {
     const int C = b->count;
     const BatchResidual<T>* res = (const BatchResidual<T>*)dtab;
     const BatchStats* sts = (const BatchStats*)(dtab + sizeof(BatchResidual<T>) * C);
-    const BatchTerm<T>* terms = (const BatchTerm<T>*)(dtab + sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C);
+    const char* dsingles = dtab + sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
+    const char* dpairs = dtab + b->pair_table_offset;
     cudaError_t e = launch_batch_residual<T>(b->op, (int)b->scheme, res, C, b->res_tiles, flags_of(b), st);
     if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched residual: %s", cudaGetErrorString(e));
-    long long off = 0;
-    for (int t = 0; t < b->nlaunch; ++t) {
-        e = launch_batch_term(b->op, b->table_variant, terms + off, b->launch_count[t], b->launch_tiles[t], b->sms, st);
+    for (int l = 0; l < b->nlaunch; ++l) {
+        e = launch_index<T>(b, dsingles, dpairs, l, b->table_variant, st);
         if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched term: %s", cudaGetErrorString(e));
-        off += b->launch_count[t];
     }
     e = launch_batch_stats(sts, C, st);
     if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched stats: %s", cudaGetErrorString(e));
@@ -353,41 +398,67 @@ et_status upload_tables(et_batch* b, double* u, double tau, int variant, et_step
     return ET_OK;
 }
 
-// Times one launch of the first (largest) term index for every kernel variant
-// and keeps the fastest.
+// Times the first launch index (every grid's first single or two-term launch)
+// for every kernel variant, scores it per Taylor term advanced, and keeps the
+// fastest.  us_out[v]: microseconds per term of the batch.
 template <typename T>
 et_status autotune(et_batch* b, double tau, double* us_out) {
-    const int nv = batch_variant_count(b->prec);
+    const int nv = total_variants(b->prec);
     cudaEvent_t e0, e1;
     BT_CUDA(b, cudaEventCreate(&e0));
     BT_CUDA(b, cudaEventCreate(&e1));
     double best = 1e300;
     int best_v = 0;
+    const int C = b->count;
+    const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
     for (int v = 0; v < nv; ++v) {
-        // tables of the first term launch only, with u redirected to the staging field
+        // tables with the step result redirected to the staging field
         std::vector<char> bytes;
         et_status rc = build_tables<T>(b, field<double>(b, b->L.stage, 0), tau, v, bytes, true);
-        if (rc != ET_OK) break;
-        const int C = b->count;
-        const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
-        const size_t n0 = sizeof(BatchTerm<T>) * b->launch_count[0];
+        if (rc != ET_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+        // the descriptors of launch index 0 only
+        const size_t ns = sizeof(BatchTerm<T>) * b->single_count[0];
+        const size_t np = pair_desc_bytes(b->prec) * b->pair_count[0];
         char* dst = b->ws + b->L.tune_desc;
-        cudaError_t ce = cudaMemcpyAsync(dst, bytes.data() + head, n0, cudaMemcpyHostToDevice, b->stream);
+        const size_t poff = align64(ns);
+        cudaError_t ce = cudaSuccess;
+        if (ns) ce = cudaMemcpyAsync(dst, bytes.data() + head + sizeof(BatchTerm<T>) * b->single_first[0], ns,
+                                     cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess && np)
+            ce = cudaMemcpyAsync(dst + poff, bytes.data() + b->pair_table_offset, np, cudaMemcpyHostToDevice,
+                                 b->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
-        const BatchTerm<T>* d = (const BatchTerm<T>*)dst;
+        // voxel-terms advanced by launch index 0
+        double vterms = 0.0, voxels = 0.0;
+        for (int i = 0; i < C; ++i) voxels += (double)geom_of(b, i).n;
+        {
+            const BatchTerm<T>* sd = reinterpret_cast<const BatchTerm<T>*>(bytes.data() + head);
+            for (int q = 0; q < b->single_count[0]; ++q) vterms += (double)sd[q].G.n;
+            if constexpr (!std::is_same<T, double>::value) {
+                const BatchPair<T>* pd = reinterpret_cast<const BatchPair<T>*>(bytes.data() + b->pair_table_offset);
+                for (int q = 0; q < b->pair_count[0]; ++q) vterms += 2.0 * (double)pd[q].G.n;
+            }
+        }
+        // launch_index reads single_first / pair_first: point them at the copies
+        b->single_first[0] = 0;
+        b->pair_first[0] = 0;
         float ms = 0.f;
         for (int r = 0; r < 4 && ce == cudaSuccess; ++r) {  // one warm-up launch, then three timed
             if (r == 1) ce = cudaEventRecord(e0, b->stream);
-            if (ce == cudaSuccess)
-                ce = launch_batch_term(b->op, v, d, b->launch_count[0], b->launch_tiles[0], b->sms, b->stream);
+            if (ce == cudaSuccess) ce = launch_index<T>(b, dst, dst + poff, 0, v, b->stream);
         }
         if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
-        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return bfail(b, ET_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(cudaGetLastError()));
         }
-        const double us = ms * 1e3 / 3.0;
+        const double us = ms * 1e3 / 3.0 * (vterms > 0.0 ? voxels / vterms : 1.0);
         if (us_out) us_out[v] = us;
         if (us < best) {
             best = us;
@@ -510,9 +581,24 @@ et_status et_batch_create(int count, const int* dims, double h, et_precision pre
     b->exec = nullptr;
     b->variant = -1;
     b->err[0] = 0;
+    b->pair_table_offset = 0;
+    b->pair_plans.assign(count, nullptr);
+    if (precision != ET_F64) {
+        // tensor maps of every grid's fields for the two-term kernel (nullptr:
+        // its rows are not a 16-byte multiple, or its fields are not 16-byte
+        // aligned in the concatenated layout; that grid runs one term per launch)
+        const size_t es = value_bytes(precision);
+        for (int i = 0; i < count; ++i) {
+            auto at = [&](size_t region) { return (const void*)(b->ws + region + es * (size_t)offs[i]); };
+            const void* wt4[4] = {at(L.wt[0]), at(L.wt[1]), at(L.wt[2]), at(L.wt[3])};
+            const void* yz[4] = {at(L.vec[2]), at(L.vec[3]), at(L.vec[4]), at(L.vec[5])};
+            b->pair_plans[i] = pair_plan_create(geom_of(b, i), precision, wt4, at(L.vec[0]), at(L.vec[1]), yz);
+        }
+    }
     if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
         prime_launch_limits() != cudaSuccess ||
         cudaMemsetAsync(b->ws + L.misc, 0, misc_bytes(count), b->stream) != cudaSuccess) {
+        for (PairPlan* P : b->pair_plans) pair_plan_destroy(P);
         delete b;
         return bfail(nullptr, ET_ERR_CUDA, "batch set-up failed");
     }
@@ -620,7 +706,7 @@ et_status et_batch_autotune(et_batch* b, double tau, int* variant, double* us_pe
 
 et_status et_batch_set_variant(et_batch* b, int variant) {
     if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
-    if (variant < 0 || variant >= batch_variant_count(b->prec)) return bfail(b, ET_ERR_ARG, "no variant %d", variant);
+    if (variant < 0 || variant >= total_variants(b->prec)) return bfail(b, ET_ERR_ARG, "no variant %d", variant);
     BDeviceGuard dg(b->device);
     clear_graph(b);
     b->variant = variant;
@@ -630,7 +716,7 @@ et_status et_batch_set_variant(et_batch* b, int variant) {
 
 int et_batch_variant_count(et_precision precision) {
     if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64) return 0;
-    return batch_variant_count(precision);
+    return total_variants(precision);
 }
 
 et_status et_batch_sync_info(et_batch* b, et_step_info* host_out) {
@@ -676,6 +762,7 @@ void et_batch_destroy(et_batch* b) {
         clear_graph(b);
         if (b->capture) cudaStreamDestroy(b->capture);
     }
+    for (PairPlan* P : b->pair_plans) pair_plan_destroy(P);
     delete b;
 }
 

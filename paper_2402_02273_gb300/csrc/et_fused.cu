@@ -49,11 +49,6 @@ struct PairPlan {
 
 namespace {
 
-// Tensor maps of one launch (kernel parameter).
-struct PairMaps {
-    CUtensorMap zj, w0, w1, w2, dt, b, w3;
-};
-
 constexpr int kPairThreads = 352;       // 11 warps: one per voxel of the 34 x 10 halo plane
 constexpr int kHaloX = kBlockX + 2;     // 34
 constexpr int kHaloY = kBlockY + 2;     // 10
@@ -150,7 +145,8 @@ struct Arith<float2> {
 // Kernel variants: Horner pair (sub-step 0) or running-sum pair; the first
 // term scaled by zscale; the sum's base read from z_j itself (first term of a
 // later sub-step) instead of the running sum.
-enum : int { kModeHorner = 1, kModeZscale = 2, kModeBaseZ = 4 };
+// kModeTable: the term shapes are read per grid (batched launches).
+enum : int { kModeHorner = 1, kModeZscale = 2, kModeBaseZ = 4, kModeTable = 8 };
 
 // ---- mbarrier and TMA (inline PTX) -----------------------------------------
 
@@ -196,18 +192,81 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int 
 
 // ---- the kernel --------------------------------------------------------------
 
-// FP32: 4 blocks per SM fit the shared memory (46 registers a thread); DF64: 2.
-template <int OP, typename T, int MODE>
-__global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 4 : 2)
-term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
-             const __grid_constant__ TermArgs<T> a1, const __grid_constant__ TermArgs<T> a2, int tz,
-             unsigned* flags) {
+// Where the tiles of a launch come from: one grid (kernel parameters) or a
+// table of grids (the batched form), tiles numbered grid after grid.
+template <typename T>
+struct OneGrid {
+    const PairMaps* M;
+    const Geom* G;
+    const TermArgs<T>* a1;
+    const TermArgs<T>* a2;
+    int tz;
+    long long total;
+    __device__ __forceinline__ int find(long long) const { return 0; }
+    __device__ __forceinline__ const PairMaps* maps(int) const { return M; }
+    __device__ __forceinline__ const Geom& geom(int) const { return *G; }
+    __device__ __forceinline__ const TermArgs<T>& first(int) const { return *a1; }
+    __device__ __forceinline__ const TermArgs<T>& second(int) const { return *a2; }
+    __device__ __forceinline__ int planes(int) const { return tz; }
+    __device__ __forceinline__ long long begin(int) const { return 0; }
+};
+
+template <typename T>
+struct GridTable {
+    const BatchPair<T>* d;
+    int count;
+    long long total;
+    __device__ __forceinline__ int find(long long tile) const {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ const PairMaps* maps(int i) const { return &d[i].M; }
+    __device__ __forceinline__ const Geom& geom(int i) const { return d[i].G; }
+    __device__ __forceinline__ const TermArgs<T>& first(int i) const { return d[i].a1; }
+    __device__ __forceinline__ const TermArgs<T>& second(int i) const { return d[i].a2; }
+    __device__ __forceinline__ int planes(int i) const { return d[i].tz; }
+    __device__ __forceinline__ long long begin(int i) const { return d[i].tile_begin; }
+};
+
+// A tile: its grid's geometry and its place in it.
+struct TileGeom {
+    int nx, ny, nz;
+    long long sy, sz;
+    int x0, y0, k0, k1;
+};
+
+template <typename Src>
+__device__ __forceinline__ TileGeom tile_of(const Src& src, int gi, long long tile) {
+    const Geom& G = src.geom(gi);
+    TileGeom g;
+    g.nx = G.nx;
+    g.ny = G.ny;
+    g.nz = G.nz;
+    g.sy = G.sy;
+    g.sz = G.sz;
+    const int tz = src.planes(gi);
+    const int tiles_x = (g.nx + kBlockX - 1) / kBlockX;
+    const int tiles_y = (g.ny + kBlockY - 1) / kBlockY;
+    const long long lt = tile - src.begin(gi);
+    g.x0 = (int)(lt % tiles_x) * kBlockX;
+    const long long rest = lt / tiles_x;
+    g.y0 = (int)(rest % tiles_y) * kBlockY;
+    g.k0 = (int)(rest / tiles_y) * tz;
+    g.k1 = min(g.k0 + tz, g.nz);
+    return g;
+}
+
+template <int OP, typename T, int MODE, typename Src>
+__device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
     using S = Shape<T>;
     using A = Arith<T>;
     constexpr bool kLit = OP == ET_OP_LITERAL;
-    constexpr bool kHorner = (MODE & kModeHorner) != 0;
-    constexpr bool kZs = (MODE & kModeZscale) != 0;
-    constexpr bool kBaseZ = (MODE & kModeBaseZ) != 0;
+    constexpr bool kTable = (MODE & kModeTable) != 0;
     constexpr int BX = S::BX, XO = S::XO;
     constexpr int kStageBytes = S::stage_bytes(kLit);
     constexpr unsigned kTx = S::tx_bytes(kLit);
@@ -221,16 +280,6 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
         mbar_fence_init();
     }
     __syncthreads();
-
-    // everything the loop needs from the parameters, in registers
-    const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
-    const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
-    const T* const ysrc = a1.yacc;
-    T* const zout = a2.zout;
-    T* const yout = a2.yacc;
-    double* const uout = a2.u;
-    const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const long long sy = G.sy, sz = G.sz;
     const T zero = A::zero();
 
     // first-term voxel of this thread on the halo plane, second-term voxel inside
@@ -251,47 +300,44 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
     int islot = 0, wslot = 0;
     unsigned wpar = 0;
     const unsigned char *s3 = nullptr, *s2 = nullptr, *sp = nullptr, *sc = nullptr;  // planes L - 3 .. L
+    const long long total = src.total;
 
-    const int tiles_x = (nx + kBlockX - 1) / kBlockX;
-    const int tiles_y = (ny + kBlockY - 1) / kBlockY;
-    const int ntiles = tiles_x * tiles_y * ((nz + tz - 1) / tz);
-    auto tile_geom = [&](int tile, int& x0, int& y0, int& k0, int& k1) {
-        x0 = (tile % tiles_x) * kBlockX;
-        const int rest = tile / tiles_x;
-        y0 = (rest % tiles_y) * kBlockY;
-        k0 = (rest / tiles_y) * tz;
-        k1 = min(k0 + tz, nz);
-    };
     // The block's tiles (blockIdx.x, + gridDim.x, ...) form one stream of
     // stages, planes k0 - 2 .. k1 + 1 of each; loads run kPrefetch stages ahead
-    // in that stream, across tile boundaries.
-    int itile = blockIdx.x, ix0 = 0, iy0 = 0, ik0 = 0, ik1 = 0, iq = 0;
-    if (itile < ntiles) {
-        tile_geom(itile, ix0, iy0, ik0, ik1);
-        iq = ik0 - 2;
-    }
+    // in that stream, across tile (and grid) boundaries.
+    long long itile = blockIdx.x;
+    const PairMaps* iM = nullptr;
+    int ix0 = 0, iy0 = 0, ik1 = 0, iq = 0;
+    auto issue_tile = [&]() {
+        if (itile >= total) return;
+        const int gi = src.find(itile);
+        const TileGeom g = tile_of(src, gi, itile);
+        iM = src.maps(gi);
+        ix0 = g.x0;
+        iy0 = g.y0;
+        ik1 = g.k1;
+        iq = g.k0 - 2;
+    };
+    issue_tile();
     auto issue_next = [&]() {
-        if (itile >= ntiles) return;
+        if (itile >= total) return;
         if (t == 0) {
             unsigned char* st = base + islot * kStageBytes;
             uint64_t* bar = &full[islot];
             mbar_expect_tx(bar, kTx);
-            tma_load(st + S::kZj, &M.zj, ix0 - XO, iy0 - 2, iq, bar);
-            tma_load(st + S::kW1, &M.w1, ix0 - XO, iy0 - 2, iq, bar);
-            tma_load(st + S::kW0, &M.w0, ix0 - XO, iy0 - 1, iq, bar);
-            tma_load(st + S::kW2, &M.w2, ix0 - XO, iy0 - 1, iq, bar);
-            tma_load(st + S::kDt, &M.dt, ix0 - XO, iy0 - 1, iq, bar);
-            tma_load(st + S::kB, &M.b, ix0 - XO, iy0 - 1, iq, bar);
-            if (kLit) tma_load(st + S::kW3, &M.w3, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kZj, &iM->zj, ix0 - XO, iy0 - 2, iq, bar);
+            tma_load(st + S::kW1, &iM->w1, ix0 - XO, iy0 - 2, iq, bar);
+            tma_load(st + S::kW0, &iM->w0, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kW2, &iM->w2, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kDt, &iM->dt, ix0 - XO, iy0 - 1, iq, bar);
+            tma_load(st + S::kB, &iM->b, ix0 - XO, iy0 - 1, iq, bar);
+            if (kLit) tma_load(st + S::kW3, &iM->w3, ix0 - XO, iy0 - 1, iq, bar);
         }
         ++issued;
         if (++islot == kStages) islot = 0;
         if (++iq > ik1 + 1) {
             itile += gridDim.x;
-            if (itile < ntiles) {
-                tile_geom(itile, ix0, iy0, ik0, ik1);
-                iq = ik0 - 2;
-            }
+            issue_tile();
         }
     };
     // next plane: issue one more stage of the stream, wait for this one
@@ -319,13 +365,27 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
     };
 
     for (int d = 0; d < kPrefetch; ++d) issue_next();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int x0, y0, k0, k1;
-        tile_geom(tile, x0, y0, k0, k1);
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int gi = src.find(tile);
+        const TileGeom g = tile_of(src, gi, tile);
+        const TermArgs<T>& a1 = src.first(gi);
+        const TermArgs<T>& a2 = src.second(gi);
+        // the terms' scalars and outputs, in registers
+        const bool kHorner = kTable ? a1.horner != 0 : (MODE & kModeHorner) != 0;
+        const bool kZs = kTable ? a1.has_zscale != 0 : (MODE & kModeZscale) != 0;
+        const bool kBaseZ = kTable ? a1.base_mode == 2 : (MODE & kModeBaseZ) != 0;
+        const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
+        const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
+        const T* const ysrc = a1.yacc;
+        T* const zout = a2.zout;
+        T* const yout = a2.yacc;
+        double* const uout = a2.u;
+        const int k0 = g.k0, k1 = g.k1;
         const int Llast = k1 + 1;  // planes k0 - 2 .. k1 + 1 are loaded
-        const int gx = x0 + cx, gy = y0 + cy;
-        const bool store_c = has_c && gx < nx && gy < ny;
-        const long long pc = gx + sy * gy;  // column offset of the second-term voxel
+        const int gx = g.x0 + cx, gy = g.y0 + cy;
+        const bool store_c = has_c && gx < g.nx && gy < g.ny;
+        const long long pc = gx + g.sy * gy;  // column offset of the second-term voxel
+        const long long sz = g.sz;
 
         T b_zm = zero, b_w2m = zero;  // z_j and w2 of the plane below, at the halo voxel
         T c_w2m = zero;               // w2 of the plane below, at the interior voxel
@@ -353,9 +413,16 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
             }
             const T bval = hb1 ? reinterpret_cast<const T*>(sp + S::kB)[b10] : zero;
             const T wzp = W2[b10];
-            za[(q & 3) * kHalo + t] =
-                A::template stencil<kZs>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11], Zp[bz + BX],
-                                         wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1, beta1, bval);
+            T v;
+            if (kZs)
+                v = A::template stencil<true>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
+                                              Zp[bz + BX], wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1,
+                                              beta1, bval);
+            else
+                v = A::template stencil<false>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
+                                               Zp[bz + BX], wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1,
+                                               beta1, bval);
+            za[(q & 3) * kHalo + t] = v;
             b_zm = zc;
             b_w2m = wzp;
         };
@@ -446,20 +513,45 @@ term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
     }
 }
 
+// Resident blocks per SM that the shared memory allows: FP32 3, DF64 2.
+template <int OP, typename T, int MODE>
+__global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 3 : 2)
+term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
+             const __grid_constant__ TermArgs<T> a1, const __grid_constant__ TermArgs<T> a2, int tz,
+             unsigned* flags) {
+    const long long total = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
+                            ((G.nz + tz - 1) / tz);
+    const OneGrid<T> src{&M, &G, &a1, &a2, tz, total};
+    pair_body<OP, T, MODE>(src, flags);
+}
+
+template <int OP, typename T>
+__global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 3 : 2)
+batch_term2_kernel(const BatchPair<T>* __restrict__ d, int count, long long total, unsigned* flags) {
+    const GridTable<T> src{d, count, total};
+    pair_body<OP, T, kModeTable>(src, flags);
+}
+
+template <typename K>
+int blocks_per_sm_of(K kernel, int smem) {
+    int b = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kPairThreads, smem) != cudaSuccess || b < 1)
+        b = 1;
+    return b;
+}
+
 template <int OP, typename T, int MODE>
 int pair_blocks_per_sm() {
     static int cached = 0;
-    if (!cached) {
-        int b = 0;
-        const int smem = Shape<T>::smem_bytes(OP == ET_OP_LITERAL);
-        if (cudaFuncSetAttribute(term2_kernel<OP, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, term2_kernel<OP, T, MODE>, kPairThreads, smem) !=
-                cudaSuccess ||
-            b < 1)
-            b = 1;
-        cached = b;
-    }
+    if (!cached) cached = blocks_per_sm_of(term2_kernel<OP, T, MODE>, Shape<T>::smem_bytes(OP == ET_OP_LITERAL));
+    return cached;
+}
+
+template <int OP, typename T>
+int batch_pair_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) cached = blocks_per_sm_of(batch_term2_kernel<OP, T>, Shape<T>::smem_bytes(OP == ET_OP_LITERAL));
     return cached;
 }
 
@@ -513,6 +605,13 @@ bool encode(CUtensorMap* m, const void* ptr, const Geom& G, int es, int bx, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The pair kernel covers the term shapes the chain planner emits.
+template <typename T>
+bool pair_shape_ok(const TermArgs<T>& a1, const TermArgs<T>& a2) {
+    if (a1.last || a2.has_zscale || a1.horner != a2.horner) return false;
+    return a1.horner || (a2.base_mode == 0 && (a1.base_mode == 0 || a1.base_mode == 2));
+}
+
 template <int OP, typename T, int MODE>
 cudaError_t launch_pair_mode(const PairMaps& M, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
                              unsigned* flags, cudaStream_t stream) {
@@ -529,21 +628,9 @@ cudaError_t launch_pair_mode(const PairMaps& M, const Geom& G, const TermArgs<T>
 template <int OP, typename T>
 cudaError_t launch_pair_op(const PairPlan* P, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
                            unsigned* flags, cudaStream_t stream) {
-    // the pair kernel covers the term shapes the chain planner emits
-    if (a1.last || a2.has_zscale || a1.horner != a2.horner) return cudaErrorInvalidValue;
-    if (!a1.horner && (a2.base_mode != 0 || (a1.base_mode != 0 && a1.base_mode != 2))) return cudaErrorInvalidValue;
+    if (!pair_shape_ok(a1, a2)) return cudaErrorInvalidValue;
     PairMaps M;
-    int zi = -1;
-    for (int i = 0; i < 5; ++i)
-        if (P->zj_ptr[i] == static_cast<const void*>(a1.zin)) zi = i;
-    if (zi < 0) return cudaErrorInvalidValue;
-    M.zj = P->zj[zi];
-    M.w0 = P->w0;
-    M.w1 = P->w1;
-    M.w2 = P->w2;
-    M.dt = P->dt;
-    M.b = P->b;
-    M.w3 = P->w3;
+    if (!pair_maps(P, a1.zin, &M)) return cudaErrorInvalidValue;
     if (a1.horner) {
         if (a1.has_zscale) return launch_pair_mode<OP, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream);
         return launch_pair_mode<OP, T, kModeHorner>(M, G, a1, a2, flags, stream);
@@ -558,6 +645,7 @@ cudaError_t launch_pair_op(const PairPlan* P, const Geom& G, const TermArgs<T>& 
 
 template <int OP, typename T>
 void prime_pair() {
+    batch_pair_blocks_per_sm<OP, T>();
     pair_blocks_per_sm<OP, T, kModeHorner>();
     pair_blocks_per_sm<OP, T, kModeHorner | kModeZscale>();
     pair_blocks_per_sm<OP, T, kModeZscale | kModeBaseZ>();
@@ -596,6 +684,46 @@ PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const w
 }
 
 void pair_plan_destroy(PairPlan* P) { delete P; }
+
+bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out) {
+    if (!P) return false;
+    int zi = -1;
+    for (int i = 0; i < 5; ++i)
+        if (P->zj_ptr[i] == zin) zi = i;
+    if (zi < 0) return false;
+    out->zj = P->zj[zi];
+    out->w0 = P->w0;
+    out->w1 = P->w1;
+    out->w2 = P->w2;
+    out->dt = P->dt;
+    out->b = P->b;
+    out->w3 = P->w3;
+    return true;
+}
+
+// Batched launches hold many grids, so every block has several tiles even
+// with whole columns: segments of up to 64 planes.
+int batch_pair_tz(const Geom& G) { return G.nz < 64 ? (G.nz > 0 ? G.nz : 1) : 64; }
+
+template <typename T>
+cudaError_t launch_batch_term_pair(et_operator op, const BatchPair<T>* d, int count, long long tiles, int sms,
+                                   unsigned* flags, cudaStream_t stream) {
+    const int smem = Shape<T>::smem_bytes(op == ET_OP_LITERAL);
+    const int per_sm = op == ET_OP_CONSERVATIVE ? batch_pair_blocks_per_sm<ET_OP_CONSERVATIVE, T>()
+                                                : batch_pair_blocks_per_sm<ET_OP_LITERAL, T>();
+    const long long cap = (long long)(sms > 0 ? sms : 1) * per_sm;
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    if (op == ET_OP_CONSERVATIVE)
+        batch_term2_kernel<ET_OP_CONSERVATIVE, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags);
+    else
+        batch_term2_kernel<ET_OP_LITERAL, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_term_pair<float>(et_operator, const BatchPair<float>*, int, long long, int,
+                                                   unsigned*, cudaStream_t);
+template cudaError_t launch_batch_term_pair<float2>(et_operator, const BatchPair<float2>*, int, long long, int,
+                                                    unsigned*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,

@@ -2,6 +2,7 @@
 // (et_kernels.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -193,6 +194,22 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermA
 // double-float form (et_df64.cu)
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const TermArgs<float2>& a,
                         cudaStream_t stream);
+// Tensor maps of the two-term kernel for one grid and launch (et_fused.cu):
+// z_j with a two-voxel halo, the weights, the diagonal and b.
+struct PairMaps {
+    CUtensorMap zj, w0, w1, w2, dt, b, w3;
+};
+
+// One grid of a batched two-term launch.
+template <typename T>
+struct BatchPair {
+    PairMaps M;
+    Geom G;
+    TermArgs<T> a1, a2;
+    long long tile_begin;
+    int tz;  // planes per column segment
+};
+
 // Two consecutive terms of one sub-step (a1 not last) in one TMA-fed launch
 // (et_fused.cu): a1's outputs are not written, a2's are.  The plan holds the
 // tensor maps of one grid's fields: typed weights wt[0..3], b, the diagonal
@@ -205,6 +222,15 @@ void pair_plan_destroy(PairPlan* P);
 template <typename T>
 cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
                              const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
+// Fills the tensor maps of a pair launch (a1.zin selects the z_j map); false
+// if a1.zin is none of the plan's vectors.
+bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out);
+// Planes per column segment of a grid in a batched launch.
+int batch_pair_tz(const Geom& G);
+// Batched two-term launch over count grids (device table d, tiles in all).
+template <typename T>
+cudaError_t launch_batch_term_pair(et_operator op, const BatchPair<T>* d, int count, long long tiles, int sms,
+                                   unsigned* flags, cudaStream_t stream);
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
 // Adjoint launchers (et_adjoint.cu).

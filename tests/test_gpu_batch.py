@@ -246,3 +246,34 @@ def test_batch_forced_schedule_and_option_checks(et_mod, torch_cuda):
     B = et_mod.Batch(SHAPES)
     with pytest.raises(et_mod.EtError):
         B.set_coeffs(_concat(torch, Ds), RHOS, force_m=1)
+
+
+# Grids whose rows are 16-byte multiples in both FP32 and DF64 and whose
+# fields stay 16-byte aligned in the concatenated layout: every grid can take
+# the two-term launches (nz = 70 spans two column segments).
+PAIR_SHAPES = [(70, 20, 36), (16, 9, 64), (33, 40, 40), (5, 3, 8)]
+PAIR_RHOS = [0.025, 0.04, 0.015, 0.03]
+
+
+@pytest.mark.parametrize("precision", ["f32", "df64"])
+def test_two_term_batch_matches_single_grids_bitwise(et_mod, torch_cuda, precision):
+    Ds, us = [], []
+    for i, sh in enumerate(PAIR_SHAPES):
+        D, u0 = phantom.case(sh, seed=20 + i, noise=0.1)
+        if not np.any(u0 > 0.1):
+            u0 = np.zeros(sh)
+            u0.reshape(-1)[u0.size // 2] = 0.8
+        Ds.append(D)
+        us.append(u0)
+    nsteps = 3
+    nvar = et_mod.load().et_batch_variant_count(et_mod.PRECISIONS[precision])
+    for v in range(nvar // 2):  # the two-term variants
+        B, got, recs, _ = _batch_run(et_mod, torch_cuda, PAIR_SHAPES, Ds, us, PAIR_RHOS, nsteps, precision,
+                                     variant=v)
+        for i in range(len(PAIR_SHAPES)):
+            want, rec = _single_run(et_mod, torch_cuda, Ds[i], us[i], PAIR_RHOS[i], nsteps, precision)
+            assert np.array_equal(got[i], want), (v, i, np.abs(got[i] - want).max())
+            if precision == "df64":
+                ref = oracle.Problem(Ds[i], rho=PAIR_RHOS[i]).run(us[i], TAU, nsteps)[0]
+                e_max, e_l2 = _errs(got[i], ref)
+                assert e_max <= TOL64 and e_l2 <= TOL64, (v, i, e_max, e_l2)

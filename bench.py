@@ -65,9 +65,9 @@ def launch_mix(prec, s, m, pairs):
 
 
 # DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of the current kernels (cold cache); None where the kernel
-# changed after the capture.
-TERM_TRAFFIC = {"f64": 107.5e6, "df64": None, "f32": None}
+# from one ncu capture of the current kernels (cold cache; DF64 and FP32 launches
+# cover two terms); None where the kernel changed after the capture.
+TERM_TRAFFIC = {"f64": 107.7e6, "df64": 115.6e6, "f32": 50.7e6}
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
@@ -326,7 +326,7 @@ def main():
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         value = whole_job_rate(world, n, args.nsteps, ms)
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
-        traffic = TERM_TRAFFIC.get(prec) if args.grid == N_GRID else None
+        traffic = TERM_TRAFFIC.get(prec) if (args.grid == N_GRID and (prec == "f64" or not args.single_terms)) else None
         alu_frac = achieved_tflops / alu_peak
         hbm_frac = achieved_gbs / hbm_peak
         if prec == "f64" and alu_frac >= hbm_frac:

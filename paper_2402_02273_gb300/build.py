@@ -10,6 +10,7 @@ import concurrent.futures
 import os
 import shutil
 import subprocess
+import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -43,6 +44,11 @@ def _stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
+def _crashed(r) -> bool:
+    text = (r.stdout or "") + (r.stderr or "")
+    return r.returncode < 0 or "Segmentation fault" in text or "Killed" in text or "core dumped" in text
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if stale) and return the path of libet.so."""
     if not force and not _stale():
@@ -52,10 +58,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "-I" + INCLUDE, "-I" + CSRC]
 
+    retry_lock = threading.Lock()
+
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         cmd = [cc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
+        # a compiler process that crashed (signal, or a crash message) is run
+        # again, one such retry at a time, so that it has the machine's memory
+        for _ in range(2):
+            if r.returncode == 0 or not _crashed(r):
+                break
+            with retry_lock:
+                r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):

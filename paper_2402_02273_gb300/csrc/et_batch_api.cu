@@ -730,6 +730,7 @@ et_status et_batch_sync_info(et_batch* b, et_step_info* host_out) {
     BT_CUDA(b, cudaStreamSynchronize(b->stream));
     BT_CUDA(b, cudaMemsetAsync(flags_of(b), 0, sizeof(unsigned), b->stream));
     if (host_out) std::memcpy(host_out, rec.data(), sizeof(et_step_info) * b->count);
+    if (flags & ET_FLAG_TIMEOUT) return bfail(b, ET_ERR_TIMEOUT, "a device-side wait ran out; the run is not valid");
     if (flags & ET_FLAG_NONFINITE) return bfail(b, ET_ERR_NUMERIC, "non-finite density met");
     if (flags & ET_FLAG_RANGE_IN) return bfail(b, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3)");
     return ET_OK;

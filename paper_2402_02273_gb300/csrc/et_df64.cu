@@ -80,22 +80,11 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
         const float2 wxm = (OP == ET_OP_CONSERVATIVE) ? cur.wxm : (xm ? cur.w3 : zero);
         const float2 wym = (OP == ET_OP_CONSERVATIVE) ? cur.wym : (ym ? cur.w3 : zero);
         const float2 wzm = (OP == ET_OP_CONSERVATIVE) ? wzm_c : ((k > 0) ? cur.w3 : zero);
-        DotAcc A;
-        dot_first(A, cur.dt, zc);
-        dot_add(A, cur.wxp, cur.zxp);
-        dot_add(A, wxm, cur.zxm);
-        dot_add(A, cur.wyp, cur.zyp);
-        dot_add(A, wym, cur.zym);
-        dot_add(A, cur.wzp, cur.zp);
-        dot_add(A, wzm, zm);
-        float2 acc;
-        if (!a.has_zscale) {
-            if (a.has_beta) dot_add(A, a.beta, cur.bb);
-            acc = dot_result(A);
-        } else {
-            acc = df_mul(a.zscale, dot_result(A));
-            if (a.has_beta) acc = df_fma(a.beta, cur.bb, acc);
-        }
+        const float2 acc =
+            a.has_zscale ? stencil<true>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
+                                         cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb)
+                         : stencil<false>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
+                                          cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb);
         if (a.horner) {
             if (!a.last) {
                 zout[p] = acc;

@@ -66,5 +66,41 @@ __device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
     return dot_result(A);
 }
 
+// Merges two compensated accumulators into A.
+__device__ __forceinline__ void dot_merge(DotAcc& A, const DotAcc& B) {
+    float s, e;
+    two_sum(A.s, B.s, s, e);
+    A.s = s;
+    A.c = __fadd_rn(__fadd_rn(A.c, B.c), e);
+}
+
+// One Taylor term at a voxel: the 7-point stencil of the normalised operator
+// on z (diagonal dt, weights towards +x, -x, +y, -y, +z, -z), optionally
+// scaled by zscale, plus beta * b.  The eight products are summed in two
+// independent compensated halves that are merged at the end, which halves the
+// chain of dependent additions.
+template <bool ZS>
+__device__ __forceinline__ float2 stencil(float2 dt, float2 zc, float2 wxp, float2 zxp, float2 wxm, float2 zxm,
+                                          float2 wyp, float2 zyp, float2 wym, float2 zym, float2 wzp, float2 zp,
+                                          float2 wzm, float2 zm, float2 zscale, bool has_beta, float2 beta,
+                                          float2 bval) {
+    DotAcc A, B;
+    dot_first(A, dt, zc);
+    dot_first(B, wym, zym);
+    dot_add(A, wxp, zxp);
+    dot_add(B, wzp, zp);
+    dot_add(A, wxm, zxm);
+    dot_add(B, wzm, zm);
+    dot_add(A, wyp, zyp);
+    if (!ZS) {
+        if (has_beta) dot_add(B, beta, bval);
+        dot_merge(A, B);
+        return dot_result(A);
+    }
+    dot_merge(A, B);
+    const float2 acc = df_mul(zscale, dot_result(A));
+    return has_beta ? df_fma(beta, bval, acc) : acc;
+}
+
 }  // namespace df64
 }  // namespace et

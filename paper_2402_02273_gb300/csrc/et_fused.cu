@@ -56,7 +56,8 @@ constexpr int kHalo = kHaloX * kHaloY;  // 340
 constexpr int kPrefetch = 1;            // stages loaded ahead of the one consumed
 constexpr int kStages = kPrefetch + 4;  // + planes L - 3 (second term), L - 1, L (first term), L - 2
 constexpr int kRing = 4;                // z_a planes kept: the second term's three and the one being written
-constexpr int kWaitTries = 1 << 20;
+constexpr int kWaitTries = 1 << 24;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 template <typename T>
 struct Shape {
@@ -117,24 +118,8 @@ struct Arith<float2> {
                                                      float2 zxm, float2 wyp, float2 zyp, float2 wym, float2 zym,
                                                      float2 wzp, float2 zp, float2 wzm, float2 zm, float2 zscale,
                                                      bool has_beta, float2 beta, float2 bval) {
-        using namespace df64;
-        DotAcc A;
-        dot_first(A, dt, zc);
-        dot_add(A, wxp, zxp);
-        dot_add(A, wxm, zxm);
-        dot_add(A, wyp, zyp);
-        dot_add(A, wym, zym);
-        dot_add(A, wzp, zp);
-        dot_add(A, wzm, zm);
-        float2 acc;
-        if (!ZS) {
-            if (has_beta) dot_add(A, beta, bval);
-            acc = dot_result(A);
-        } else {
-            acc = df_mul(zscale, dot_result(A));
-            if (has_beta) acc = df_fma(beta, bval, acc);
-        }
-        return acc;
+        return df64::stencil<ZS>(dt, zc, wxp, zxp, wxm, zxm, wyp, zyp, wym, zym, wzp, zp, wzm, zm, zscale, has_beta,
+                                 beta, bval);
     }
     static __device__ __forceinline__ float2 axpy(float2 g, float2 x, float2 base) { return df64::df_fma(g, x, base); }
     static __device__ __forceinline__ float2 scale(float2 g, float2 x) { return df64::df_mul(g, x); }
@@ -175,10 +160,21 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete, for at most about
+// kWaitNs of the global timer (and kWaitTries polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (int i = 0; i < kWaitTries; ++i)
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kWaitTries; ++i) {
         if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 
@@ -635,10 +631,7 @@ cudaError_t launch_pair_op(const PairPlan* P, const Geom& G, const TermArgs<T>& 
         if (a1.has_zscale) return launch_pair_mode<OP, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream);
         return launch_pair_mode<OP, T, kModeHorner>(M, G, a1, a2, flags, stream);
     }
-    if (a1.has_zscale) {
-        if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeZscale | kModeBaseZ>(M, G, a1, a2, flags, stream);
-        return launch_pair_mode<OP, T, kModeZscale>(M, G, a1, a2, flags, stream);
-    }
+    if (a1.has_zscale) return cudaErrorInvalidValue;  // only the chain's first (Horner) term is scaled
     if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeBaseZ>(M, G, a1, a2, flags, stream);
     return launch_pair_mode<OP, T, 0>(M, G, a1, a2, flags, stream);
 }
@@ -648,8 +641,6 @@ void prime_pair() {
     batch_pair_blocks_per_sm<OP, T>();
     pair_blocks_per_sm<OP, T, kModeHorner>();
     pair_blocks_per_sm<OP, T, kModeHorner | kModeZscale>();
-    pair_blocks_per_sm<OP, T, kModeZscale | kModeBaseZ>();
-    pair_blocks_per_sm<OP, T, kModeZscale>();
     pair_blocks_per_sm<OP, T, kModeBaseZ>();
     pair_blocks_per_sm<OP, T, 0>();
 }

@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--nsteps", type=int, default=NSTEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint form")
+    ap.add_argument("--adjoint-forms", default="f64,f32")
     ap.add_argument("--no-forms", action="store_true", help="time the plain FP64 form only")
     ap.add_argument("--single-terms", action="store_true", help="one Taylor term per launch in every form")
     ap.add_argument("--no-batch", action="store_true", help="skip timing the batched many-grid form")
@@ -349,22 +350,26 @@ def main():
         del g
         torch.cuda.empty_cache()
 
-    # adjoint form: one gradient = forward run of ADJ_STEPS steps + et_vjp with
-    # checkpoints every ADJ_CK steps (the misfit cotangent u_K - u_target is the
-    # caller's, computed with one torch subtraction)
+    # adjoint form: one gradient = forward run of ADJ_STEPS steps keeping
+    # checkpoints every ADJ_CK steps + the reverse pass from them (the misfit
+    # cotangent u_K - u_target is the caller's, one torch subtraction)
     adjoint = {}
     if not args.no_adjoint and not args.no_forms:
-        for prec in ("f64", "f32"):
+        for prec in [f for f in args.adjoint_forms.split(",") if f]:
             g = et.Grid(D.shape, precision=prec, stream=stream)
             g.set_coeffs(torch.from_numpy(D).to("cuda"), rho=RHO)
             u0d = torch.from_numpy(u0).to("cuda")
             tgt = u0d * 0.5
             u = torch.empty_like(u0d)
 
+            ws = g.adjoint_workspace(TAU, ADJ_STEPS, ADJ_CK)
+
             def adj_step():
+                # one gradient: the forward run keeps the checkpoints, the
+                # reverse pass starts from them
                 u.copy_(u0d)
-                g.run(u, TAU, ADJ_STEPS)
-                g.vjp(u0d, TAU, ADJ_STEPS, u - tgt, ADJ_CK)
+                g.run_checkpointed(u, TAU, ADJ_STEPS, ADJ_CK, workspace=ws)
+                g.vjp_checkpointed(ws, TAU, ADJ_STEPS, u - tgt, ADJ_CK)
                 flush.add_(1)
 
             with torch.cuda.stream(stream):

@@ -214,8 +214,11 @@ ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_us
  * ubar_final = dJ/du^K for u^K = step^K(u0), returns dJ/du0 in ubar0, dJ/drho
  * in *grad_rho and d/ds J(s D)|_{s=1} (D scaled uniformly) in *grad_dscale.
  * Runs its own forward pass from u0 keeping u every checkpoint_every steps,
- * then recomputes each segment of steps and each step's Taylor terms while
- * reversing them.  ET_F64 and ET_F32 grids (ET_ERR_UNSUPPORTED for ET_DF64).
+ * then runs each segment forward once more, recording every step (its b,
+ * diagonal and Taylor terms), and reverses the segment's steps.  The workspace
+ * holds the checkpoints and one segment's records (about checkpoint_every x
+ * (s m + s + 3) vectors of the grid's precision).  ET_F64 and ET_F32 grids
+ * (ET_ERR_UNSUPPORTED for ET_DF64).
  *  u0, ubar_final, ubar0: device, n FP64 values (ubar0 may alias neither).
  *  workspace: device, >= et_vjp_workspace_bytes(...), 256-byte aligned.
  * Synchronises the stream (the two gradients are read back). */
@@ -223,6 +226,17 @@ ET_API size_t et_vjp_workspace_bytes(const et_grid* g, double tau, int nsteps, i
 ET_API et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int checkpoint_every,
                         const double* ubar_final, double* ubar0, double* grad_rho, double* grad_dscale,
                         void* workspace, size_t workspace_bytes);
+/* The same adjoint split in two, so that a forward run and its reverse pass
+ * share one pass: et_run_checkpointed advances u (device, in place) by nsteps
+ * steps like et_run and keeps the checkpoints in the adjoint workspace;
+ * et_vjp_checkpointed then runs the reverse pass from them (same tau, nsteps,
+ * checkpoint_every and workspace; coefficients unchanged in between).  The
+ * results equal et_vjp's from the same u0. */
+ET_API et_status et_run_checkpointed(et_grid* g, double* u, double tau, int nsteps, int checkpoint_every,
+                                     void* workspace, size_t workspace_bytes);
+ET_API et_status et_vjp_checkpointed(et_grid* g, double tau, int nsteps, int checkpoint_every,
+                                     const double* ubar_final, double* ubar0, double* grad_rho,
+                                     double* grad_dscale, void* workspace, size_t workspace_bytes);
 
 /* ---- Batched form: many grids (patients, scenarios) advanced together ----
  * Grids of different sizes, each with its own D, rho and (s, m) schedule, share

@@ -79,6 +79,9 @@ _SIGS = {
     "et_destroy": ([_VP], None),
     "et_vjp_workspace_bytes": ([_VP, _D, _I, _I], ctypes.c_size_t),
     "et_vjp": ([_VP, _VP, _D, _I, _I, _VP, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP, ctypes.c_size_t], _I),
+    "et_run_checkpointed": ([_VP, _VP, _D, _I, _I, _VP, ctypes.c_size_t], _I),
+    "et_vjp_checkpointed": ([_VP, _D, _I, _I, _VP, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP,
+                             ctypes.c_size_t], _I),
     "et_batch_workspace_bytes": ([_I, _VP, _I], ctypes.c_size_t),
     "et_batch_create": ([_I, _VP, _D, _I, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)], _I),
     "et_batch_set_coeffs": ([_VP, _VP, _VP, _I, _I, ctypes.POINTER(et_options)], _I),
@@ -299,6 +302,31 @@ class Grid:
                                   ws_ptr, nbytes))
         return ubar0, g_rho.value, g_ds.value
 
+    def adjoint_workspace(self, tau, nsteps, checkpoint_every=10):
+        """A device buffer for et_run_checkpointed / et_vjp_checkpointed: (tensor, aligned pointer, bytes)."""
+        torch = self._torch
+        nbytes = self.lib.et_vjp_workspace_bytes(self.handle, float(tau), int(nsteps), int(checkpoint_every))
+        if nbytes == 0:
+            raise EtError(ET_ERR_STATE, "no adjoint workspace size (coefficients set? tau valid?)")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        return ws, (ws.data_ptr() + 255) // 256 * 256, nbytes
+
+    def run_checkpointed(self, u, tau, nsteps, checkpoint_every=10, workspace=None):
+        """et_run keeping checkpoints for a later vjp_checkpointed; returns the workspace."""
+        ws = workspace if workspace is not None else self.adjoint_workspace(tau, nsteps, checkpoint_every)
+        self._chk(self.lib.et_run_checkpointed(self.handle, self._dev_f64(u, "u"), float(tau), int(nsteps),
+                                               int(checkpoint_every), ws[1], ws[2]))
+        return ws
+
+    def vjp_checkpointed(self, workspace, tau, nsteps, ubar_final, checkpoint_every=10):
+        """Reverse pass from the checkpoints of run_checkpointed: (dJ/du0, dJ/drho, d/ds J(s D))."""
+        ubar0 = self._torch.empty_like(ubar_final)
+        g_rho, g_ds = _D(), _D()
+        self._chk(self.lib.et_vjp_checkpointed(self.handle, float(tau), int(nsteps), int(checkpoint_every),
+                                               self._dev_f64(ubar_final, "ubar_final"), self._dev_f64(ubar0, "ubar0"),
+                                               ctypes.byref(g_rho), ctypes.byref(g_ds), workspace[1], workspace[2]))
+        return ubar0, g_rho.value, g_ds.value
+
     def set_stream(self, stream):
         self.stream = stream
         self._chk(self.lib.et_set_stream(self.handle, stream.cuda_stream))
@@ -425,8 +453,9 @@ def tumour_run(u0, rho, dscale, D0, tau, nsteps, grid=None, checkpoint_every=10,
 
     u0: float64 CUDA tensor (n values); rho, dscale: 0-d float64 tensors (or
     floats); D0: float64 CUDA tensor of per-voxel diffusion.  The backward pass
-    is the library's discrete adjoint (et_vjp), checkpointed every
-    `checkpoint_every` steps; the schedule (s, m, mu) is frozen at the forward
+    is the library's discrete adjoint, checkpointed every `checkpoint_every`
+    steps (the forward run keeps the checkpoints: et_run_checkpointed, then
+    et_vjp_checkpointed); the schedule (s, m, mu) is frozen at the forward
     values.  `grid`: a Grid of the right shape (created if None).
     """
     import torch
@@ -439,17 +468,17 @@ def tumour_run(u0, rho, dscale, D0, tau, nsteps, grid=None, checkpoint_every=10,
             ds = float(dscale_)
             g.set_coeffs(D0 * ds, rho=r, **coeff_opts)
             u = u0_.detach().clone().contiguous()
-            g.run(u, tau, nsteps)
+            # the forward run keeps the checkpoints the backward pass starts from
+            ctx.ws = g.run_checkpointed(u, tau, nsteps, checkpoint_every)
             g.sync_info()
             ctx.g, ctx.ds = g, ds
             ctx.devs = (rho_.device, dscale_.device)
-            ctx.save_for_backward(u0_.detach())
             return u
 
         @staticmethod
         def backward(ctx, ubar):
-            (u0s,) = ctx.saved_tensors
-            ubar0, g_rho, g_ds = ctx.g.vjp(u0s, tau, nsteps, ubar.contiguous(), checkpoint_every)
+            ubar0, g_rho, g_ds = ctx.g.vjp_checkpointed(ctx.ws, tau, nsteps, ubar.contiguous(), checkpoint_every)
+            ctx.ws = None
             # D = dscale D0:  dJ/d dscale = (1 / dscale) d/ds J(s D) at s = 1
             return (ubar0, torch.tensor(g_rho, dtype=torch.float64, device=ctx.devs[0]),
                     torch.tensor(g_ds / ctx.ds, dtype=torch.float64, device=ctx.devs[1]))

@@ -159,6 +159,13 @@ __global__ void cast_kernel(long long n, const double* __restrict__ src, double 
         dst[p] = (float)(src[p] * scale);
 }
 
+template <typename T>
+__global__ void add_widen_kernel(long long n, const double* __restrict__ u, const T* __restrict__ y,
+                                 double* __restrict__ out) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        out[p] = u[p] + (double)y[p];
+}
+
 dim3 voxel_grid3(const Geom& G) {
     return dim3((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
 }
@@ -166,6 +173,14 @@ dim3 voxel_grid3(const Geom& G) {
 }  // namespace
 
 size_t sum_partials_bytes() { return sizeof(double) * kSumBlocks; }
+
+template <typename T>
+cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* out, cudaStream_t stream) {
+    add_widen_kernel<T><<<1024, 256, 0, stream>>>(n, u, y, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_add_widen<double>(long long, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_add_widen<float>(long long, const double*, const float*, double*, cudaStream_t);
 
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream) {
     cast_kernel<<<1024, 256, 0, stream>>>(n, src, scale, dst);

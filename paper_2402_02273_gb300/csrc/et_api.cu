@@ -526,10 +526,14 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
 // ---------------------------------------------------------------------------
 // Adjoint (vector-Jacobian product) of nsteps steps, checkpointed.
 
+// Adjoint workspace: checkpoints, the states of one segment, and the recorded
+// forward steps of that segment (per step: b, the diagonal, every z_j and y_k).
 struct AdjLayout {
-    size_t zstore, ystore, ckpt, seg, ubar[2], bbar, cbar, zbar[2], ybar[2], sacc, racc, partial, slots;
+    size_t zstore, ystore, bstore, dtstore, ckpt, seg, ubar[2], bbar, cbar, zbar[2], ybar[2], sacc, racc, partial,
+        slots;
     size_t total;
-    int nck;
+    size_t zstep, ystep;  // bytes of one step's z and y records
+    int nck, ck;
 };
 
 bool adj_layout(const et_grid* g, const Schedule& S, int nsteps, int ck, AdjLayout* A) {
@@ -542,8 +546,13 @@ bool adj_layout(const et_grid* g, const Schedule& S, int nsteps, int ck, AdjLayo
         return at;
     };
     A->nck = (nsteps + ck - 1) / ck;
-    A->zstore = take((size_t)S.s * S.m * vb * n);
-    A->ystore = take((size_t)(S.s + 1) * vb * n);
+    A->ck = ck;
+    A->zstep = (size_t)S.s * S.m * vb * n;
+    A->ystep = (size_t)(S.s + 1) * vb * n;
+    A->zstore = take((size_t)ck * A->zstep);
+    A->ystore = take((size_t)ck * A->ystep);
+    A->bstore = take((size_t)ck * vb * n);
+    A->dtstore = take((size_t)ck * vb * n);
     A->ckpt = take((size_t)A->nck * 8 * n);
     A->seg = take((size_t)ck * 8 * n);
     for (int i = 0; i < 2; ++i) A->ubar[i] = take(8 * n);
@@ -559,30 +568,53 @@ bool adj_layout(const et_grid* g, const Schedule& S, int nsteps, int ck, AdjLayo
     return true;
 }
 
-// Reverse of one recorded step: given ubar_next = dJ/du^{n+1}, writes ubar =
-// dJ/du^n and accumulates the per-voxel rho and D-scale cotangents.
+// Buffers and record of step `slot` of the current segment.
 template <typename T>
-et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, const double* un,
-                               const double* ubar_next, double* ubar, char* ws, const AdjLayout& A,
-                               cudaStream_t st) {
+Buffers<T> slot_buffers(et_grid* g, char* ws, const AdjLayout& A, int slot, ChainRecord<T>* rec) {
     Buffers<T> B = typed_buffers<T>(g);
-    const long long n = g->n;
+    const size_t vb = sizeof(T) * (size_t)g->n;
+    B.b = (const T*)(ws + A.bstore + (size_t)slot * vb);
+    B.dt = (T*)(ws + A.dtstore + (size_t)slot * vb);
+    rec->zstore = (T*)(ws + A.zstore + (size_t)slot * A.zstep);
+    rec->ystore = (T*)(ws + A.ystore + (size_t)slot * A.ystep);
+    rec->n = g->n;
+    return B;
+}
+
+// Forward step from u^n into the record of `slot`: its b, diagonal, every
+// z_j and y_k (y_s + u^n is u^{n+1}).
+template <typename T>
+et_status record_step(et_grid* g, const Schedule& S, double hstep, const double* un, char* ws, const AdjLayout& A,
+                      int slot, cudaStream_t st) {
+    ChainRecord<T> rec;
+    rec.m = S.m;
+    Buffers<T> B = slot_buffers<T>(g, ws, A, slot, &rec);
     Weights<double> W64;
     for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
-    // 1. record the forward step from u^n
     const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
     const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
     cudaError_t e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, dt_scale, g->scheme,
                                        const_cast<T*>(B.b), B.dt, g->flags, st);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
-    ChainRecord<T> rec;
-    rec.zstore = (T*)(ws + A.zstore);
-    rec.ystore = (T*)(ws + A.ystore);
-    rec.n = n;
-    rec.m = S.m;
     long long launches = 0;
     e = enqueue_chain<T>(g, B, nullptr, S, hstep, st, &launches, &rec);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "recording launch: %s", cudaGetErrorString(e));
+    return ET_OK;
+}
+
+// Reverse of one recorded step: given ubar_next = dJ/du^{n+1}, writes ubar =
+// dJ/du^n and accumulates the per-voxel rho and D-scale cotangents.
+template <typename T>
+et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, const double* un,
+                               const double* ubar_next, double* ubar, char* ws, const AdjLayout& A, int slot,
+                               cudaStream_t st) {
+    const long long n = g->n;
+    Weights<double> W64;
+    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+    ChainRecord<T> rec;
+    rec.m = S.m;
+    Buffers<T> B = slot_buffers<T>(g, ws, A, slot, &rec);
+    cudaError_t e;
     // 2. reverse the chain
     T* bbar = (T*)(ws + A.bbar);
     T* cbar = (T*)(ws + A.cbar);
@@ -663,28 +695,40 @@ et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, cons
     return ET_OK;
 }
 
+// Forward pass from u (in place) keeping u^0, u^ck, u^2ck, ... as checkpoints;
+// all nsteps steps when `full`, else the nsteps - 1 the adjoint needs.
+et_status forward_checkpoints(et_grid* g, double* u, double tau, int nsteps, const Schedule& S, char* ws,
+                              const AdjLayout& A, bool full) {
+    cudaStream_t st = g->stream;
+    const long long n = g->n;
+    const size_t nb = 8ull * n;
+    double* ckpt = (double*)(ws + A.ckpt);
+    long long tl = 0, ol = 0;
+    ET_CUDA(g, cudaMemcpyAsync(ckpt, u, nb, cudaMemcpyDeviceToDevice, st));
+    const int last = full ? nsteps : nsteps - 1;
+    for (int t = 0; t < last; ++t) {
+        et_status rc = enqueue_step(g, u, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
+        if (rc != ET_OK) return rc;
+        if ((t + 1) % A.ck == 0 && t + 1 < nsteps)
+            ET_CUDA(g, cudaMemcpyAsync(ckpt + (size_t)((t + 1) / A.ck) * n, u, nb, cudaMemcpyDeviceToDevice, st));
+    }
+    return ET_OK;
+}
+
+// Reverse pass from the checkpoints: each segment is run forward once with
+// every step recorded, then its steps are reversed.
 template <typename T>
-et_status vjp_impl(et_grid* g, const double* u0, double tau, int nsteps, int ck, const double* ubar_final,
-                   double* ubar0, double* grad_rho, double* grad_dscale, char* ws, const AdjLayout& A,
-                   const Schedule& S) {
+et_status reverse_from_checkpoints(et_grid* g, double tau, int nsteps, const double* ubar_final, double* ubar0,
+                                   double* grad_rho, double* grad_dscale, char* ws, const AdjLayout& A,
+                                   const Schedule& S) {
     cudaStream_t st = g->stream;
     const long long n = g->n;
     const size_t nb = 8ull * n;
     const double hstep = tau / S.s;
+    const int ck = A.ck;
     double* ckpt = (double*)(ws + A.ckpt);
     double* seg = (double*)(ws + A.seg);
     double* ub[2] = {(double*)(ws + A.ubar[0]), (double*)(ws + A.ubar[1])};
-    long long tl = 0, ol = 0;
-    // forward pass, keeping u at every checkpoint (u^0, u^ck, u^2ck, ...)
-    ET_CUDA(g, cudaMemcpyAsync(ckpt, u0, nb, cudaMemcpyDeviceToDevice, st));
-    ET_CUDA(g, cudaMemcpyAsync(seg, u0, nb, cudaMemcpyDeviceToDevice, st));
-    for (int t = 0; t + 1 < nsteps; ++t) {
-        et_status rc = enqueue_step(g, seg, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
-        if (rc != ET_OK) return rc;
-        if ((t + 1) % ck == 0)
-            ET_CUDA(g, cudaMemcpyAsync(ckpt + (size_t)((t + 1) / ck) * n, seg, nb, cudaMemcpyDeviceToDevice, st));
-    }
-    // reverse pass, segment by segment
     ET_CUDA(g, cudaMemcpyAsync(ub[0], ubar_final, nb, cudaMemcpyDeviceToDevice, st));
     ET_CUDA(g, cudaMemsetAsync(ws + A.sacc, 0, nb, st));
     ET_CUDA(g, cudaMemsetAsync(ws + A.racc, 0, nb, st));
@@ -692,18 +736,22 @@ et_status vjp_impl(et_grid* g, const double* u0, double tau, int nsteps, int ck,
     for (int sgi = A.nck - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * ck;
         const int n1 = std::min(n0 + ck, nsteps);
-        // states u^{n0} .. u^{n1-1} of the segment
+        // record the segment's steps; u^{t+1} = u^t + y_s of step t
         ET_CUDA(g, cudaMemcpyAsync(seg, ckpt + (size_t)sgi * n, nb, cudaMemcpyDeviceToDevice, st));
-        for (int t = n0; t + 1 < n1; ++t) {
-            double* src = seg + (size_t)(t - n0) * n;
-            double* dst = src + n;
-            ET_CUDA(g, cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, st));
-            et_status rc = enqueue_step(g, dst, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
+        for (int t = n0; t < n1; ++t) {
+            const int slot = t - n0;
+            double* ut = seg + (size_t)slot * n;
+            et_status rc = record_step<T>(g, S, hstep, ut, ws, A, slot, st);
             if (rc != ET_OK) return rc;
+            if (t + 1 < n1) {
+                const T* ys = (const T*)(ws + A.ystore + (size_t)slot * A.ystep) + (size_t)S.s * n;
+                const cudaError_t e = launch_add_widen<T>(n, ut, ys, ut + n, st);
+                if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "state update: %s", cudaGetErrorString(e));
+            }
         }
         for (int t = n1 - 1; t >= n0; --t) {
             et_status rc = enqueue_step_adjoint<T>(g, S, hstep, seg + (size_t)(t - n0) * n, ub[cur], ub[cur ^ 1],
-                                                   ws, A, st);
+                                                   ws, A, t - n0, st);
             if (rc != ET_OK) return rc;
             cur ^= 1;
         }
@@ -719,6 +767,23 @@ et_status vjp_impl(et_grid* g, const double* u0, double tau, int nsteps, int ck,
     ET_CUDA(g, cudaStreamSynchronize(st));
     if (grad_rho) *grad_rho = host[0];
     if (grad_dscale) *grad_dscale = host[1];
+    return ET_OK;
+}
+
+// Common checks of the adjoint entry points; fills the schedule and layout.
+et_status adjoint_setup(et_grid* g, double tau, int nsteps, int checkpoint_every, void* workspace,
+                        size_t workspace_bytes, Schedule* S, AdjLayout* A) {
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    if (g->prec == ET_DF64) return fail(g, ET_ERR_UNSUPPORTED, "the adjoint is provided for ET_F64 and ET_F32");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(g, ET_ERR_ARG, "tau must be finite and > 0");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(g, ET_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0)
+        return fail(g, ET_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (schedule_for(g, tau, S) != ET_OK) return fail(g, ET_ERR_ARG, "no (s, m) for tau = %g", tau);
+    adj_layout(g, *S, nsteps, std::min(checkpoint_every, nsteps), A);
+    if (workspace_bytes < A->total)
+        return fail(g, ET_ERR_ARG, "adjoint workspace has %zu bytes, %zu needed", workspace_bytes, A->total);
+    clear_graphs(g);  // the forward steps below run without graphs
     return ET_OK;
 }
 
@@ -1021,27 +1086,50 @@ et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int check
                  void* workspace, size_t workspace_bytes) {
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
-    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
-    if (g->prec == ET_DF64) return fail(g, ET_ERR_UNSUPPORTED, "the adjoint is provided for ET_F64 and ET_F32");
     if (!u0 || !ubar_final || !ubar0 || !aligned8(u0) || !aligned8(ubar_final) || !aligned8(ubar0))
         return fail(g, ET_ERR_ARG, "u0, ubar_final and ubar0 must be 8-byte aligned device pointers");
-    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(g, ET_ERR_ARG, "tau must be finite and > 0");
-    if (nsteps < 1 || checkpoint_every < 1) return fail(g, ET_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
-    if (!workspace || ((uintptr_t)workspace % kAlign) != 0)
-        return fail(g, ET_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
     Schedule S;
-    if (schedule_for(g, tau, &S) != ET_OK) return fail(g, ET_ERR_ARG, "no (s, m) for tau = %g", tau);
-    const int ck = std::min(checkpoint_every, nsteps);
     AdjLayout A;
-    adj_layout(g, S, nsteps, ck, &A);
-    if (workspace_bytes < A.total)
-        return fail(g, ET_ERR_ARG, "adjoint workspace has %zu bytes, %zu needed", workspace_bytes, A.total);
-    clear_graphs(g);  // the forward steps below run without graphs
+    et_status rc = adjoint_setup(g, tau, nsteps, checkpoint_every, workspace, workspace_bytes, &S, &A);
+    if (rc != ET_OK) return rc;
+    char* ws = (char*)workspace;
+    // the checkpoint pass runs on the first segment-state slot
+    double* u = (double*)(ws + A.seg);
+    ET_CUDA(g, cudaMemcpyAsync(u, u0, 8ull * g->n, cudaMemcpyDeviceToDevice, g->stream));
+    rc = forward_checkpoints(g, u, tau, nsteps, S, ws, A, false);
+    if (rc != ET_OK) return rc;
     if (g->prec == ET_F64)
-        return vjp_impl<double>(g, u0, tau, nsteps, ck, ubar_final, ubar0, grad_rho, grad_dscale,
-                                (char*)workspace, A, S);
-    return vjp_impl<float>(g, u0, tau, nsteps, ck, ubar_final, ubar0, grad_rho, grad_dscale, (char*)workspace,
-                           A, S);
+        return reverse_from_checkpoints<double>(g, tau, nsteps, ubar_final, ubar0, grad_rho, grad_dscale, ws, A, S);
+    return reverse_from_checkpoints<float>(g, tau, nsteps, ubar_final, ubar0, grad_rho, grad_dscale, ws, A, S);
+}
+
+et_status et_run_checkpointed(et_grid* g, double* u, double tau, int nsteps, int checkpoint_every, void* workspace,
+                              size_t workspace_bytes) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    if (!u || !aligned8(u)) return fail(g, ET_ERR_ARG, "u must be an 8-byte aligned device pointer");
+    Schedule S;
+    AdjLayout A;
+    et_status rc = adjoint_setup(g, tau, nsteps, checkpoint_every, workspace, workspace_bytes, &S, &A);
+    if (rc != ET_OK) return rc;
+    return forward_checkpoints(g, u, tau, nsteps, S, (char*)workspace, A, true);
+}
+
+et_status et_vjp_checkpointed(et_grid* g, double tau, int nsteps, int checkpoint_every, const double* ubar_final,
+                              double* ubar0, double* grad_rho, double* grad_dscale, void* workspace,
+                              size_t workspace_bytes) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(g->device);
+    if (!ubar_final || !ubar0 || !aligned8(ubar_final) || !aligned8(ubar0))
+        return fail(g, ET_ERR_ARG, "ubar_final and ubar0 must be 8-byte aligned device pointers");
+    Schedule S;
+    AdjLayout A;
+    et_status rc = adjoint_setup(g, tau, nsteps, checkpoint_every, workspace, workspace_bytes, &S, &A);
+    if (rc != ET_OK) return rc;
+    char* ws = (char*)workspace;
+    if (g->prec == ET_F64)
+        return reverse_from_checkpoints<double>(g, tau, nsteps, ubar_final, ubar0, grad_rho, grad_dscale, ws, A, S);
+    return reverse_from_checkpoints<float>(g, tau, nsteps, ubar_final, ubar0, grad_rho, grad_dscale, ws, A, S);
 }
 
 void et_destroy(et_grid* g) {

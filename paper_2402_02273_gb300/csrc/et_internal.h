@@ -244,6 +244,9 @@ cudaError_t launch_adj_step(const Geom& G, et_operator op, Weights<double> W, co
 // Deterministic sum of v[0..n) into *out; partial holds sum_partials_bytes().
 size_t sum_partials_bytes();
 cudaError_t launch_sum(long long n, const double* v, double* partial, double* out, cudaStream_t stream);
+// out[p] = u[p] + y[p] in FP64 (y widened as the last term of a step adds it)
+template <typename T>
+cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* out, cudaStream_t stream);
 // dst[p] = (float)(src[p] * scale)
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);
 

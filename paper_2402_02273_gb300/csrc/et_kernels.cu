@@ -190,6 +190,12 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
     residual_point<OP, T>(G, u, W, rho, dt_shift, dt_scale, scheme, b, dt, flags, i, j, k);
 }
 
+// gamma * sum, rounded to the value type and widened, then added to u: the
+// product is rounded on its own (never fused with the addition), so that u
+// plus a recorded gamma * sum (the adjoint's segment states) is the same sum.
+__device__ __forceinline__ double widened_product(double x, double g) { return __dmul_rn(x, g); }
+__device__ __forceinline__ double widened_product(float x, float g) { return (double)(x * g); }
+
 // One (i, j) column of TZ planes of a term, marching in z with the z-neighbours
 // (and, for the conservative operator, the -z face weight) carried in registers.
 template <int OP, typename T, int TZ>
@@ -232,7 +238,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
         if (a.has_beta) acc = fma(a.beta, bv[p], acc);
         if (a.horner) {
             if (!a.last) zout[p] = acc;
-            else if (u) u[p] += (double)(acc * a.gamma);
+            else if (u) u[p] += widened_product(acc, a.gamma);
             else yacc[p] = acc * a.gamma;
         } else {
             T base;
@@ -244,7 +250,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
                 zout[p] = acc;
                 yacc[p] = sum;
             } else if (u) {
-                u[p] += (double)(sum * a.gamma);
+                u[p] += widened_product(sum, a.gamma);
             } else {
                 yacc[p] = sum * a.gamma;
             }
@@ -298,7 +304,7 @@ __device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<doub
     if (a.horner) {
         // sub-step 0 by Horner's rule: no running sum to read or write
         if (!a.last) a.zout[p] = acc;
-        else if (a.u) a.u[p] += acc * a.gamma;
+        else if (a.u) a.u[p] += widened_product(acc, a.gamma);
         else a.yacc[p] = acc * a.gamma;
         return;
     }
@@ -311,7 +317,7 @@ __device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<doub
         a.zout[p] = acc;
         a.yacc[p] = sum;
     } else if (a.u) {
-        a.u[p] += sum * a.gamma;
+        a.u[p] += widened_product(sum, a.gamma);
     } else {
         a.yacc[p] = sum * a.gamma;
     }

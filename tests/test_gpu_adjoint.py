@@ -60,6 +60,28 @@ def test_checkpoint_spacing_does_not_change_the_gradient(env):
         assert torch.equal(got[0], ref[0]) and got[1] == ref[1] and got[2] == ref[2]
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_checkpointed_forward_and_reverse_equal_vjp(env, precision):
+    """et_run_checkpointed + et_vjp_checkpointed (one forward pass shared with
+    the caller's run) give et_run's state and et_vjp's gradients bitwise."""
+    et, torch = env
+    shape, tau, K, ck = (20, 18, 24), 7.3, 7, 3
+    D, u0, tgt = _problem(shape, seed=9)
+    g = et.Grid(shape, precision=precision)
+    g.set_coeffs(torch.from_numpy(D).cuda())
+    u0d = torch.from_numpy(u0.copy()).cuda()
+    u_run = u0d.clone()
+    g.run(u_run, tau, K)
+    u_ck = u0d.clone()
+    ws = g.run_checkpointed(u_ck, tau, K, ck)
+    torch.cuda.synchronize()
+    assert torch.equal(u_run, u_ck)
+    ubarK = (u_ck - torch.from_numpy(tgt.copy()).cuda()).contiguous()
+    ref = g.vjp(u0d, tau, K, ubarK, checkpoint_every=ck)
+    got = g.vjp_checkpointed(ws, tau, K, ubarK, checkpoint_every=ck)
+    assert torch.equal(got[0], ref[0]) and got[1] == ref[1] and got[2] == ref[2]
+
+
 def test_fp32_adjoint_error_is_small(env):
     et, torch = env
     shape, tau, K = (18, 20, 22), 7.3, 4
@@ -80,7 +102,7 @@ def test_fp32_adjoint_error_is_small(env):
     assert g_ds == pytest.approx(o_ds, rel=1e-4)
 
 
-def test_config4_128cubed_50_steps_against_central_differences(env):
+def test_128cubed_50_steps_against_central_differences(env):
     """128^3, 50 steps, checkpoints every 10; target from the forward model with
     rho x 1.1, D scale x 1.1 and the seed shifted by 2 voxels; gradients in rho, the D
     scale and a random direction of u0 against central differences (eps 1e-6)."""

@@ -71,7 +71,7 @@ FP64_FORMS = ["f64", "df64"]  # both held to the FP64 parity tolerance
 
 
 @pytest.mark.parametrize("precision", FP64_FORMS)
-def test_config0_32cubed_10_steps(et_mod, torch_cuda, precision):
+def test_32cubed_10_steps(et_mod, torch_cuda, precision):
     """32^3 phantom, h = 1, tau = 7.3 d, 10 steps (white-matter D = 0.065)."""
     D, u0 = phantom.case(32, seed=0, d_white=0.065)
     _compare_every_step(et_mod, torch_cuda, D, u0, 7.3, 10, TOL64, precision=precision)

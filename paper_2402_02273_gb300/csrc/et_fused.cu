@@ -386,16 +386,17 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         T b_zm = zero, b_w2m = zero;  // z_j and w2 of the plane below, at the halo voxel
         T c_w2m = zero;               // w2 of the plane below, at the interior voxel
 
-        // first term on plane q = L - 1 from stages sp (q) and sc (q + 1)
-        auto first = [&](int q) {
-            if (!has_b) return;
+        // first term on plane q = L - 1 from stages sp (q) and sc (q + 1); returns
+        // z_a at the halo voxel, with its z_j and +z weight for the carries
+        auto first_val = [&](int q, T& zc, T& wzp) -> T {
+            (void)q;
             const T* Zp = reinterpret_cast<const T*>(sp + S::kZj);
             const T* Zc = reinterpret_cast<const T*>(sc + S::kZj);
             const T* W0 = reinterpret_cast<const T*>(sp + S::kW0);
             const T* W1 = reinterpret_cast<const T*>(sp + S::kW1);
             const T* W2 = reinterpret_cast<const T*>(sp + S::kW2);
             const T* DT = reinterpret_cast<const T*>(sp + S::kDt);
-            const T zc = Zp[bz];
+            zc = Zp[bz];
             T wxm, wym, wzm;
             if (kLit) {
                 const T w3 = reinterpret_cast<const T*>(sp + S::kW3)[b10];
@@ -408,71 +409,93 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                 wzm = b_w2m;
             }
             const T bval = hb1 ? reinterpret_cast<const T*>(sp + S::kB)[b10] : zero;
-            const T wzp = W2[b10];
-            T v;
+            wzp = W2[b10];
             if (kZs)
-                v = A::template stencil<true>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
+                return A::template stencil<true>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
+                                                 Zp[bz + BX], wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1,
+                                                 beta1, bval);
+            return A::template stencil<false>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
                                               Zp[bz + BX], wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1,
                                               beta1, bval);
-            else
-                v = A::template stencil<false>(DT[b10], zc, W0[b10], Zp[bz + 1], wxm, Zp[bz - 1], W1[b11],
-                                               Zp[bz + BX], wym, Zp[bz - BX], wzp, Zc[bz], wzm, b_zm, zscale1, hb1,
-                                               beta1, bval);
+        };
+        auto first = [&](int q) {
+            if (!has_b) return;
+            T zc, wzp;
+            const T v = first_val(q, zc, wzp);
             za[(q & 3) * kHalo + t] = v;
             b_zm = zc;
             b_w2m = wzp;
         };
-        // second term on plane q = L - 3 from stage s3 (q) and the z_a ring
-        auto second = [&](int q) {
-            if (!has_c) return;
-            const T wzp = reinterpret_cast<const T*>(s3 + S::kW2)[c10];
-            if (store_c) {
-                const T* Ac = za + (q & 3) * kHalo;
-                const T* Ap = za + ((q + 1) & 3) * kHalo;
-                const T* Am = za + ((q - 1) & 3) * kHalo;
-                const T* W0 = reinterpret_cast<const T*>(s3 + S::kW0);
-                const T* W1 = reinterpret_cast<const T*>(s3 + S::kW1);
-                const T* DT = reinterpret_cast<const T*>(s3 + S::kDt);
-                const T acen = Ac[ca];
-                T wxm, wym, wzm;
-                if (kLit) {
-                    const T w3 = reinterpret_cast<const T*>(s3 + S::kW3)[c10];
-                    wxm = w3;
-                    wym = w3;
-                    wzm = w3;
+        // second term on plane q = L - 3 from stage s3 (q) and the z_a ring;
+        // returns z_b at the interior voxel (computed also for voxels past the
+        // grid's edge, which are not stored)
+        auto second_val = [&](int q, T& acen, T& wzp, T& bval) -> T {
+            const T* Ac = za + (q & 3) * kHalo;
+            const T* Ap = za + ((q + 1) & 3) * kHalo;
+            const T* Am = za + ((q - 1) & 3) * kHalo;
+            const T* W0 = reinterpret_cast<const T*>(s3 + S::kW0);
+            const T* W1 = reinterpret_cast<const T*>(s3 + S::kW1);
+            const T* DT = reinterpret_cast<const T*>(s3 + S::kDt);
+            wzp = reinterpret_cast<const T*>(s3 + S::kW2)[c10];
+            acen = Ac[ca];
+            T wxm, wym, wzm;
+            if (kLit) {
+                const T w3 = reinterpret_cast<const T*>(s3 + S::kW3)[c10];
+                wxm = w3;
+                wym = w3;
+                wzm = w3;
+            } else {
+                wxm = W0[c10 - 1];
+                wym = W1[c11 - BX];
+                wzm = c_w2m;
+            }
+            bval = hb2 ? reinterpret_cast<const T*>(s3 + S::kB)[c10] : zero;
+            return A::template stencil<false>(DT[c10], acen, W0[c10], Ac[ca + 1], wxm, Ac[ca - 1], W1[c11],
+                                              Ac[ca + kHaloX], wym, Ac[ca - kHaloX], wzp, Ap[ca], wzm, Am[ca], zero,
+                                              hb2, beta2, bval);
+        };
+        auto second_store = [&](int q, T zb, T acen) {
+            const long long p = pc + sz * q;
+            if (kHorner) {
+                if (!last2) {
+                    zout[p] = zb;
                 } else {
-                    wxm = W0[c10 - 1];
-                    wym = W1[c11 - BX];
-                    wzm = c_w2m;
+                    const T r = A::scale(gamma2, zb);
+                    if (uout) uout[p] += A::widen(r);
+                    else yout[p] = r;
                 }
-                const T bval = hb2 ? reinterpret_cast<const T*>(s3 + S::kB)[c10] : zero;
-                const T zb = A::template stencil<false>(DT[c10], acen, W0[c10], Ac[ca + 1], wxm, Ac[ca - 1], W1[c11],
-                                                        Ac[ca + kHaloX], wym, Ac[ca - kHaloX], wzp, Ap[ca], wzm, Am[ca],
-                                                        zero, hb2, beta2, bval);
-                const long long p = pc + sz * q;
-                if (kHorner) {
-                    if (!last2) {
-                        zout[p] = zb;
-                    } else {
-                        const T r = A::scale(gamma2, zb);
-                        if (uout) uout[p] += A::widen(r);
-                        else yout[p] = r;
-                    }
+            } else {
+                const T sb0 = kBaseZ ? reinterpret_cast<const T*>(s3 + S::kZj)[c12] : ysrc[p];
+                const T sa = A::axpy(g1, acen, sb0);
+                T sb = A::axpy(g2, zb, sa);
+                if (!last2) {
+                    zout[p] = zb;
+                    yout[p] = sb;
                 } else {
-                    const T sb0 = kBaseZ ? reinterpret_cast<const T*>(s3 + S::kZj)[c12] : ysrc[p];
-                    const T sa = A::axpy(g1, acen, sb0);
-                    T sb = A::axpy(g2, zb, sa);
-                    if (!last2) {
-                        zout[p] = zb;
-                        yout[p] = sb;
-                    } else {
-                        sb = A::scale(gamma2, sb);
-                        if (uout) uout[p] += A::widen(sb);
-                        else yout[p] = sb;
-                    }
+                    sb = A::scale(gamma2, sb);
+                    if (uout) uout[p] += A::widen(sb);
+                    else yout[p] = sb;
                 }
             }
+        };
+        auto second = [&](int q) {
+            if (!has_c) return;
+            T acen, wzp, bval;
+            const T zb = second_val(q, acen, wzp, bval);
+            if (store_c) second_store(q, zb, acen);
             c_w2m = wzp;
+        };
+        // both terms in one stretch of code (the first 8 warps), so that the
+        // two independent chains of dependent additions interleave
+        auto both = [&](int qb, int qc) {
+            T zc, wzpb, acen, wzpc, bval;
+            const T v = first_val(qb, zc, wzpb);
+            const T zb = second_val(qc, acen, wzpc, bval);
+            za[(qb & 3) * kHalo + t] = v;
+            b_zm = zc;
+            b_w2m = wzpb;
+            if (store_c) second_store(qc, zb, acen);
+            c_w2m = wzpc;
         };
 
         // Plane L arrives: the first term runs on plane L - 1, the second on
@@ -498,8 +521,10 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         if (timed_out(ok)) return;
         for (int L = k0 + 3; L <= Llast; ++L) {
             ok = advance();
-            if (ok) first(L - 1);
-            second(L - 3);
+            // (a first term from a stage whose load failed is never read: the
+            // block stops at the vote below)
+            if (has_c) both(L - 1, L - 3);
+            else first(L - 1);
             if (timed_out(ok)) return;
         }
         // plane k1 - 1: its z_a neighbours are complete

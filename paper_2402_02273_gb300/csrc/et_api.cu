@@ -291,9 +291,12 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         }
         return cudaSuccess;
     }
-    // recorded chain (adjoint): every term to its own buffer
+    // recorded chain (adjoint): every term to its own buffer; F32 / DF64 pair
+    // consecutive terms of a sub-step, the pair kernel storing both
+    const bool pairs = !std::is_same<T, double>::value && g->pair &&
+                       !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
     const T* zin = nullptr;
-    for (const PlannedTerm& t : P.terms) {
+    auto rec_args = [&](const PlannedTerm& t) {
         const int k = t.k, j = t.j;
         if (k == 0 && j == 1) zin = B.b;
         if (k > 0 && j == 0) zin = rec->y(k);
@@ -314,6 +317,35 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.yacc = rec->y(k + 1);
         a.u = nullptr;
         a.zout = t.last ? nullptr : rec->z(k, j + 1);
+        return a;
+    };
+    if constexpr (!std::is_same<T, double>::value) {
+        if (pairs) {
+            for (size_t ti = 0; ti < P.terms.size(); ++ti) {
+                const PlannedTerm& t = P.terms[ti];
+                cudaError_t e;
+                if (!t.last && ti + 1 < P.terms.size() && P.terms[ti + 1].k == t.k) {
+                    const TermArgs<T> a1 = rec_args(t);
+                    zin = a1.zout;
+                    const TermArgs<T> a2 = rec_args(P.terms[ti + 1]);
+                    ++ti;
+                    PairMaps M;
+                    if (!pair_maps_for(g->pair, g->G, g->prec, a1.zin, B.b, B.dt, &M)) return cudaErrorInvalidValue;
+                    e = launch_term_pair_maps(M, g->G, g->op, a1, a2, g->flags, st);
+                    if (!a2.last) zin = a2.zout;
+                } else {
+                    const TermArgs<T> a = rec_args(t);
+                    e = launch_term(g->G, g->op, B.W, a, st);
+                    if (!t.last) zin = a.zout;
+                }
+                if (e != cudaSuccess) return e;
+                ++*launches;
+            }
+            return cudaSuccess;
+        }
+    }
+    for (const PlannedTerm& t : P.terms) {
+        const TermArgs<T> a = rec_args(t);
         const cudaError_t e = launch_term(g->G, g->op, B.W, a, st);
         if (e != cudaSuccess) return e;
         ++*launches;

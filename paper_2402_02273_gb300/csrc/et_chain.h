@@ -60,6 +60,7 @@ std::vector<ChainOp<T>> chain_ops(const ChainPlan& P, int s, const T* b, const T
         if (pairs && !t.last && ti + 1 < P.terms.size() && P.terms[ti + 1].k == t.k) {
             op.pair = true;
             op.a1 = args_of(t);  // its outputs stay on chip
+            op.a1.zout = nullptr;
             op.a2 = args_of(P.terms[ti + 1]);
             ++ti;
             if (!op.a2.last) {

@@ -373,6 +373,7 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
         const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
         const T* const ysrc = a1.yacc;
+        T* const zfirst = a1.zout;  // nullptr unless the chain is recorded
         T* const zout = a2.zout;
         T* const yout = a2.yacc;
         double* const uout = a2.u;
@@ -456,6 +457,7 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         };
         auto second_store = [&](int q, T zb, T acen) {
             const long long p = pc + sz * q;
+            if (zfirst) zfirst[p] = acen;  // a recorded chain keeps the first term too
             if (kHorner) {
                 if (!last2) {
                     zout[p] = zb;
@@ -716,6 +718,47 @@ bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out) {
     out->w3 = P->w3;
     return true;
 }
+
+bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const void* zin, const void* b,
+                   const void* dt, PairMaps* out) {
+    if (!P || prec == ET_F64) return false;
+    const int es = prec == ET_F32 ? 4 : 8;
+    const int bx = es == 8 ? Shape<float2>::BX : Shape<float>::BX;
+    out->w0 = P->w0;
+    out->w1 = P->w1;
+    out->w2 = P->w2;
+    out->w3 = P->w3;
+    return encode(&out->zj, zin, G, es, bx, 12) && encode(&out->b, b, G, es, bx, 10) &&
+           encode(&out->dt, dt, G, es, bx, 10);
+}
+
+template <typename T>
+cudaError_t launch_term_pair_maps(const PairMaps& M, const Geom& G, et_operator op, const TermArgs<T>& a1,
+                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream) {
+    if (!pair_shape_ok(a1, a2)) return cudaErrorInvalidValue;
+    if (op == ET_OP_CONSERVATIVE) {
+        if (a1.horner)
+            return a1.has_zscale ? launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeHorner | kModeZscale>(M, G, a1, a2,
+                                                                                                    flags, stream)
+                                 : launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeHorner>(M, G, a1, a2, flags, stream);
+        if (a1.has_zscale) return cudaErrorInvalidValue;
+        return a1.base_mode == 2 ? launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeBaseZ>(M, G, a1, a2, flags, stream)
+                                 : launch_pair_mode<ET_OP_CONSERVATIVE, T, 0>(M, G, a1, a2, flags, stream);
+    }
+    if (a1.horner)
+        return a1.has_zscale
+                   ? launch_pair_mode<ET_OP_LITERAL, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream)
+                   : launch_pair_mode<ET_OP_LITERAL, T, kModeHorner>(M, G, a1, a2, flags, stream);
+    if (a1.has_zscale) return cudaErrorInvalidValue;
+    return a1.base_mode == 2 ? launch_pair_mode<ET_OP_LITERAL, T, kModeBaseZ>(M, G, a1, a2, flags, stream)
+                             : launch_pair_mode<ET_OP_LITERAL, T, 0>(M, G, a1, a2, flags, stream);
+}
+
+template cudaError_t launch_term_pair_maps<float>(const PairMaps&, const Geom&, et_operator, const TermArgs<float>&,
+                                                  const TermArgs<float>&, unsigned*, cudaStream_t);
+template cudaError_t launch_term_pair_maps<float2>(const PairMaps&, const Geom&, et_operator,
+                                                   const TermArgs<float2>&, const TermArgs<float2>&, unsigned*,
+                                                   cudaStream_t);
 
 // Batched launches hold many grids, so every block has several tiles even
 // with whole columns: segments of up to 64 planes.

@@ -225,6 +225,15 @@ cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, c
 // Fills the tensor maps of a pair launch (a1.zin selects the z_j map); false
 // if a1.zin is none of the plan's vectors.
 bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out);
+// Tensor maps for a pair launch on other buffers than the plan's (z_j, b and
+// the diagonal encoded now; the weights from the plan).
+bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const void* zin, const void* b,
+                   const void* dt, PairMaps* out);
+// A pair launch with explicit tensor maps; a1.zout non-null also stores the
+// first term (a recorded chain).
+template <typename T>
+cudaError_t launch_term_pair_maps(const PairMaps& M, const Geom& G, et_operator op, const TermArgs<T>& a1,
+                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
 // Planes per column segment of a grid in a batched launch.
 int batch_pair_tz(const Geom& G);
 // Batched two-term launch over count grids (device table d, tiles in all).

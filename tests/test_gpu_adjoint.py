@@ -102,6 +102,31 @@ def test_fp32_adjoint_error_is_small(env):
     assert g_ds == pytest.approx(o_ds, rel=1e-4)
 
 
+@pytest.mark.parametrize("sched", [{}, {"force_s": 2, "force_m": 5}, {"force_s": 3, "force_m": 4}])
+def test_fp32_recorded_pairs_equal_single_terms(env, sched):
+    """On TMA-eligible rows the FP32 adjoint records its forward chains with the
+    two-term kernel (storing both terms); the gradients equal those of the
+    one-term recording bitwise, and stay within the FP32 bound of the oracle's."""
+    et, torch = env
+    shape, tau, K = (18, 20, 24), 7.3, 4
+    D, u0, tgt = _problem(shape, seed=4)
+    P = oracle.Problem(D)
+    uK, _ = P.run(u0, tau, K)
+    o_ub, o_rho, o_ds = oracle.vjp(P, u0, tau, K, uK - tgt)
+    got = []
+    for single in (False, True):
+        g = et.Grid(shape, precision="f32")
+        g.set_coeffs(torch.from_numpy(D).cuda(), single_terms=single, **sched)
+        got.append(g.vjp(torch.from_numpy(u0.copy()).cuda(), tau, K,
+                         torch.from_numpy((uK - tgt).copy()).cuda(), checkpoint_every=2))
+    assert torch.equal(got[0][0], got[1][0]) and got[0][1] == got[1][1] and got[0][2] == got[1][2]
+    if not sched:
+        ub = got[0][0].cpu().numpy().reshape(shape)
+        assert np.abs(ub - o_ub).max() <= 1e-4 * np.abs(o_ub).max()
+        assert got[0][1] == pytest.approx(o_rho, rel=1e-4)
+        assert got[0][2] == pytest.approx(o_ds, rel=1e-4)
+
+
 def test_128cubed_50_steps_against_central_differences(env):
     """128^3, 50 steps, checkpoints every 10; target from the forward model with
     rho x 1.1, D scale x 1.1 and the seed shifted by 2 voxels; gradients in rho, the D

@@ -67,7 +67,7 @@ def launch_mix(prec, s, m, pairs):
 # DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of the current kernels (cold cache; DF64 and FP32 launches
 # cover two terms); None where the kernel changed after the capture.
-TERM_TRAFFIC = {"f64": 107.0e6, "df64": None, "f32": None}
+TERM_TRAFFIC = {"f64": 107.0e6, "df64": 115.1e6, "f32": 50.7e6}
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10

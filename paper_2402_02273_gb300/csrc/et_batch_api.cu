@@ -399,8 +399,9 @@ et_status upload_tables(et_batch* b, double* u, double tau, int variant, et_step
 }
 
 // Times the first launch index (every grid's first single or two-term launch)
-// for every kernel variant, scores it per Taylor term advanced, and keeps the
-// fastest.  us_out[v]: microseconds per term of the batch.
+// for every kernel variant and scores it per Taylor term advanced; keeps the
+// fastest one-term variant, with two-term launches if those are faster still.
+// us_out[v]: microseconds per term of the batch.
 template <typename T>
 et_status autotune(et_batch* b, double tau, double* us_out) {
     const int nv = total_variants(b->prec);
@@ -409,6 +410,7 @@ et_status autotune(et_batch* b, double tau, double* us_out) {
     BT_CUDA(b, cudaEventCreate(&e1));
     double best = 1e300;
     int best_v = 0;
+    std::vector<double> times(nv, 1e300);
     const int C = b->count;
     const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
     for (int v = 0; v < nv; ++v) {
@@ -459,14 +461,25 @@ et_status autotune(et_batch* b, double tau, double* us_out) {
             return bfail(b, ET_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(cudaGetLastError()));
         }
         const double us = ms * 1e3 / 3.0 * (vterms > 0.0 ? voxels / vterms : 1.0);
+        times[v] = us;
         if (us_out) us_out[v] = us;
-        if (us < best) {
-            best = us;
-            best_v = v;
-        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // The fastest one-term variant also runs the leftover single terms of the
+    // two-term variants, so it is chosen on its own; two-term launches are then
+    // kept if their best time per term beats it.
+    const int nsv = batch_variant_count(b->prec);
+    int best_single = nv - nsv;
+    for (int v = nv - nsv; v < nv; ++v)
+        if (times[v] < times[best_single]) best_single = v;
+    best_v = best_single;
+    if (nv > nsv) {
+        double best_pair = times[0];
+        for (int v = 1; v < nsv; ++v) best_pair = std::min(best_pair, times[v]);
+        if (best_pair < times[best_single]) best_v = best_single - nsv;  // the same single variant, with pairs
+    }
+    (void)best;
     b->variant = best_v;
     b->table_tau = -1.0;  // tables must be rebuilt for the chosen variant
     return ET_OK;

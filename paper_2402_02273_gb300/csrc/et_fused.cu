@@ -373,7 +373,7 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
         const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
         const T* const ysrc = a1.yacc;
-        T* const zfirst = a1.zout;  // nullptr unless the chain is recorded
+        T* const zfirst = kTable ? nullptr : a1.zout;  // nullptr unless the chain is recorded
         T* const zout = a2.zout;
         T* const yout = a2.yacc;
         double* const uout = a2.u;

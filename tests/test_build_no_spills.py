@@ -1,0 +1,42 @@
+"""The hot kernels compile without register spills for sm_103a (ptxas -v);
+a spill in a Taylor-term kernel costs it a large part of its throughput.
+Needs nvcc only (no GPU)."""
+import os
+import re
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2402_02273_gb300", "csrc")
+HOT = ["et_kernels.cu", "et_df64.cu", "et_fused.cu"]
+
+
+def _ptxas_report(src):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", os.devnull]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stderr
+
+
+def test_term_kernels_do_not_spill():
+    with ThreadPoolExecutor(len(HOT)) as ex:
+        reports = dict(zip(HOT, ex.map(_ptxas_report, HOT)))
+    spills = []
+    for src, text in reports.items():
+        entry = None
+        for line in text.splitlines():
+            m = re.search(r"Compiling entry function '([^']+)'", line)
+            if m:
+                entry = m.group(1)
+            m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+            if m and entry and "term" in entry and (int(m.group(1)) or int(m.group(2))):
+                spills.append((src, entry, line.strip()))
+    assert not spills, spills

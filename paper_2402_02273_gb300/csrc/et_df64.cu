@@ -141,7 +141,7 @@ term_kernel_df64(const __grid_constant__ Geom G, const __grid_constant__ Weights
 
 // Batched form: blocks loop over the tiles of all grids of the launch.
 template <int OP, int TZ>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
 batch_term_df64_kernel(const BatchTerm<float2>* __restrict__ d, int count, long long tiles) {
     __shared__ BatchTerm<float2> sd;
     const int tid = threadIdx.x + kBlockX * threadIdx.y;

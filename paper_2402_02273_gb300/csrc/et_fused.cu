@@ -23,8 +23,10 @@
 // both give identical numbers.
 //
 // Eligible grids: rows of a 16-byte multiple (nx even for DF64, a multiple of
-// 4 for FP32), as TMA requires of the global strides; other grids and the
-// adjoint's recorded chains run one term per launch.
+// 4 for FP32), as TMA requires of the global strides; other grids run one
+// term per launch.  The same body serves one grid (kernel parameters), a
+// table of grids (the batched form) and recorded chains of the adjoint (the
+// first term is then stored too, to the record).
 //
 // Every mbarrier wait is bounded; a wait that runs out sets ET_FLAG_TIMEOUT,
 // waits (bounded) for the block's copies still in flight and ends the block.

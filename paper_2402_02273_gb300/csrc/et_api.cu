@@ -274,7 +274,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
     const int s = S.s;
     if (!rec) {
         // F32 / DF64: consecutive terms of a sub-step go in pairs (et_fused.cu)
-        const bool pairs = !std::is_same<T, double>::value && g->pair &&
+        const bool pairs = !std::is_same<T, double>::value && g->pair && pair_preferred(g->op, g->prec) &&
                            !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
         T* const Y[2] = {B.Y[0], B.Y[1]};
         T* const Z[2] = {B.Z[0], B.Z[1]};
@@ -293,7 +293,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
     }
     // recorded chain (adjoint): every term to its own buffer; F32 / DF64 pair
     // consecutive terms of a sub-step, the pair kernel storing both
-    const bool pairs = !std::is_same<T, double>::value && g->pair &&
+    const bool pairs = !std::is_same<T, double>::value && g->pair && pair_preferred(g->op, g->prec) &&
                        !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
     const T* zin = nullptr;
     auto rec_args = [&](const PlannedTerm& t) {

@@ -794,6 +794,20 @@ cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, c
     return launch_pair_op<ET_OP_LITERAL, T>(P, G, a1, a2, flags, stream);
 }
 
+bool pair_preferred(et_operator op, et_precision prec) {
+    // Shared memory of the literal DF64 stage admits only one block per SM,
+    // where two single-term launches are faster (measured at 128^3).
+    if (prec == ET_F64) return false;
+    int per_sm;
+    if (prec == ET_F32)
+        per_sm = op == ET_OP_CONSERVATIVE ? pair_blocks_per_sm<ET_OP_CONSERVATIVE, float, kModeHorner>()
+                                          : pair_blocks_per_sm<ET_OP_LITERAL, float, kModeHorner>();
+    else
+        per_sm = op == ET_OP_CONSERVATIVE ? pair_blocks_per_sm<ET_OP_CONSERVATIVE, float2, kModeHorner>()
+                                          : pair_blocks_per_sm<ET_OP_LITERAL, float2, kModeHorner>();
+    return per_sm >= 2;
+}
+
 cudaError_t prime_launch_limits_pair() {
     prime_pair<ET_OP_CONSERVATIVE, float>();
     prime_pair<ET_OP_LITERAL, float>();

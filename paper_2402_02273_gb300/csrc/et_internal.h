@@ -234,6 +234,9 @@ bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const vo
 template <typename T>
 cudaError_t launch_term_pair_maps(const PairMaps& M, const Geom& G, et_operator op, const TermArgs<T>& a1,
                                   const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
+// Whether two terms per launch beat two one-term launches for this operator
+// and form (resident blocks per SM of the pair kernel: at least 2).
+bool pair_preferred(et_operator op, et_precision prec);
 // Planes per column segment of a grid in a batched launch.
 int batch_pair_tz(const Geom& G);
 // Batched two-term launch over count grids (device table d, tiles in all).

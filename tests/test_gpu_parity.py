@@ -140,7 +140,10 @@ def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op
     fused, rf = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, **kw)
     single, rs = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, single_terms=True, **kw)
     assert (rf["s"], rf["m"]) == (rs["s"], rs["m"])
+    # pairs run where TMA can address the rows, except the literal DF64 stage,
+    # whose shared memory admits one block per SM (one-term launches are faster)
     eligible = (shape[2] * (4 if precision == "f32" else 8)) % 16 == 0
+    eligible = eligible and not (op == "literal" and precision == "df64")
     if eligible and rf["m"] >= 3:
         assert rf["term_launches"] < rs["term_launches"]
     else:

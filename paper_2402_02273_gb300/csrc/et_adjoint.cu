@@ -11,7 +11,8 @@
 //     cbar_p   += f_j / nu * w_p x_p,      sbar_p += f_j / nu * (L^T w)_p x_p,
 // x being the forward input of that term (zeta_j, y_k, or b).  cbar is the
 // cotangent of the diagonal rho(1 - 2u^n) and sbar that of a uniform scale s
-// of D (D -> s D), both per voxel and reduced at the end.  Per step,
+// of D (D -> s D), both per voxel; a step's sbar terms are summed in the value
+// type and added to the FP64 total by the step kernel, reduced at the end.  Per step,
 //     ubar^n = ubar^{n+1} + L^T bbar + rho (1 - 2u) bbar - 2 rho cbar,
 //     rho-gradient += u(1-u) bbar + (1 - 2u) cbar,   s-gradient += bbar (L u),
 // from b = L u + rho u (1-u) and c = rho (1 - 2u) (exponential Euler: no c).
@@ -71,7 +72,7 @@ adj_term_kernel(Geom G, Weights<T> W, AdjTermArgs<T> a) {
     const T ltw = fma(a.negR[p], wp, off);
     // d A^/d c_p = e_p e_p^T / nu;  d A^/d s = L / nu (ltw already carries the 1/nu)
     a.cbar[p] = fma(a.f * a.inv_nu * wp, x, a.cbar[p]);
-    a.sbar_acc[p] = fma((double)(a.f * ltw), (double)x, a.sbar_acc[p]);
+    a.sstep[p] = fma(a.f * ltw, x, a.sstep[p]);
     T bb = a.bbar[p];
     if (a.has_beta) bb = fma(a.beta, wp, bb);
     if (a.out_to_bbar) {
@@ -85,8 +86,9 @@ adj_term_kernel(Geom G, Weights<T> W, AdjTermArgs<T> a) {
 template <int OP, typename T>
 __global__ void __launch_bounds__(kThreads)
 adj_step_kernel(Geom G, Weights<double> W, const double* __restrict__ u, const T* __restrict__ bbar,
-                const T* __restrict__ cbar, const double* __restrict__ ubar_next, double rho, int scheme,
-                double* __restrict__ ubar, double* __restrict__ sbar_acc, double* __restrict__ rbar_acc) {
+                const T* __restrict__ cbar, const T* __restrict__ sstep, const double* __restrict__ ubar_next,
+                double rho, int scheme, double* __restrict__ ubar, double* __restrict__ sbar_acc,
+                double* __restrict__ rbar_acc) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
@@ -124,6 +126,7 @@ adj_step_kernel(Geom G, Weights<double> W, const double* __restrict__ u, const T
     }
     ubar[p] = ub;
     rbar_acc[p] += rb;
+    sbar_acc[p] += (double)sstep[p];
     sbar_acc[p] += bp * lu;
 }
 
@@ -200,15 +203,15 @@ cudaError_t launch_adj_term(const Geom& G, et_operator op, Weights<T> W, const A
 
 template <typename T>
 cudaError_t launch_adj_step(const Geom& G, et_operator op, Weights<double> W, const double* u, const T* bbar,
-                            const T* cbar, const double* ubar_next, double rho, et_scheme scheme, double* ubar,
-                            double* sbar_acc, double* rbar_acc, cudaStream_t stream) {
+                            const T* cbar, const T* sstep, const double* ubar_next, double rho, et_scheme scheme,
+                            double* ubar, double* sbar_acc, double* rbar_acc, cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
         adj_step_kernel<ET_OP_CONSERVATIVE, T><<<voxel_grid3(G), block, 0, stream>>>(
-            G, W, u, bbar, cbar, ubar_next, rho, (int)scheme, ubar, sbar_acc, rbar_acc);
+            G, W, u, bbar, cbar, sstep, ubar_next, rho, (int)scheme, ubar, sbar_acc, rbar_acc);
     else
         adj_step_kernel<ET_OP_LITERAL, T><<<voxel_grid3(G), block, 0, stream>>>(
-            G, W, u, bbar, cbar, ubar_next, rho, (int)scheme, ubar, sbar_acc, rbar_acc);
+            G, W, u, bbar, cbar, sstep, ubar_next, rho, (int)scheme, ubar, sbar_acc, rbar_acc);
     return cudaGetLastError();
 }
 
@@ -223,10 +226,10 @@ template cudaError_t launch_adj_term<double>(const Geom&, et_operator, Weights<d
 template cudaError_t launch_adj_term<float>(const Geom&, et_operator, Weights<float>, const AdjTermArgs<float>&,
                                             cudaStream_t);
 template cudaError_t launch_adj_step<double>(const Geom&, et_operator, Weights<double>, const double*,
-                                             const double*, const double*, const double*, double, et_scheme,
-                                             double*, double*, double*, cudaStream_t);
+                                             const double*, const double*, const double*, const double*, double,
+                                             et_scheme, double*, double*, double*, cudaStream_t);
 template cudaError_t launch_adj_step<float>(const Geom&, et_operator, Weights<double>, const double*, const float*,
-                                            const float*, const double*, double, et_scheme, double*, double*,
-                                            double*, cudaStream_t);
+                                            const float*, const float*, const double*, double, et_scheme, double*,
+                                            double*, double*, cudaStream_t);
 
 }  // namespace et

@@ -561,7 +561,8 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
 // Adjoint workspace: checkpoints, the states of one segment, and the recorded
 // forward steps of that segment (per step: b, the diagonal, every z_j and y_k).
 struct AdjLayout {
-    size_t zstore, ystore, bstore, dtstore, ckpt, seg, ubar[2], bbar, cbar, zbar[2], ybar[2], sacc, racc, partial,
+    size_t zstore, ystore, bstore, dtstore, ckpt, seg, ubar[2], bbar, cbar, sstep, zbar[2], ybar[2], sacc, racc,
+        partial,
         slots;
     size_t total;
     size_t zstep, ystep;  // bytes of one step's z and y records
@@ -590,6 +591,7 @@ bool adj_layout(const et_grid* g, const Schedule& S, int nsteps, int ck, AdjLayo
     for (int i = 0; i < 2; ++i) A->ubar[i] = take(8 * n);
     A->bbar = take(vb * n);
     A->cbar = take(vb * n);
+    A->sstep = take(vb * n);
     for (int i = 0; i < 2; ++i) A->zbar[i] = take(vb * n);
     for (int i = 0; i < 2; ++i) A->ybar[i] = take(vb * n);
     A->sacc = take(8 * n);
@@ -656,6 +658,8 @@ et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, cons
     double* racc = (double*)(ws + A.racc);
     ET_CUDA(g, cudaMemsetAsync(bbar, 0, sizeof(T) * n, st));
     ET_CUDA(g, cudaMemsetAsync(cbar, 0, sizeof(T) * n, st));
+    T* sstep = (T*)(ws + A.sstep);
+    ET_CUDA(g, cudaMemsetAsync(sstep, 0, sizeof(T) * n, st));
     const T* ynext;  // cotangent of y_{k+1}
     int yi = 0;
     if constexpr (std::is_same<T, double>::value) {
@@ -703,7 +707,7 @@ et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, cons
         a.beta = Scalar<T>::make(t.beta);
         a.bbar = bbar;
         a.cbar = cbar;
-        a.sbar_acc = sacc;
+        a.sstep = sstep;
         a.out_to_bbar = into_b;
         if (into_y) {
             a.zbar_out = ybar[yi];
@@ -722,7 +726,8 @@ et_status enqueue_step_adjoint(et_grid* g, const Schedule& S, double hstep, cons
         }
     }
     // 3. through b = L u + rho u (1 - u) and c = rho (1 - 2u) to u^n, rho, D scale
-    e = launch_adj_step<T>(g->G, g->op, W64, un, bbar, cbar, ubar_next, g->rho, g->scheme, ubar, sacc, racc, st);
+    e = launch_adj_step<T>(g->G, g->op, W64, un, bbar, cbar, sstep, ubar_next, g->rho, g->scheme, ubar, sacc, racc,
+                           st);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "adjoint step launch: %s", cudaGetErrorString(e));
     return ET_OK;
 }

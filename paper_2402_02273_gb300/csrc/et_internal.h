@@ -119,7 +119,7 @@ struct AdjTermArgs {
     T beta;
     T* bbar;             // cotangent of b (accumulated)
     T* cbar;             // cotangent of the diagonal rho(1 - 2u) (accumulated)
-    double* sbar_acc;    // per-voxel cotangent of the D scale (accumulated)
+    T* sstep;            // per-voxel cotangent of the D scale, this step's terms
     int out_to_bbar;     // the output adds to bbar instead of zbar_out
     T* zbar_out;
 };
@@ -251,8 +251,8 @@ cudaError_t launch_adj_term(const Geom& G, et_operator op, Weights<T> W, const A
                             cudaStream_t stream);
 template <typename T>
 cudaError_t launch_adj_step(const Geom& G, et_operator op, Weights<double> W, const double* u, const T* bbar,
-                            const T* cbar, const double* ubar_next, double rho, et_scheme scheme, double* ubar,
-                            double* sbar_acc, double* rbar_acc, cudaStream_t stream);
+                            const T* cbar, const T* sstep, const double* ubar_next, double rho, et_scheme scheme,
+                            double* ubar, double* sbar_acc, double* rbar_acc, cudaStream_t stream);
 // Deterministic sum of v[0..n) into *out; partial holds sum_partials_bytes().
 size_t sum_partials_bytes();
 cudaError_t launch_sum(long long n, const double* v, double* partial, double* out, cudaStream_t stream);

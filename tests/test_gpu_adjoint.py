@@ -160,11 +160,23 @@ def test_128cubed_50_steps_against_central_differences(env):
     v *= (u0 > 1e-3)  # a direction inside the seed
     fd_u = (loss(forward(u0 + eps * v, rho, ds)) - loss(forward(u0 - eps * v, rho, ds))) / (2 * eps)
     ad_u = float((ub.cpu() * torch.from_numpy(v)).sum())
-    print(f"config 4: rho {g_rho:.6e} vs fd {fd_rho:.6e}; D scale {g_ds:.6e} vs {fd_ds:.6e}; "
+    print(f"128^3 x 50: rho {g_rho:.6e} vs fd {fd_rho:.6e}; D scale {g_ds:.6e} vs {fd_ds:.6e}; "
           f"u0 dir {ad_u:.6e} vs {fd_u:.6e}")
     assert g_rho == pytest.approx(fd_rho, rel=1e-5)
     assert g_ds == pytest.approx(fd_ds, rel=1e-5)
     assert ad_u == pytest.approx(fd_u, rel=1e-5)
+    # the FP32 adjoint of the FP32 forward, checked against these FP64 gradients
+    gf = et.Grid(shape, precision="f32")
+    gf.set_coeffs(Dd, rho=rho)
+    uf = u0d.clone()
+    gf.run(uf, tau, K)
+    ubf, f_rho, f_ds = gf.vjp(u0d, tau, K, (uf - tgt).contiguous(), checkpoint_every=10)
+    f_u = float((ubf.cpu() * torch.from_numpy(v)).sum())
+    print(f"FP32 adjoint at 128^3 x 50: rho {abs(f_rho / g_rho - 1):.2e}, D scale {abs(f_ds / g_ds - 1):.2e}, "
+          f"u0 dir {abs(f_u / ad_u - 1):.2e} relative to FP64")
+    assert f_rho == pytest.approx(g_rho, rel=1e-4)
+    assert f_ds == pytest.approx(g_ds, rel=1e-4)
+    assert f_u == pytest.approx(ad_u, rel=1e-4)
 
 
 def test_autograd_function_gradients(env):

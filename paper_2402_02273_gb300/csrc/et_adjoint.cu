@@ -162,6 +162,15 @@ __global__ void cast_kernel(long long n, const double* __restrict__ src, double 
         dst[p] = (float)(src[p] * scale);
 }
 
+__global__ void split_kernel(long long n, const double* __restrict__ src, double scale, float2* __restrict__ dst) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const double x = src[p] * scale;
+        const float hi = (float)x;
+        dst[p] = make_float2(hi, (float)(x - (double)hi));
+    }
+}
+
 template <typename T>
 __global__ void add_widen_kernel(long long n, const double* __restrict__ u, const T* __restrict__ y,
                                  double* __restrict__ out) {
@@ -184,6 +193,11 @@ cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* o
 }
 template cudaError_t launch_add_widen<double>(long long, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_add_widen<float>(long long, const double*, const float*, double*, cudaStream_t);
+
+cudaError_t launch_split(long long n, const double* src, double scale, float2* dst, cudaStream_t stream) {
+    split_kernel<<<1024, 256, 0, stream>>>(n, src, scale, dst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream) {
     cast_kernel<<<1024, 256, 0, stream>>>(n, src, scale, dst);

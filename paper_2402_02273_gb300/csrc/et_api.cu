@@ -37,6 +37,7 @@ struct Layout {
     size_t wt[5];     // typed, 1/nu-scaled copies of w[0..4] (F32, DF64)
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
+    size_t ushadow;   // DF64: u as pairs, read by the pair-arithmetic residual
     size_t partial;   // 3 * nblocks doubles
     size_t misc;      // counters, flags, info slots
     size_t total;
@@ -66,6 +67,7 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     for (int a = 0; a < 5; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * n) : SIZE_MAX;
     for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * n);
     L->stage = take(8ull * n);
+    L->ushadow = prec == ET_DF64 ? take(8ull * n) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks);
     L->misc = take(kMiscBytes);
     L->total = off;
@@ -132,6 +134,7 @@ struct et_grid {
     double* stage;
     double* partial;
     PairPlan* pair;  // tensor maps of the two-term kernel (F32 / DF64), or nullptr
+    float2* ush;     // DF64: the pair copy of u (nullptr otherwise)
     unsigned long long* rmax_bits;
     unsigned* flags;
     unsigned* ticket;
@@ -278,7 +281,8 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                            !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
         T* const Y[2] = {B.Y[0], B.Y[1]};
         T* const Z[2] = {B.Z[0], B.Z[1]};
-        for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs)) {
+        void* ush = std::is_same<T, float2>::value ? (void*)g->ush : nullptr;
+        for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs, ush)) {
             cudaError_t e;
             if constexpr (std::is_same<T, double>::value) {
                 e = launch_term(g->G, g->op, B.W, op.a1, st);
@@ -316,6 +320,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.horner = t.horner;
         a.yacc = rec->y(k + 1);
         a.u = nullptr;
+        a.ush = nullptr;
         a.zout = t.last ? nullptr : rec->z(k, j + 1);
         return a;
     };
@@ -362,8 +367,20 @@ et_status enqueue_form(et_grid* g, double* u, const Schedule& S, double hstep, d
     Weights<double> W64;
     for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
     const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
-    cudaError_t e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, dt_scale, g->scheme,
-                                       const_cast<T*>(B.b), B.dt, g->flags, st);
+    cudaError_t e;
+    if constexpr (std::is_same<T, float2>::value) {
+        // DF64: the residual in pair arithmetic from the pair copy of u, on the
+        // FP32 pipes (the FP64 residual is bound by GB300's FP64 rate)
+        Weights<float2> WT = B.W;
+        WT.w[4] = (const float2*)g->wt[4];
+        const double k_u = g->scheme == ET_SCHEME_ROSENBROCK ? -2.0 * g->rho / g->nu : 0.0;
+        e = launch_residual_df64(g->G, g->op, g->ush, WT, Scalar<float2>::make(g->nu), Scalar<float2>::make(g->rho),
+                                 Scalar<float2>::make(dt_shift / g->nu), Scalar<float2>::make(k_u), g->scheme,
+                                 const_cast<float2*>(B.b), B.dt, g->flags, st);
+    } else {
+        e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, dt_scale, g->scheme, const_cast<T*>(B.b), B.dt,
+                               g->flags, st);
+    }
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
     ++*other_launches;
     if (ev_begin) ET_CUDA(g, cudaEventRecordWithFlags(ev_begin, st, evflags));
@@ -425,6 +442,12 @@ et_status enqueue_run(et_grid* g, double* u, double tau, int nsteps, et_step_inf
     et_step_info* dst = info ? info : g->info_slot;
     const int stride = info ? 1 : 0;
     long long tl = 0, ol = 0;
+    if (g->ush) {
+        // the pair copy of u that the DF64 residual reads; the steps keep it current
+        const cudaError_t e = launch_split(g->n, u, 1.0, g->ush, st);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "split launch: %s", cudaGetErrorString(e));
+        ++ol;
+    }
     for (int t = 0; t < nsteps; ++t) {
         cudaEvent_t e0 = g->timing ? g->ev[2 * t] : nullptr;
         cudaEvent_t e1 = g->timing ? g->ev[2 * t + 1] : nullptr;
@@ -543,6 +566,7 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
         } else {
             float2* dst[4] = {(float2*)g->wt[0], (float2*)g->wt[1], (float2*)g->wt[2], (float2*)g->wt[3]};
             e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
+            if (e == cudaSuccess) e = launch_split(g->n, g->w[4], 1.0 / g->nu, (float2*)g->wt[4], g->stream);
         }
         if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
     }
@@ -952,6 +976,7 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     for (int a = 0; a < 5; ++a) g->wt[a] = precision != ET_F64 ? (void*)(g->ws + L.wt[a]) : nullptr;
     for (int v = 0; v < 6; ++v) g->vec[v] = (void*)(g->ws + L.vec[v]);
     g->stage = (double*)(g->ws + L.stage);
+    g->ush = precision == ET_DF64 ? (float2*)(g->ws + L.ushadow) : nullptr;
     g->partial = (double*)(g->ws + L.partial);
     g->pair = nullptr;
     if (precision != ET_F64) {

@@ -66,6 +66,17 @@ __device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
     return dot_result(A);
 }
 
+// a + b of two pairs (TwoSum of the high parts, low parts added to the error,
+// one renormalisation).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    float hi, lo;
+    two_sum(s, e, hi, lo);
+    return make_float2(hi, lo);
+}
+
 // Merges two compensated accumulators into A.
 __device__ __forceinline__ void dot_merge(DotAcc& A, const DotAcc& B) {
     float s, e;

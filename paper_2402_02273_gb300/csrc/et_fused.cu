@@ -37,6 +37,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "et_df64_arith.h"
 #include "et_internal.h"
@@ -379,6 +380,7 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         T* const zout = a2.zout;
         T* const yout = a2.yacc;
         double* const uout = a2.u;
+        float2* const ushadow = static_cast<float2*>(a2.ush);  // DF64: the pair copy of u
         const int k0 = g.k0, k1 = g.k1;
         const int Llast = k1 + 1;  // planes k0 - 2 .. k1 + 1 are loaded
         const int gx = g.x0 + cx, gy = g.y0 + cy;
@@ -465,8 +467,14 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                     zout[p] = zb;
                 } else {
                     const T r = A::scale(gamma2, zb);
-                    if (uout) uout[p] += A::widen(r);
-                    else yout[p] = r;
+                    if (uout) {
+                        uout[p] += A::widen(r);
+                        if constexpr (std::is_same<T, float2>::value) {
+                            if (ushadow) ushadow[p] = df64::df_add(ushadow[p], r);
+                        }
+                    } else {
+                        yout[p] = r;
+                    }
                 }
             } else {
                 const T sb0 = kBaseZ ? reinterpret_cast<const T*>(s3 + S::kZj)[c12] : ysrc[p];
@@ -477,8 +485,14 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                     yout[p] = sb;
                 } else {
                     sb = A::scale(gamma2, sb);
-                    if (uout) uout[p] += A::widen(sb);
-                    else yout[p] = sb;
+                    if (uout) {
+                        uout[p] += A::widen(sb);
+                        if constexpr (std::is_same<T, float2>::value) {
+                            if (ushadow) ushadow[p] = df64::df_add(ushadow[p], sb);
+                        }
+                    } else {
+                        yout[p] = sb;
+                    }
                 }
             }
         };

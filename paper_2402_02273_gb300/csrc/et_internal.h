@@ -100,6 +100,7 @@ struct TermArgs {
     int horner;      // Horner step of sub-step 0: output acc itself (no running sum)
     T* yacc;         // sub-step sum (read when base_mode == 0, written unless finishing)
     double* u;       // non-null on the last term of the step: u += gamma * sum
+    void* ush;       // DF64 only, with u: the pair copy of u receives the same increment
 };
 
 // Arguments of one reverse Taylor-term launch (et_adjoint.cu).
@@ -259,6 +260,14 @@ cudaError_t launch_sum(long long n, const double* v, double* partial, double* ou
 // out[p] = u[p] + y[p] in FP64 (y widened as the last term of a step adds it)
 template <typename T>
 cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* out, cudaStream_t stream);
+// dst[p] = src[p] * scale as a pair (hi = nearest float, lo = the rest)
+cudaError_t launch_split(long long n, const double* src, double scale, float2* dst, cudaStream_t stream);
+// The residual of the DF64 form in pair arithmetic from the pair copy of u:
+// b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u (all
+// pairs; W holds the 1/nu-scaled weights with W.w[4] = -rowsum / nu).
+cudaError_t launch_residual_df64(const Geom& G, et_operator op, const float2* ush, Weights<float2> W, float2 nu,
+                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, float2* b, float2* dt,
+                                 unsigned* flags, cudaStream_t stream);
 // dst[p] = (float)(src[p] * scale)
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);
 

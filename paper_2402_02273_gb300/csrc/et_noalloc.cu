@@ -210,6 +210,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             a.last = (j + 1 == m);
             a.yacc = yacc;
             a.u = nullptr;
+            a.ush = nullptr;
             a.zout = a.last ? nullptr : Z[zi];
             if (a.last) {
                 a.gamma = gamma;

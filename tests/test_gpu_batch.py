@@ -263,7 +263,7 @@ PAIR_RHOS = [0.025, 0.04, 0.015, 0.03]
 
 
 @pytest.mark.parametrize("precision", ["f32", "df64"])
-def test_two_term_batch_matches_single_grids_bitwise(et_mod, torch_cuda, precision):
+def test_two_term_batch_matches_single_grids(et_mod, torch_cuda, precision):
     Ds, us = [], []
     for i, sh in enumerate(PAIR_SHAPES):
         D, u0 = phantom.case(sh, seed=20 + i, noise=0.1)
@@ -279,7 +279,11 @@ def test_two_term_batch_matches_single_grids_bitwise(et_mod, torch_cuda, precisi
                                      variant=v)
         for i in range(len(PAIR_SHAPES)):
             want, rec = _single_run(et_mod, torch_cuda, Ds[i], us[i], PAIR_RHOS[i], nsteps, precision)
-            assert np.array_equal(got[i], want), (v, i, np.abs(got[i] - want).max())
+            if precision == "f32":
+                assert np.array_equal(got[i], want), (v, i, np.abs(got[i] - want).max())
+            else:
+                # the single grid's DF64 residual runs in pair arithmetic, the batch's in FP64
+                assert _errs(got[i], want)[0] <= 1e-13, (v, i, _errs(got[i], want))
             if precision == "df64":
                 ref = oracle.Problem(Ds[i], rho=PAIR_RHOS[i]).run(us[i], TAU, nsteps)[0]
                 e_max, e_l2 = _errs(got[i], ref)

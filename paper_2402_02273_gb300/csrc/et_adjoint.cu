@@ -25,6 +25,7 @@
 
 #include <cfloat>
 
+#include "et_df64_arith.h"
 #include "et_internal.h"
 
 namespace et {
@@ -165,9 +166,7 @@ __global__ void cast_kernel(long long n, const double* __restrict__ src, double 
 __global__ void split_kernel(long long n, const double* __restrict__ src, double scale, float2* __restrict__ dst) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        const double x = src[p] * scale;
-        const float hi = (float)x;
-        dst[p] = make_float2(hi, (float)(x - (double)hi));
+        dst[p] = df64::from_double(__dmul_rn(src[p], scale));
     }
 }
 

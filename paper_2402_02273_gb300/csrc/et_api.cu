@@ -35,9 +35,10 @@ size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
 struct Layout {
     size_t w[5];      // FP64 coefficient fields (all forms; the residual reads them)
     size_t wt[5];     // typed, 1/nu-scaled copies of w[0..4] (F32, DF64)
+    size_t wpair[5];  // F32: the same scaled weights as pairs, read by the residual
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
-    size_t ushadow;   // DF64: u as pairs, read by the pair-arithmetic residual
+    size_t ushadow;   // F32, DF64: u as pairs, read by the pair-arithmetic residual
     size_t partial;   // 3 * nblocks doubles
     size_t misc;      // counters, flags, info slots
     size_t total;
@@ -65,9 +66,10 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     const size_t vb = value_bytes(prec);
     for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * n);
     for (int a = 0; a < 5; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * n) : SIZE_MAX;
+    for (int a = 0; a < 5; ++a) L->wpair[a] = (prec == ET_F32) ? take(8ull * n) : SIZE_MAX;
     for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * n);
     L->stage = take(8ull * n);
-    L->ushadow = prec == ET_DF64 ? take(8ull * n) : SIZE_MAX;
+    L->ushadow = prec != ET_F64 ? take(8ull * n) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks);
     L->misc = take(kMiscBytes);
     L->total = off;
@@ -134,7 +136,8 @@ struct et_grid {
     double* stage;
     double* partial;
     PairPlan* pair;  // tensor maps of the two-term kernel (F32 / DF64), or nullptr
-    float2* ush;     // DF64: the pair copy of u (nullptr otherwise)
+    float2* wres[5];  // F32, DF64: the 1/nu-scaled pair weights the residual reads
+    float2* ush;      // F32, DF64: the pair copy of u (nullptr for F64)
     unsigned long long* rmax_bits;
     unsigned* flags;
     unsigned* ticket;
@@ -281,7 +284,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                            !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
         T* const Y[2] = {B.Y[0], B.Y[1]};
         T* const Z[2] = {B.Z[0], B.Z[1]};
-        void* ush = std::is_same<T, float2>::value ? (void*)g->ush : nullptr;
+        void* ush = g->ush;
         for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs, ush)) {
             cudaError_t e;
             if constexpr (std::is_same<T, double>::value) {
@@ -359,26 +362,32 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
     return cudaSuccess;
 }
 
+// b and the shifted diagonal of the F32 / DF64 forms from the pair copy ush of u.
+template <typename T>
+cudaError_t enqueue_pair_residual(et_grid* g, const float2* ush, const Buffers<T>& B, double dt_shift,
+                                  cudaStream_t st) {
+    Weights<float2> WT;
+    for (int a = 0; a < 5; ++a) WT.w[a] = g->wres[a];
+    const double k_u = g->scheme == ET_SCHEME_ROSENBROCK ? -2.0 * g->rho / g->nu : 0.0;
+    return launch_residual_df64<T>(g->G, g->op, ush, WT, Scalar<float2>::make(g->nu), Scalar<float2>::make(g->rho),
+                                   Scalar<float2>::make(dt_shift / g->nu), Scalar<float2>::make(k_u), g->scheme,
+                                   const_cast<T*>(B.b), B.dt, g->flags, st);
+}
+
 template <typename T>
 et_status enqueue_form(et_grid* g, double* u, const Schedule& S, double hstep, double dt_shift,
                        cudaStream_t st, cudaEvent_t ev_begin, unsigned evflags, long long* term_launches,
                        long long* other_launches) {
     Buffers<T> B = typed_buffers<T>(g);
-    Weights<double> W64;
-    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
-    const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
     cudaError_t e;
-    if constexpr (std::is_same<T, float2>::value) {
-        // DF64: the residual in pair arithmetic from the pair copy of u, on the
-        // FP32 pipes (the FP64 residual is bound by GB300's FP64 rate)
-        Weights<float2> WT = B.W;
-        WT.w[4] = (const float2*)g->wt[4];
-        const double k_u = g->scheme == ET_SCHEME_ROSENBROCK ? -2.0 * g->rho / g->nu : 0.0;
-        e = launch_residual_df64(g->G, g->op, g->ush, WT, Scalar<float2>::make(g->nu), Scalar<float2>::make(g->rho),
-                                 Scalar<float2>::make(dt_shift / g->nu), Scalar<float2>::make(k_u), g->scheme,
-                                 const_cast<float2*>(B.b), B.dt, g->flags, st);
+    if constexpr (!std::is_same<T, double>::value) {
+        // F32, DF64: the residual in pair arithmetic from the pair copy of u, on
+        // the FP32 pipes (the FP64 residual is bound by GB300's FP64 rate)
+        e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st);
     } else {
-        e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, dt_scale, g->scheme, const_cast<T*>(B.b), B.dt,
+        Weights<double> W64;
+        for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+        e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
                                g->flags, st);
     }
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
@@ -432,6 +441,14 @@ et_status ensure_events(et_grid* g, int nsteps) {
     return ET_OK;
 }
 
+// The pair copy of u that the F32 / DF64 residual reads, taken at the start of
+// a run; the last term of every step keeps it current.
+et_status start_pair_copy(et_grid* g, const double* u, cudaStream_t st) {
+    const cudaError_t e = launch_split(g->n, u, 1.0, g->ush, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "split launch: %s", cudaGetErrorString(e));
+    return ET_OK;
+}
+
 // Enqueues a whole run (counter reset + nsteps steps) on stream st.
 et_status enqueue_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info, cudaStream_t st,
                       bool external_events) {
@@ -443,9 +460,8 @@ et_status enqueue_run(et_grid* g, double* u, double tau, int nsteps, et_step_inf
     const int stride = info ? 1 : 0;
     long long tl = 0, ol = 0;
     if (g->ush) {
-        // the pair copy of u that the DF64 residual reads; the steps keep it current
-        const cudaError_t e = launch_split(g->n, u, 1.0, g->ush, st);
-        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "split launch: %s", cudaGetErrorString(e));
+        rc = start_pair_copy(g, u, st);
+        if (rc != ET_OK) return rc;
         ++ol;
     }
     for (int t = 0; t < nsteps; ++t) {
@@ -563,6 +579,9 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
             float* dst[4] = {(float*)g->wt[0], (float*)g->wt[1], (float*)g->wt[2], (float*)g->wt[3]};
             e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
             if (e == cudaSuccess) e = launch_cast(g->n, g->w[4], 1.0 / g->nu, (float*)g->wt[4], g->stream);
+            float2* pdst[4] = {g->wres[0], g->wres[1], g->wres[2], g->wres[3]};
+            if (e == cudaSuccess) e = launch_convert_weights(g->G, src, pdst, 1.0 / g->nu, g->stream);
+            if (e == cudaSuccess) e = launch_split(g->n, g->w[4], 1.0 / g->nu, g->wres[4], g->stream);
         } else {
             float2* dst[4] = {(float2*)g->wt[0], (float2*)g->wt[1], (float2*)g->wt[2], (float2*)g->wt[3]};
             e = launch_convert_weights(g->G, src, dst, 1.0 / g->nu, g->stream);
@@ -650,9 +669,16 @@ et_status record_step(et_grid* g, const Schedule& S, double hstep, const double*
     Weights<double> W64;
     for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
     const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
-    const double dt_scale = g->prec == ET_F64 ? 1.0 : 1.0 / g->nu;
-    cudaError_t e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, dt_scale, g->scheme,
-                                       const_cast<T*>(B.b), B.dt, g->flags, st);
+    cudaError_t e;
+    if constexpr (std::is_same<T, double>::value) {
+        e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
+                               g->flags, st);
+    } else {
+        // the residual of the forward step: from the pair nearest u^n, which is
+        // the pair copy the forward run keeps
+        e = launch_split(g->n, un, 1.0, g->ush, st);
+        if (e == cudaSuccess) e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st);
+    }
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
     long long launches = 0;
     e = enqueue_chain<T>(g, B, nullptr, S, hstep, st, &launches, &rec);
@@ -766,6 +792,10 @@ et_status forward_checkpoints(et_grid* g, double* u, double tau, int nsteps, con
     double* ckpt = (double*)(ws + A.ckpt);
     long long tl = 0, ol = 0;
     ET_CUDA(g, cudaMemcpyAsync(ckpt, u, nb, cudaMemcpyDeviceToDevice, st));
+    if (g->ush) {
+        const et_status rc = start_pair_copy(g, u, st);
+        if (rc != ET_OK) return rc;
+    }
     const int last = full ? nsteps : nsteps - 1;
     for (int t = 0; t < last; ++t) {
         et_status rc = enqueue_step(g, u, tau, S, g->info_slot, 0, st, nullptr, nullptr, false, &tl, &ol);
@@ -976,7 +1006,11 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     for (int a = 0; a < 5; ++a) g->wt[a] = precision != ET_F64 ? (void*)(g->ws + L.wt[a]) : nullptr;
     for (int v = 0; v < 6; ++v) g->vec[v] = (void*)(g->ws + L.vec[v]);
     g->stage = (double*)(g->ws + L.stage);
-    g->ush = precision == ET_DF64 ? (float2*)(g->ws + L.ushadow) : nullptr;
+    g->ush = precision != ET_F64 ? (float2*)(g->ws + L.ushadow) : nullptr;
+    for (int a = 0; a < 5; ++a)
+        g->wres[a] = precision == ET_F32    ? (float2*)(g->ws + L.wpair[a])
+                     : precision == ET_DF64 ? (float2*)g->wt[a]
+                                            : nullptr;
     g->partial = (double*)(g->ws + L.partial);
     g->pair = nullptr;
     if (precision != ET_F64) {

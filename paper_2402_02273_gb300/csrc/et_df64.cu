@@ -212,15 +212,19 @@ int df64_blocks_per_sm() {
     return cached;
 }
 
-// Residual of the DF64 form from the pair copy of u, one voxel per thread:
-// S = (L / nu) u by the stencil code of the terms (diagonal W.w[4] = -rowsum/nu),
-// b = nu S + rho u (1 - u), dt = W.w[4] + shift + k_u u (k_u = -2 rho / nu for
-// the folded reaction, 0 otherwise).
-template <int OP>
+// Residual of the FP32 and DF64 forms from the pair copy of u, one voxel per
+// thread: S = (L / nu) u by the stencil code of the terms (diagonal W.w[4] =
+// -rowsum/nu), b = nu S + rho u (1 - u), dt = W.w[4] + shift + k_u u (k_u =
+// -2 rho / nu for the folded reaction, 0 otherwise).  FP32 outputs take the
+// high part of the normalised pair (the nearest float).
+__device__ __forceinline__ void store_pair(float2* d, float2 v) { *d = v; }
+__device__ __forceinline__ void store_pair(float* d, float2 v) { *d = v.x; }
+
+template <int OP, typename TO>
 __global__ void __launch_bounds__(kThreads)
 residual_df64_kernel(const __grid_constant__ Geom G, const float2* __restrict__ ush,
                      const __grid_constant__ Weights<float2> W, float2 nu, float2 rho, float2 shift, float2 k_u,
-                     int scheme, float2* __restrict__ b, float2* __restrict__ dt, unsigned* flags) {
+                     int scheme, TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
@@ -238,8 +242,8 @@ residual_df64_kernel(const __grid_constant__ Geom G, const float2* __restrict__ 
                                     W.w[2][p], (k + 1 < G.nz) ? ush[p + G.sz] : zero, wzm, zmk ? ush[p - G.sz] : zero,
                                     zero, false, zero, zero);
     const float2 one_minus_u = df_add(make_float2(1.f, 0.f), make_float2(-uc.x, -uc.y));
-    b[p] = df_add(df_mul(nu, S), df_mul(rho, df_mul(uc, one_minus_u)));
-    dt[p] = df_add(w4, df_fma(k_u, uc, shift));
+    store_pair(&b[p], df_add(df_mul(nu, S), df_mul(rho, df_mul(uc, one_minus_u))));
+    store_pair(&dt[p], df_add(w4, df_fma(k_u, uc, shift)));
     const float uh = uc.x;
     if (!isfinite(uh)) atomicOr(flags, ET_FLAG_NONFINITE);
     if (scheme == ET_SCHEME_ROSENBROCK && (uh < (float)-kRangeSlack || uh > (float)(1.0 + kRangeSlack)))
@@ -248,19 +252,27 @@ residual_df64_kernel(const __grid_constant__ Geom G, const float2* __restrict__ 
 
 }  // namespace
 
+template <typename TO>
 cudaError_t launch_residual_df64(const Geom& G, et_operator op, const float2* ush, Weights<float2> W, float2 nu,
-                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, float2* b, float2* dt,
+                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, TO* b, TO* dt,
                                  unsigned* flags, cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     const dim3 grid((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
     if (op == ET_OP_CONSERVATIVE)
-        residual_df64_kernel<ET_OP_CONSERVATIVE><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u,
-                                                                              (int)scheme, b, dt, flags);
+        residual_df64_kernel<ET_OP_CONSERVATIVE, TO><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u,
+                                                                                  (int)scheme, b, dt, flags);
     else
-        residual_df64_kernel<ET_OP_LITERAL><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u, (int)scheme,
-                                                                         b, dt, flags);
+        residual_df64_kernel<ET_OP_LITERAL, TO><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u,
+                                                                             (int)scheme, b, dt, flags);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_residual_df64<float2>(const Geom&, et_operator, const float2*, Weights<float2>, float2,
+                                                  float2, float2, float2, et_scheme, float2*, float2*, unsigned*,
+                                                  cudaStream_t);
+template cudaError_t launch_residual_df64<float>(const Geom&, et_operator, const float2*, Weights<float2>, float2,
+                                                 float2, float2, float2, et_scheme, float*, float*, unsigned*,
+                                                 cudaStream_t);
 
 cudaError_t prime_launch_limits_df64() {
     df64_blocks_per_sm<ET_OP_CONSERVATIVE>();

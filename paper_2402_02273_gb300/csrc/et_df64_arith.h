@@ -14,6 +14,13 @@
 namespace et {
 namespace df64 {
 
+// The pair nearest an FP64 value: hi = fl32(v), lo = fl32(v - hi) (the
+// subtraction is exact; |v - (hi + lo)| <= 2^-48 |v| barring underflow).
+__device__ __forceinline__ float2 from_double(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);

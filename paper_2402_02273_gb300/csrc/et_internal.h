@@ -262,11 +262,13 @@ template <typename T>
 cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* out, cudaStream_t stream);
 // dst[p] = src[p] * scale as a pair (hi = nearest float, lo = the rest)
 cudaError_t launch_split(long long n, const double* src, double scale, float2* dst, cudaStream_t stream);
-// The residual of the DF64 form in pair arithmetic from the pair copy of u:
-// b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u (all
-// pairs; W holds the 1/nu-scaled weights with W.w[4] = -rowsum / nu).
+// The residual of the FP32 and DF64 forms in pair arithmetic from the pair
+// copy of u: b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u
+// (W: the 1/nu-scaled pair weights with W.w[4] = -rowsum / nu), stored in the
+// form's value type.
+template <typename TO>
 cudaError_t launch_residual_df64(const Geom& G, et_operator op, const float2* ush, Weights<float2> W, float2 nu,
-                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, float2* b, float2* dt,
+                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, TO* b, TO* dt,
                                  unsigned* flags, cudaStream_t stream);
 // dst[p] = (float)(src[p] * scale)
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);

@@ -30,6 +30,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "et_df64_arith.h"
 #include "et_internal.h"
 
 namespace et {
@@ -213,6 +214,15 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
     T* __restrict__ zout = a.zout;
     T* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
+    float2* __restrict__ ush = static_cast<float2*>(a.ush);  // FP32: the pair copy of u
+    // u^{n+1} = u^n + gamma * sum, and (FP32 form) its pair copy for the residual
+    auto update_u = [&](long long q, T r) {
+        const double un = u[q] + widened_product(r, a.gamma);
+        u[q] = un;
+        if constexpr (std::is_same<T, float>::value) {
+            if (ush) ush[q] = df64::from_double(un);
+        }
+    };
     const int k0 = tz * TZ;
     const int k1 = min(k0 + TZ, G.nz);
     long long p = i + G.sy * j + G.sz * k0;
@@ -238,7 +248,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
         if (a.has_beta) acc = fma(a.beta, bv[p], acc);
         if (a.horner) {
             if (!a.last) zout[p] = acc;
-            else if (u) u[p] += widened_product(acc, a.gamma);
+            else if (u) update_u(p, acc);
             else yacc[p] = acc * a.gamma;
         } else {
             T base;
@@ -250,7 +260,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
                 zout[p] = acc;
                 yacc[p] = sum;
             } else if (u) {
-                u[p] += widened_product(sum, a.gamma);
+                update_u(p, sum);
             } else {
                 yacc[p] = sum * a.gamma;
             }

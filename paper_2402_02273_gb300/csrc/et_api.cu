@@ -38,7 +38,7 @@ struct Layout {
     size_t wpair[5];  // F32: the same scaled weights as pairs, read by the residual
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
-    size_t ushadow;   // F32, DF64: u as pairs, read by the pair-arithmetic residual
+    size_t ushadow;   // F32, DF64: the pair nearest each u, read by the pair-arithmetic residual
     size_t partial;   // 3 * nblocks doubles
     size_t misc;      // counters, flags, info slots
     size_t total;
@@ -284,8 +284,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                            !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
         T* const Y[2] = {B.Y[0], B.Y[1]};
         T* const Z[2] = {B.Z[0], B.Z[1]};
-        void* ush = g->ush;
-        for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs, ush)) {
+        for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs)) {
             cudaError_t e;
             if constexpr (std::is_same<T, double>::value) {
                 e = launch_term(g->G, g->op, B.W, op.a1, st);
@@ -323,7 +322,6 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         a.horner = t.horner;
         a.yacc = rec->y(k + 1);
         a.u = nullptr;
-        a.ush = nullptr;
         a.zout = t.last ? nullptr : rec->z(k, j + 1);
         return a;
     };
@@ -366,12 +364,8 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
 template <typename T>
 cudaError_t enqueue_pair_residual(et_grid* g, const float2* ush, const Buffers<T>& B, double dt_shift,
                                   cudaStream_t st) {
-    Weights<float2> WT;
-    for (int a = 0; a < 5; ++a) WT.w[a] = g->wres[a];
-    const double k_u = g->scheme == ET_SCHEME_ROSENBROCK ? -2.0 * g->rho / g->nu : 0.0;
-    return launch_residual_df64<T>(g->G, g->op, ush, WT, Scalar<float2>::make(g->nu), Scalar<float2>::make(g->rho),
-                                   Scalar<float2>::make(dt_shift / g->nu), Scalar<float2>::make(k_u), g->scheme,
-                                   const_cast<T*>(B.b), B.dt, g->flags, st);
+    const PairResidualArgs R = pair_residual_args(ush, g->wres, g->nu, g->rho, dt_shift, g->scheme);
+    return launch_residual_df64<T>(g->G, g->op, R, g->scheme, const_cast<T*>(B.b), B.dt, g->flags, st);
 }
 
 template <typename T>
@@ -412,6 +406,7 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
     sink.last = g->info_slot;
     sink.s = S.s;
     sink.m = S.m;
+    sink.ush = g->ush;
     const double hstep = tau / S.s;
     const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
     const unsigned evflags = external_events ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -442,7 +437,7 @@ et_status ensure_events(et_grid* g, int nsteps) {
 }
 
 // The pair copy of u that the F32 / DF64 residual reads, taken at the start of
-// a run; the last term of every step keeps it current.
+// a run; the stats launch that ends every step writes it for the next one.
 et_status start_pair_copy(et_grid* g, const double* u, cudaStream_t st) {
     const cudaError_t e = launch_split(g->n, u, 1.0, g->ush, st);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "split launch: %s", cudaGetErrorString(e));
@@ -674,8 +669,7 @@ et_status record_step(et_grid* g, const Schedule& S, double hstep, const double*
         e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
                                g->flags, st);
     } else {
-        // the residual of the forward step: from the pair nearest u^n, which is
-        // the pair copy the forward run keeps
+        // the residual of the forward step, from the pair nearest u^n
         e = launch_split(g->n, un, 1.0, g->ush, st);
         if (e == cudaSuccess) e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st);
     }

@@ -54,7 +54,8 @@ size_t desc_bytes_per_instance(et_precision prec) {
 }
 
 struct BatchLayout {
-    size_t w[5], wt[5], vec[6], stage, partial, desc, tune_desc, misc;
+    // wpair: F32 pair weights of the residual; ush: F32 / DF64 pair copy of u
+    size_t w[5], wt[5], wpair[5], vec[6], stage, ush, partial, desc, tune_desc, misc;
     size_t total;
     long long ntot;
 };
@@ -82,8 +83,10 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
     };
     for (int a = 0; a < 5; ++a) L->w[a] = take(8ull * ntot);
     for (int a = 0; a < 5; ++a) L->wt[a] = (prec != ET_F64) ? take(vb * ntot) : SIZE_MAX;
+    for (int a = 0; a < 5; ++a) L->wpair[a] = (prec == ET_F32) ? take(8ull * ntot) : SIZE_MAX;
     for (int v = 0; v < 6; ++v) L->vec[v] = take(vb * ntot);
     L->stage = take(8ull * ntot);
+    L->ush = (prec != ET_F64) ? take(8ull * ntot) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks * count);
     L->desc = take(desc_bytes_per_instance(prec) * count);
     L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec)) * count + 256);
@@ -200,6 +203,11 @@ T* field(et_batch* b, size_t region, int i) {
     return (T*)(b->ws + region) + b->offs[i];
 }
 
+// Pair weight a of grid i read by the F32 / DF64 residual.
+float2* pair_weight(et_batch* b, int a, int i) {
+    return field<float2>(b, b->prec == ET_F32 ? b->L.wpair[a] : b->L.wt[a], i);
+}
+
 et_status sched_of(const et_batch* b, int i, double tau, Sched* S) {
     const et_status rc = et_select_schedule(tau, b->rmax[i], b->rho[i], b->scheme, b->prec,
                                             b->opt_set ? &b->opt : nullptr, &S->s, &S->m, &S->mu, &S->theta);
@@ -254,6 +262,12 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         r.rho = b->rho[i];
         r.dt_shift = (b->scheme == ET_SCHEME_ROSENBROCK ? b->rho[i] : 0.0) - S[i].mu;
         r.dt_scale = b->prec == ET_F64 ? 1.0 : 1.0 / b->nu[i];
+        std::memset(&r.P, 0, sizeof(r.P));
+        if (b->prec != ET_F64) {
+            float2* wres[5];
+            for (int a = 0; a < 5; ++a) wres[a] = pair_weight(b, a, i);
+            r.P = pair_residual_args(field<float2>(b, b->L.ush, i), wres, b->nu[i], b->rho[i], r.dt_shift, b->scheme);
+        }
         r.b = field<T>(b, b->L.vec[0], i);
         r.dt = field<T>(b, b->L.vec[1], i);
         r.tile_begin = rt;
@@ -331,6 +345,7 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         sk.last = slot_of(b, i);
         sk.s = S[i].s;
         sk.m = S[i].m;
+        sk.ush = b->prec != ET_F64 ? field<float2>(b, b->L.ush, i) : nullptr;
     }
     // [residual x C][stats x C][single terms][pad to 64 bytes][two-term]
     const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
@@ -509,6 +524,11 @@ et_status run_impl(et_batch* b, double* u, double tau, int nsteps, et_step_info*
     rc = ET_OK;
     for (int i = 0; i < b->count && rc == ET_OK; ++i)
         if (cudaMemsetAsync(counter_of(b, i), 0, sizeof(unsigned), b->capture) != cudaSuccess) rc = ET_ERR_CUDA;
+    // the pair copy of u for the first residual (F32 / DF64); each step's
+    // stats launch writes it for the next
+    if (rc == ET_OK && b->prec != ET_F64 &&
+        launch_split(b->ntot, u, 1.0, field<float2>(b, b->L.ush, 0), b->capture) != cudaSuccess)
+        rc = ET_ERR_CUDA;
     for (int t = 0; t < nsteps && rc == ET_OK; ++t) rc = enqueue_batch_step<T>(b, b->ws + b->L.desc, b->capture);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
@@ -682,6 +702,12 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
                 for (int a = 0; a < 4; ++a) dst[a] = field<float2>(b, b->L.wt[a], i);
                 e = launch_convert_weights(G, src, dst, 1.0 / b->nu[i], b->stream);
             }
+            // the pair weights of the residual (DF64: the term weights themselves)
+            float2* pw[4];
+            for (int a = 0; a < 4; ++a) pw[a] = pair_weight(b, a, i);
+            if (e == cudaSuccess && b->prec == ET_F32) e = launch_convert_weights(G, src, pw, 1.0 / b->nu[i], b->stream);
+            if (e == cudaSuccess)
+                e = launch_split(G.n, field<double>(b, b->L.w[4], i), 1.0 / b->nu[i], pair_weight(b, 4, i), b->stream);
             if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "weight conversion: %s", cudaGetErrorString(e));
         }
     }

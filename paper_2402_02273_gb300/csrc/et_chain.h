@@ -20,14 +20,13 @@ struct ChainOp {
 };
 
 // Buffers: b (also z_0 of sub-step 0), dt (diagonal), Y[2] (sub-step sums,
-// ping-pong), Z[2] (terms, ping-pong); u receives the finished step, and
-// ush (DF64, optional) the same increment in pair arithmetic.  With
+// ping-pong), Z[2] (terms, ping-pong); u receives the finished step.  With
 // pairs, two consecutive terms of one sub-step share a launch; the first
 // term's outputs are then not written and the term buffers alternate per
 // launch.
 template <typename T>
 std::vector<ChainOp<T>> chain_ops(const ChainPlan& P, int s, const T* b, const T* dt, T* const Y[2], T* const Z[2],
-                                  double* u, bool pairs, void* ush = nullptr) {
+                                  double* u, bool pairs) {
     std::vector<ChainOp<T>> ops;
     ops.reserve(P.terms.size());
     int zi = 0;  // next z buffer to write
@@ -52,7 +51,6 @@ std::vector<ChainOp<T>> chain_ops(const ChainPlan& P, int s, const T* b, const T
         a.horner = t.horner;
         a.yacc = Y[(k + 1) & 1];
         a.u = (t.last && k == s - 1) ? u : nullptr;
-        a.ush = a.u ? ush : nullptr;
         a.zout = t.last ? nullptr : Z[zi];
         return a;
     };

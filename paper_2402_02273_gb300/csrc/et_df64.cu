@@ -14,6 +14,7 @@
 
 #include "et_df64_arith.h"
 #include "et_internal.h"
+#include "et_residual_pair.h"
 
 namespace et {
 namespace {
@@ -45,7 +46,6 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
     float2* __restrict__ zout = a.zout;
     float2* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
-    float2* __restrict__ ush = static_cast<float2*>(a.ush);
     const float2 zero = make_float2(0.f, 0.f);
     const bool need_b = a.has_beta || (!a.horner && a.base_mode == 1);
     const bool need_y = !a.horner && a.base_mode == 0;
@@ -91,12 +91,8 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
                 zout[p] = acc;
             } else {
                 const float2 r = df_mul(a.gamma, acc);
-                if (u) {
-                    u[p] += (double)r.x + (double)r.y;
-                    if (ush) ush[p] = df_add(ush[p], r);
-                } else {
-                    yacc[p] = r;
-                }
+                if (u) u[p] += (double)r.x + (double)r.y;
+                else yacc[p] = r;
             }
         } else {
             float2 base;
@@ -109,12 +105,8 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
                 yacc[p] = sum;
             } else {
                 sum = df_mul(a.gamma, sum);
-                if (u) {
-                    u[p] += (double)sum.x + (double)sum.y;
-                    if (ush) ush[p] = df_add(ush[p], sum);
-                } else {
-                    yacc[p] = sum;
-                }
+                if (u) u[p] += (double)sum.x + (double)sum.y;
+                else yacc[p] = sum;
             }
         }
         zm = zc;
@@ -212,67 +204,34 @@ int df64_blocks_per_sm() {
     return cached;
 }
 
-// Residual of the FP32 and DF64 forms from the pair copy of u, one voxel per
-// thread: S = (L / nu) u by the stencil code of the terms (diagonal W.w[4] =
-// -rowsum/nu), b = nu S + rho u (1 - u), dt = W.w[4] + shift + k_u u (k_u =
-// -2 rho / nu for the folded reaction, 0 otherwise).  FP32 outputs take the
-// high part of the normalised pair (the nearest float).
-__device__ __forceinline__ void store_pair(float2* d, float2 v) { *d = v; }
-__device__ __forceinline__ void store_pair(float* d, float2 v) { *d = v.x; }
-
 template <int OP, typename TO>
 __global__ void __launch_bounds__(kThreads)
-residual_df64_kernel(const __grid_constant__ Geom G, const float2* __restrict__ ush,
-                     const __grid_constant__ Weights<float2> W, float2 nu, float2 rho, float2 shift, float2 k_u,
-                     int scheme, TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags) {
+residual_df64_kernel(const __grid_constant__ Geom G, const __grid_constant__ PairResidualArgs R, int scheme,
+                     TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
-    const int k = blockIdx.z;
     if (i >= G.nx || j >= G.ny) return;
-    const long long p = i + G.sy * j + G.sz * k;
-    const float2 zero = make_float2(0.f, 0.f);
-    const float2 uc = ush[p];
-    const float2 w4 = W.w[4][p];
-    const bool xm = i > 0, ym = j > 0, zmk = k > 0;
-    const float2 wxm = xm ? (OP == ET_OP_CONSERVATIVE ? W.w[0][p - 1] : W.w[3][p]) : zero;
-    const float2 wym = ym ? (OP == ET_OP_CONSERVATIVE ? W.w[1][p - G.sy] : W.w[3][p]) : zero;
-    const float2 wzm = zmk ? (OP == ET_OP_CONSERVATIVE ? W.w[2][p - G.sz] : W.w[3][p]) : zero;
-    const float2 S = stencil<false>(w4, uc, W.w[0][p], (i + 1 < G.nx) ? ush[p + 1] : zero, wxm, xm ? ush[p - 1] : zero,
-                                    W.w[1][p], (j + 1 < G.ny) ? ush[p + G.sy] : zero, wym, ym ? ush[p - G.sy] : zero,
-                                    W.w[2][p], (k + 1 < G.nz) ? ush[p + G.sz] : zero, wzm, zmk ? ush[p - G.sz] : zero,
-                                    zero, false, zero, zero);
-    const float2 one_minus_u = df_add(make_float2(1.f, 0.f), make_float2(-uc.x, -uc.y));
-    store_pair(&b[p], df_add(df_mul(nu, S), df_mul(rho, df_mul(uc, one_minus_u))));
-    store_pair(&dt[p], df_add(w4, df_fma(k_u, uc, shift)));
-    const float uh = uc.x;
-    if (!isfinite(uh)) atomicOr(flags, ET_FLAG_NONFINITE);
-    if (scheme == ET_SCHEME_ROSENBROCK && (uh < (float)-kRangeSlack || uh > (float)(1.0 + kRangeSlack)))
-        atomicOr(flags, ET_FLAG_RANGE_IN);
+    residual_pair_point<OP, TO>(G, R, scheme, b, dt, flags, i, j, blockIdx.z);
 }
 
 }  // namespace
 
 template <typename TO>
-cudaError_t launch_residual_df64(const Geom& G, et_operator op, const float2* ush, Weights<float2> W, float2 nu,
-                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, TO* b, TO* dt,
-                                 unsigned* flags, cudaStream_t stream) {
+cudaError_t launch_residual_df64(const Geom& G, et_operator op, const PairResidualArgs& R, et_scheme scheme, TO* b,
+                                 TO* dt, unsigned* flags, cudaStream_t stream) {
     const dim3 block(kBlockX, kBlockY, 1);
     const dim3 grid((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
     if (op == ET_OP_CONSERVATIVE)
-        residual_df64_kernel<ET_OP_CONSERVATIVE, TO><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u,
-                                                                                  (int)scheme, b, dt, flags);
+        residual_df64_kernel<ET_OP_CONSERVATIVE, TO><<<grid, block, 0, stream>>>(G, R, (int)scheme, b, dt, flags);
     else
-        residual_df64_kernel<ET_OP_LITERAL, TO><<<grid, block, 0, stream>>>(G, ush, W, nu, rho, shift, k_u,
-                                                                             (int)scheme, b, dt, flags);
+        residual_df64_kernel<ET_OP_LITERAL, TO><<<grid, block, 0, stream>>>(G, R, (int)scheme, b, dt, flags);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_residual_df64<float2>(const Geom&, et_operator, const float2*, Weights<float2>, float2,
-                                                  float2, float2, float2, et_scheme, float2*, float2*, unsigned*,
-                                                  cudaStream_t);
-template cudaError_t launch_residual_df64<float>(const Geom&, et_operator, const float2*, Weights<float2>, float2,
-                                                 float2, float2, float2, et_scheme, float*, float*, unsigned*,
-                                                 cudaStream_t);
+template cudaError_t launch_residual_df64<float2>(const Geom&, et_operator, const PairResidualArgs&, et_scheme,
+                                                  float2*, float2*, unsigned*, cudaStream_t);
+template cudaError_t launch_residual_df64<float>(const Geom&, et_operator, const PairResidualArgs&, et_scheme, float*,
+                                                 float*, unsigned*, cudaStream_t);
 
 cudaError_t prime_launch_limits_df64() {
     df64_blocks_per_sm<ET_OP_CONSERVATIVE>();

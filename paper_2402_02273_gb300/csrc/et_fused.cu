@@ -380,8 +380,6 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         T* const zout = a2.zout;
         T* const yout = a2.yacc;
         double* const uout = a2.u;
-        // FP32, DF64: the pair copy of u (single grids only)
-        float2* const ushadow = kTable ? nullptr : static_cast<float2*>(a2.ush);
         const int k0 = g.k0, k1 = g.k1;
         const int Llast = k1 + 1;  // planes k0 - 2 .. k1 + 1 are loaded
         const int gx = g.x0 + cx, gy = g.y0 + cy;
@@ -460,16 +458,6 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                                               Ac[ca + kHaloX], wym, Ac[ca - kHaloX], wzp, Ap[ca], wzm, Am[ca], zero,
                                               hb2, beta2, bval);
         };
-        // u^{n+1} = u^n + r and its pair copy for the residual: DF64 adds r to
-        // the copy in pair arithmetic, FP32 takes the pair nearest u^{n+1}
-        auto update_u = [&](long long p, T r) {
-            const double un = uout[p] + A::widen(r);
-            uout[p] = un;
-            if (ushadow) {
-                if constexpr (std::is_same<T, float2>::value) ushadow[p] = df64::df_add(ushadow[p], r);
-                else ushadow[p] = df64::from_double(un);
-            }
-        };
         auto second_store = [&](int q, T zb, T acen) {
             const long long p = pc + sz * q;
             if (zfirst) zfirst[p] = acen;  // a recorded chain keeps the first term too
@@ -478,11 +466,8 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                     zout[p] = zb;
                 } else {
                     const T r = A::scale(gamma2, zb);
-                    if (uout) {
-                        update_u(p, r);
-                    } else {
-                        yout[p] = r;
-                    }
+                    if (uout) uout[p] += A::widen(r);
+                    else yout[p] = r;
                 }
             } else {
                 const T sb0 = kBaseZ ? reinterpret_cast<const T*>(s3 + S::kZj)[c12] : ysrc[p];
@@ -493,11 +478,8 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
                     yout[p] = sb;
                 } else {
                     sb = A::scale(gamma2, sb);
-                    if (uout) {
-                        update_u(p, sb);
-                    } else {
-                        yout[p] = sb;
-                    }
+                    if (uout) uout[p] += A::widen(sb);
+                    else yout[p] = sb;
                 }
             }
         };

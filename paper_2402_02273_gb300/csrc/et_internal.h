@@ -59,6 +59,7 @@ struct StatsSink {
     int info_stride;        // records step t at info[t * info_stride] (0: always info[0])
     et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
     int s, m;               // recorded in the info
+    float2* ush;            // F32 / DF64: receives the pair nearest each u (nullptr: none)
 };
 
 // Scalars of the kernels' value types: double (FP64), float (FP32) and
@@ -100,7 +101,6 @@ struct TermArgs {
     int horner;      // Horner step of sub-step 0: output acc itself (no running sum)
     T* yacc;         // sub-step sum (read when base_mode == 0, written unless finishing)
     double* u;       // non-null on the last term of the step: u += gamma * sum
-    void* ush;       // DF64 only, with u: the pair copy of u receives the same increment
 };
 
 // Arguments of one reverse Taylor-term launch (et_adjoint.cu).
@@ -137,12 +137,24 @@ struct BatchTerm {
     long long tile_begin;
 };
 
+// Inputs of the pair-arithmetic residual of the F32 and DF64 forms: the pair
+// nearest each u, the 1/nu-scaled pair weights (w[4] = -rowsum / nu), nu,
+// rho, the diagonal shift / nu and the coefficient of u in the diagonal.
+struct PairResidualArgs {
+    const float2* ush;
+    Weights<float2> W;
+    float2 nu, rho, shift, k_u;
+};
+
+// One grid of the batched residual: FP64 from u (F64 form) or in pair
+// arithmetic from P (F32, DF64).
 template <typename T>
 struct BatchResidual {
     Geom G;
     const double* u;
     Weights<double> W;
     double rho, dt_shift, dt_scale;
+    PairResidualArgs P;
     T* b;
     T* dt;
     long long tile_begin;
@@ -263,13 +275,24 @@ cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* o
 // dst[p] = src[p] * scale as a pair (hi = nearest float, lo = the rest)
 cudaError_t launch_split(long long n, const double* src, double scale, float2* dst, cudaStream_t stream);
 // The residual of the FP32 and DF64 forms in pair arithmetic from the pair
-// copy of u: b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u
-// (W: the 1/nu-scaled pair weights with W.w[4] = -rowsum / nu), stored in the
-// form's value type.
+// copy of u: b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u,
+// stored in the form's value type.
+// PairResidualArgs of a grid with scaling nu, rate rho and the diagonal shift
+// (rho for the folded reaction, minus the series shift mu).
+inline PairResidualArgs pair_residual_args(const float2* ush, float2* const w[5], double nu, double rho,
+                                           double dt_shift, et_scheme scheme) {
+    PairResidualArgs R;
+    R.ush = ush;
+    for (int a = 0; a < 5; ++a) R.W.w[a] = w[a];
+    R.nu = Scalar<float2>::make(nu);
+    R.rho = Scalar<float2>::make(rho);
+    R.shift = Scalar<float2>::make(dt_shift / nu);
+    R.k_u = Scalar<float2>::make(scheme == ET_SCHEME_ROSENBROCK ? -2.0 * rho / nu : 0.0);
+    return R;
+}
 template <typename TO>
-cudaError_t launch_residual_df64(const Geom& G, et_operator op, const float2* ush, Weights<float2> W, float2 nu,
-                                 float2 rho, float2 shift, float2 k_u, et_scheme scheme, TO* b, TO* dt,
-                                 unsigned* flags, cudaStream_t stream);
+cudaError_t launch_residual_df64(const Geom& G, et_operator op, const PairResidualArgs& R, et_scheme scheme, TO* b,
+                                 TO* dt, unsigned* flags, cudaStream_t stream);
 // dst[p] = (float)(src[p] * scale)
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);
 

@@ -32,6 +32,7 @@
 
 #include "et_df64_arith.h"
 #include "et_internal.h"
+#include "et_residual_pair.h"
 
 namespace et {
 namespace {
@@ -214,15 +215,6 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
     T* __restrict__ zout = a.zout;
     T* __restrict__ yacc = a.yacc;
     double* __restrict__ u = a.u;
-    float2* __restrict__ ush = static_cast<float2*>(a.ush);  // FP32: the pair copy of u
-    // u^{n+1} = u^n + gamma * sum, and (FP32 form) its pair copy for the residual
-    auto update_u = [&](long long q, T r) {
-        const double un = u[q] + widened_product(r, a.gamma);
-        u[q] = un;
-        if constexpr (std::is_same<T, float>::value) {
-            if (ush) ush[q] = df64::from_double(un);
-        }
-    };
     const int k0 = tz * TZ;
     const int k1 = min(k0 + TZ, G.nz);
     long long p = i + G.sy * j + G.sz * k0;
@@ -248,7 +240,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
         if (a.has_beta) acc = fma(a.beta, bv[p], acc);
         if (a.horner) {
             if (!a.last) zout[p] = acc;
-            else if (u) update_u(p, acc);
+            else if (u) u[p] += widened_product(acc, a.gamma);
             else yacc[p] = acc * a.gamma;
         } else {
             T base;
@@ -260,7 +252,7 @@ __device__ __forceinline__ void term_column(const Geom& G, const Weights<T>& W, 
                 zout[p] = acc;
                 yacc[p] = sum;
             } else if (u) {
-                update_u(p, sum);
+                u[p] += widened_product(sum, a.gamma);
             } else {
                 yacc[p] = sum * a.gamma;
             }
@@ -345,7 +337,8 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
 
 // ---------------------------------------------------------------------------
 // stats: sum, min and max of u (min/max through integer order keys, one FP64
-// add per voxel), the non-finite flag, then the step record.  A fixed grid of
+// add per voxel), the non-finite flag, then the step record; the F32 and DF64
+// forms also take here the pair nearest each u, which their next residual reads.  A fixed grid of
 // kStatsBlocks blocks fixes every summation order (bitwise reproducible).
 // Block `blk` (of kStatsBlocks) of the reduction over u[0..n).
 __device__ __forceinline__ void stats_body(long long n, const double* __restrict__ u, const StatsSink& s, int blk) {
@@ -360,6 +353,7 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
     bool bad = false;
     for (long long p = blk * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
         const double v = u[p];
+        if (s.ush) s.ush[p] = df64::from_double(v);
         sum += v;
         const unsigned long long key = order_key(v);
         kmin = key < kmin ? key : kmin;
@@ -488,7 +482,10 @@ batch_residual_kernel(const BatchResidual<T>* __restrict__ d, int count, int sch
     const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
     const int k = (int)(rest / tiles_y);
     if (i >= sd.G.nx || j >= sd.G.ny) return;
-    residual_point<OP, T>(sd.G, sd.u, sd.W, sd.rho, sd.dt_shift, sd.dt_scale, scheme, sd.b, sd.dt, flags, i, j, k);
+    if constexpr (std::is_same<T, double>::value)
+        residual_point<OP, T>(sd.G, sd.u, sd.W, sd.rho, sd.dt_shift, sd.dt_scale, scheme, sd.b, sd.dt, flags, i, j, k);
+    else
+        residual_pair_point<OP, T>(sd.G, sd.P, scheme, sd.b, sd.dt, flags, i, j, k);
 }
 
 // FP64, one tile (32 x 8 x 1) per block.

@@ -180,6 +180,7 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
     sink.last = record;
     sink.s = s;
     sink.m = m;
+    sink.ush = nullptr;
 
     // the scaled Taylor recurrence of exp(h (B - mu I)) on [y; a], sub-step by sub-step
     const double hs = tau / s;
@@ -210,7 +211,6 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
             a.last = (j + 1 == m);
             a.yacc = yacc;
             a.u = nullptr;
-            a.ush = nullptr;
             a.zout = a.last ? nullptr : Z[zi];
             if (a.last) {
                 a.gamma = gamma;

@@ -279,11 +279,8 @@ def test_two_term_batch_matches_single_grids(et_mod, torch_cuda, precision):
                                      variant=v)
         for i in range(len(PAIR_SHAPES)):
             want, rec = _single_run(et_mod, torch_cuda, Ds[i], us[i], PAIR_RHOS[i], nsteps, precision)
-            # the single grid's residual runs in pair arithmetic, the batch's in
-            # FP64: both round b to the form's value type, so they part only
-            # where the two roundings of b part (FP32: a few ulp after 3 steps)
-            tol = 2e-6 if precision == "f32" else 1e-13
-            assert _errs(got[i], want)[0] <= tol, (v, i, _errs(got[i], want))
+            # the same pair-arithmetic residual and per-voxel term arithmetic
+            assert np.array_equal(got[i], want), (v, i, np.abs(got[i] - want).max())
             if precision == "df64":
                 ref = oracle.Problem(Ds[i], rho=PAIR_RHOS[i]).run(us[i], TAU, nsteps)[0]
                 e_max, e_l2 = _errs(got[i], ref)

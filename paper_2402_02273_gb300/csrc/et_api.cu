@@ -38,7 +38,7 @@ struct Layout {
     size_t wpair[5];  // F32: the same scaled weights as pairs, read by the residual
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
-    size_t ushadow;   // F32, DF64: the pair nearest each u, read by the pair-arithmetic residual
+    size_t ushadow;   // F32, DF64: the pair of each u, read by the pair-arithmetic residual
     size_t partial;   // 3 * nblocks doubles
     size_t misc;      // counters, flags, info slots
     size_t total;
@@ -669,7 +669,7 @@ et_status record_step(et_grid* g, const Schedule& S, double hstep, const double*
         e = launch_residual<T>(g->G, g->op, un, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
                                g->flags, st);
     } else {
-        // the residual of the forward step, from the pair nearest u^n
+        // the residual of the forward step, from the pair of u^n
         e = launch_split(g->n, un, 1.0, g->ush, st);
         if (e == cudaSuccess) e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st);
     }

@@ -14,11 +14,35 @@
 namespace et {
 namespace df64 {
 
-// The pair nearest an FP64 value: hi = fl32(v), lo = fl32(v - hi) (the
-// subtraction is exact; |v - (hi + lo)| <= 2^-48 |v| barring underflow).
+// A pair for an FP64 value, built from its bits with integer instructions
+// only (GB300 runs FP64 conversions at its FP64 rate, 2 per clock per SM):
+// hi = v with the significand cut to 24 bits, lo = the 29 bits below them cut
+// to 24, so |v - (hi + lo)| < 2^-46 |v| for 2^-70 <= |v| < 2^128.  A part
+// below the FP32 normal range becomes a zero of v's sign (absolute error under
+// 2^-126); infinities, NaNs and values beyond the FP32 range give (+-inf or
+// NaN, 0).
 __device__ __forceinline__ float2 from_double(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const unsigned h = (unsigned)(bits >> 32), l = (unsigned)bits;
+    const unsigned sign = h & 0x80000000u;
+    const int e = (int)((h >> 20) & 0x7ffu);  // biased FP64 exponent
+    const int ef = e - 896;                   // the same exponent biased for FP32
+    const float zero = __uint_as_float(sign);
+    if (e == 0x7ff) {
+        const bool nan = ((h & 0xfffffu) | l) != 0u;
+        return make_float2(__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
+    }
+    if (ef <= 0) return make_float2(zero, zero);
+    if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const unsigned m23 = ((h & 0xfffffu) << 3) | (l >> 29);  // top 23 stored significand bits
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
+    const unsigned rem = l & 0x1fffffffu;  // the 29 bits below, of weight 2^(e - 1075) each
+    if (rem == 0u) return make_float2(hi, zero);
+    const int p = 31 - __clz((int)rem);  // leading bit of rem, 0..28
+    const int el = ef - 52 + p;          // biased FP32 exponent of lo
+    if (el <= 0) return make_float2(hi, zero);
+    const unsigned mm = p >= 23 ? rem >> (p - 23) : rem << (23 - p);
+    return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | (mm & 0x7fffffu)));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -48,7 +48,7 @@ struct Geom {
 
 // Device-side accumulation of per-step observables: block partials, a ticket
 // counter for the last-block reduction, the step index and the flag word.
-constexpr int kStatsBlocks = 2048;  // fixed, so the summation order is fixed
+constexpr int kStatsBlocks = 608;  // 4 per SM; fixed, so the summation order is fixed
 constexpr int kStatsThreads = 256;
 struct StatsSink {
     double* partial;        // 3 * kStatsBlocks: sum, min key, max key
@@ -59,7 +59,7 @@ struct StatsSink {
     int info_stride;        // records step t at info[t * info_stride] (0: always info[0])
     et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
     int s, m;               // recorded in the info
-    float2* ush;            // F32 / DF64: receives the pair nearest each u (nullptr: none)
+    float2* ush;            // F32 / DF64: receives the pair of each u (nullptr: none)
 };
 
 // Scalars of the kernels' value types: double (FP64), float (FP32) and
@@ -138,7 +138,7 @@ struct BatchTerm {
 };
 
 // Inputs of the pair-arithmetic residual of the F32 and DF64 forms: the pair
-// nearest each u, the 1/nu-scaled pair weights (w[4] = -rowsum / nu), nu,
+// of each u (df64::from_double), the 1/nu-scaled pair weights (w[4] = -rowsum / nu), nu,
 // rho, the diagonal shift / nu and the coefficient of u in the diagonal.
 struct PairResidualArgs {
     const float2* ush;
@@ -272,7 +272,7 @@ cudaError_t launch_sum(long long n, const double* v, double* partial, double* ou
 // out[p] = u[p] + y[p] in FP64 (y widened as the last term of a step adds it)
 template <typename T>
 cudaError_t launch_add_widen(long long n, const double* u, const T* y, double* out, cudaStream_t stream);
-// dst[p] = src[p] * scale as a pair (hi = nearest float, lo = the rest)
+// dst[p] = src[p] * scale as a pair (df64::from_double of the FP64 product)
 cudaError_t launch_split(long long n, const double* src, double scale, float2* dst, cudaStream_t stream);
 // The residual of the FP32 and DF64 forms in pair arithmetic from the pair
 // copy of u: b = nu (L~ u) + rho u (1 - u) and the diagonal w4~ + shift + k u,

@@ -338,7 +338,7 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
 // ---------------------------------------------------------------------------
 // stats: sum, min and max of u (min/max through integer order keys, one FP64
 // add per voxel), the non-finite flag, then the step record; the F32 and DF64
-// forms also take here the pair nearest each u, which their next residual reads.  A fixed grid of
+// forms also take here the pair of each u, which their next residual reads.  A fixed grid of
 // kStatsBlocks blocks fixes every summation order (bitwise reproducible).
 // Block `blk` (of kStatsBlocks) of the reduction over u[0..n).
 __device__ __forceinline__ void stats_body(long long n, const double* __restrict__ u, const StatsSink& s, int blk) {
@@ -351,6 +351,7 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
     double sum = 0.0;
     unsigned long long kmin = ~0ull, kmax = 0ull;
     bool bad = false;
+#pragma unroll 4
     for (long long p = blk * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
         const double v = u[p];
         if (s.ush) s.ush[p] = df64::from_double(v);

@@ -4,7 +4,7 @@
 //
 // The residual of the step (Eq. 2 and the scheme of Section 3) is
 // b = L u + rho u (1 - u) with the diagonal of the shifted Jacobian beside it.
-// Here it is computed from the pair nearest each u (ush) and the 1/nu-scaled
+// Here it is computed from the pair of each u (ush) and the 1/nu-scaled
 // pair weights W (W.w[4] = -rowsum / nu): S = (L / nu) u by the stencil code
 // of the Taylor terms, b = nu S + rho u (1 - u) and dt = W.w[4] + shift + k_u u
 // (k_u = -2 rho / nu for the folded reaction, else 0).  About 2^-44 relative,

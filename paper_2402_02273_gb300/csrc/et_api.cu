@@ -76,7 +76,30 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     return true;
 }
 
+// The scalars of the coefficient setup that a captured run bakes into its
+// kernel arguments (the weights themselves are read from device memory when
+// the graph runs, so a new D with the same scalars reuses the graph).
+struct CoeffKey {
+    double nu = 0.0, rmax = 0.0, rho = 0.0;
+    int op = -1, scheme = -1;
+    bool opt_set = false;
+    et_options opt{};
+};
+
+bool same_coeffs(const CoeffKey& a, const CoeffKey& b) {
+    // bit patterns, so that a NaN never matches and -0 differs from +0
+    auto eq = [](double x, double y) { return std::memcmp(&x, &y, sizeof(double)) == 0; };
+    if (!eq(a.nu, b.nu) || !eq(a.rmax, b.rmax) || !eq(a.rho, b.rho) || a.op != b.op || a.scheme != b.scheme ||
+        a.opt_set != b.opt_set)
+        return false;
+    if (!a.opt_set) return true;
+    const et_options &x = a.opt, &y = b.opt;
+    return eq(x.tol, y.tol) && eq(x.theta_max, y.theta_max) && x.shift == y.shift && x.force_s == y.force_s &&
+           x.force_m == y.force_m && x.use_graph == y.use_graph && x.single_terms == y.single_terms;
+}
+
 struct GraphEntry {
+    CoeffKey coeffs;
     double* u = nullptr;
     et_step_info* info = nullptr;
     double tau = 0.0;
@@ -195,6 +218,18 @@ struct DeviceGuard {
 };
 
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+CoeffKey coeff_key(const et_grid* g) {
+    CoeffKey k;
+    k.nu = g->nu;
+    k.rmax = g->rmax;
+    k.rho = g->rho;
+    k.op = (int)g->op;
+    k.scheme = (int)g->scheme;
+    k.opt_set = g->opt_set;
+    if (g->opt_set) k.opt = g->opt;
+    return k;
+}
 
 void clear_graphs(et_grid* g) {
     for (auto& e : g->graphs)
@@ -485,8 +520,10 @@ et_status run_impl(et_grid* g, double* u, double tau, int nsteps, et_step_info* 
     const ResolvedOptions ro = resolve(g->opt_set ? &g->opt : nullptr, g->prec);
     if (!ro.use_graph) return enqueue_run(g, u, tau, nsteps, info, g->stream, false);
 
+    const CoeffKey key = coeff_key(g);
     for (auto& e : g->graphs) {
-        if (e.u == u && e.info == info && e.tau == tau && e.nsteps == nsteps && e.timing == g->timing) {
+        if (e.u == u && e.info == info && e.tau == tau && e.nsteps == nsteps && e.timing == g->timing &&
+            same_coeffs(e.coeffs, key)) {
             e.stamp = ++g->stamp;
             ET_CUDA(g, cudaGraphLaunch(e.exec, g->stream));
             g->last_term_launches = e.term_launches;
@@ -517,6 +554,7 @@ et_status run_impl(et_grid* g, double* u, double tau, int nsteps, et_step_info* 
         g->graphs.erase(g->graphs.begin() + oldest);
     }
     GraphEntry ent;
+    ent.coeffs = key;
     ent.u = u;
     ent.info = info;
     ent.tau = tau;
@@ -544,7 +582,7 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
         if (opt->force_m == 1) return fail(g, ET_ERR_ARG, "options.force_m must be 0 or >= 2");
         if (opt->force_s < 0 || opt->force_m < 0) return fail(g, ET_ERR_ARG, "forced s, m must be >= 0");
     }
-    clear_graphs(g);
+    // cached graphs stay: a run reuses one only if its coefficient scalars match
     g->coeffs_set = false;
     ET_CUDA(g, cudaMemsetAsync(g->rmax_bits, 0, sizeof(unsigned long long), g->stream));
     ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));

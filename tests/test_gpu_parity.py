@@ -211,6 +211,42 @@ def test_run_graph_direct_and_host_paths_agree_bitwise(et_mod, torch_cuda):
     assert rec["step"] == 4
 
 
+@pytest.mark.parametrize("precision", ["f64", "df64", "f32"])
+def test_new_coefficients_after_a_captured_run(et_mod, torch_cuda, precision):
+    """et_set_coeffs keeps the grid's captured runs; a later run replays one
+    only if every coefficient scalar it holds is unchanged.  A new D with the
+    same bound rmax replays the graph (which reads the new weights), a new rho
+    or a D with another bound captures a new one: every result equals that of
+    a fresh grid with the same coefficients."""
+    torch = torch_cuda
+    D, u0 = phantom.case(40, seed=3, noise=0.1)
+    g = et_mod.Grid(D.shape, precision=precision)
+    g.set_coeffs(torch.from_numpy(D).cuda())
+    r0 = g.rmax()
+    # a D that differs at one tissue voxel but keeps the bound
+    D_same = None
+    for q in np.flatnonzero(D.ravel() > 0)[::97]:
+        cand = D.copy()
+        cand.reshape(-1)[q] *= 0.5
+        g.set_coeffs(torch.from_numpy(cand).cuda())
+        if g.rmax() == r0:
+            D_same = cand
+            break
+    assert D_same is not None
+    cases = [(D, 0.025), (D_same, 0.025), (D_same, 0.03), (D * 1.5, 0.03), (D, 0.025)]
+    for Dc, rho in cases:
+        g.set_coeffs(torch.from_numpy(Dc).cuda(), rho=rho)
+        u = torch.from_numpy(u0.copy()).cuda()
+        g.run(u, 7.3, 3)
+        g.sync_info()
+        fresh = et_mod.Grid(D.shape, precision=precision)
+        fresh.set_coeffs(torch.from_numpy(Dc).cuda(), rho=rho)
+        v = torch.from_numpy(u0.copy()).cuda()
+        fresh.run(v, 7.3, 3)
+        fresh.sync_info()
+        assert torch.equal(u, v), (rho, float((u - v).abs().max()))
+
+
 @pytest.fixture(scope="module")
 def oracle_128_three_steps():
     D, u0 = phantom.case(128, seed=0, noise=0.1)

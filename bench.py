@@ -51,7 +51,7 @@ def launch_mix(prec, s, m, pairs):
     """(launches, algorithmic bytes, flops) per voxel of one step's term chain.
 
     Sub-step 0 has m - 1 Horner terms, each later sub-step m terms.  With pairs
-    (F32 / DF64 default) two consecutive terms of a sub-step share one launch
+    (the DF64 default) two consecutive terms of a sub-step share one launch
     that reads z, the weights, the diagonal and b once and writes one z (and the
     sum), so a pair moves the bytes of one single term and does twice its flops."""
     def count(nterms):
@@ -65,9 +65,20 @@ def launch_mix(prec, s, m, pairs):
 
 
 # DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of the current kernels (cold cache; DF64 and FP32 launches
-# cover two terms); None where the kernel changed after the capture.
-TERM_TRAFFIC = {"f64": 107.0e6, "df64": 115.1e6, "f32": 50.7e6}
+# from one ncu capture of each current kernel (cold cache; a DF64 launch covers
+# two terms); None where the kernel changed after the capture.
+TERM_TRAFFIC = {"term_kernel_f64": 107.0e6, "term2_kernel": 115.1e6, "term_quad_kernel": 50.4e6}
+
+
+def term_kernel_of(prec, single_terms):
+    """The kernel that runs the Taylor terms of a single grid: FP64 one term per
+    launch; DF64 two per launch (one with --single-terms); FP32 one per launch
+    on the four-voxel kernel."""
+    if prec == "f64":
+        return "term_kernel_f64", False
+    if prec == "df64":
+        return ("term_kernel_df64", False) if single_terms else ("term2_kernel", True)
+    return "term_quad_kernel", False
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
@@ -249,6 +260,27 @@ def run_reference(args):
     return 0
 
 
+L2_BYTES = 129e6  # GB300 L2
+
+
+def l2_copy_gbs(torch, stream, nbytes=32 << 20, reps=200):
+    """Copy bandwidth of a buffer pair that stays in L2 (read + write bytes per
+    second, CUDA events): the denominator for kernels whose working set is
+    L2-resident, beside the HBM copy peak."""
+    a = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record(stream)
+    e1.synchronize()
+    return 2.0 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def measure_form(et, torch, D, u0, precision, args, stream, flush, timing=True):
     """Times K bench steps of one precision form; returns a dict of numbers."""
     n = D.size
@@ -307,6 +339,7 @@ def main():
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    l2_peak = l2_copy_gbs(torch, stream)
 
     def barrier():
         if world > 1:
@@ -342,14 +375,15 @@ def main():
         rec = g.sync_info()
         avg_launch_ms = term_ms / max(term_launches, 1)
         s_, m_ = info["s"], info["m"]
-        nl, vb, vf = launch_mix(prec, s_, m_, prec != "f64" and not args.single_terms)
+        kname, pairs = term_kernel_of(prec, args.single_terms)
+        nl, vb, vf = launch_mix(prec, s_, m_, pairs)
         bytes_per_launch = vb / nl * n
         flops_per_launch = vf / nl * n
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         value = whole_job_rate(world, n, args.nsteps, ms)
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
-        traffic = TERM_TRAFFIC.get(prec) if (args.grid == N_GRID and (prec == "f64" or not args.single_terms)) else None
+        traffic = TERM_TRAFFIC.get(kname) if args.grid == N_GRID else None
         alu_frac = achieved_tflops / alu_peak
         hbm_frac = achieved_gbs / hbm_peak
         if prec == "f64" and alu_frac >= hbm_frac:
@@ -359,9 +393,12 @@ def main():
         else:
             roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_frac, "traffic": traffic, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"}
-        kname = "term2_kernel (two terms per launch)" if (prec != "f64" and not args.single_terms) else \
-            ("term_kernel_df64" if prec == "df64" else "term_kernel")
-        roof.update({"kernel": kname, "avg_launch_us": avg_launch_ms * 1e3,
+        # the fields one term launch touches against the L2: where they fit, the
+        # chain runs largely from L2 (the HBM fraction can then exceed 1), and
+        # its bandwidth is also set against an L2-resident copy
+        if bytes_per_launch < L2_BYTES:
+            roof.update({"l2_resident": True, "l2_copy_gbs": l2_peak, "l2_frac": achieved_gbs / l2_peak})
+        roof.update({"kernel": kname + (" (two terms per launch)" if pairs else ""), "avg_launch_us": avg_launch_ms * 1e3,
                      "launches_per_run": term_launches, "algorithmic_bytes_per_launch": bytes_per_launch,
                      "algorithmic_flops_per_launch": flops_per_launch,
                      "hbm_frac": hbm_frac, "hbm_achieved_gbs": achieved_gbs, "alu_frac": alu_frac})

@@ -102,10 +102,12 @@ typedef struct {
     int force_m;      /* > 0: use this many Taylor terms per sub-step (>= 2) */
     int use_graph;    /* 1 (default): replay et_run / et_step as CUDA graphs;
                          -1: launch kernels directly */
-    int single_terms; /* 1: one Taylor term per launch; 0 (default): the F32 and
-                         DF64 forms evaluate two consecutive terms of a
-                         sub-step per launch (same arithmetic per voxel, about
-                         half the memory traffic); F64 always runs one */
+    int single_terms; /* Taylor terms per launch (same arithmetic per voxel in
+                         every case).  1: one.  -1: two consecutive terms of a
+                         sub-step wherever the two-term kernel can run (F32,
+                         DF64; about half the memory traffic).  0 (default):
+                         DF64 two, F32 one (its four-voxel one-term kernel is
+                         the faster), F64 always one */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */

@@ -144,9 +144,14 @@ def _check(rc: int, handle=None):
         raise EtError(rc, msg or lib.et_status_string(rc).decode())
 
 
-def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True, single_terms=False):
+def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True, single_terms=False,
+                 two_terms=False):
+    """et_options; single_terms / two_terms force one / two Taylor terms per
+    launch (default: the form's own choice)."""
+    if single_terms and two_terms:
+        raise ValueError("single_terms and two_terms exclude each other")
     return et_options(float(tol), float(theta_max), int(shift), int(force_s), int(force_m),
-                      1 if use_graph else -1, 1 if single_terms else 0)
+                      1 if use_graph else -1, 1 if single_terms else (-1 if two_terms else 0))
 
 
 def select_schedule(tau, rmax, rho, scheme="rosenbrock", precision="f64", **opts):

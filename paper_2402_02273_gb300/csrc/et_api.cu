@@ -117,7 +117,8 @@ struct Schedule {
 
 struct ResolvedOptions {
     double tol, theta_max;
-    int shift, force_s, force_m, use_graph, single_terms;
+    int shift, force_s, force_m, use_graph;
+    int single_terms;  // 1: one term per launch; -1: two where possible; 0: per form
 };
 
 ResolvedOptions resolve(const et_options* o, et_precision prec) {
@@ -134,7 +135,7 @@ ResolvedOptions resolve(const et_options* o, et_precision prec) {
     r.force_s = (o && o->force_s > 0) ? o->force_s : 0;
     r.force_m = (o && o->force_m > 0) ? o->force_m : 0;
     r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
-    r.single_terms = (o && o->single_terms > 0) ? 1 : 0;
+    r.single_terms = !o ? 0 : (o->single_terms > 0 ? 1 : (o->single_terms < 0 ? -1 : 0));
     return r;
 }
 
@@ -281,6 +282,17 @@ Buffers<T> typed_buffers(et_grid* g) {
 // with weights theta^j / j!, theta = h nu, so the vectors stay O(|b| / nu).
 // On sub-step 0, zeta_1 = b / nu is read as b with the stencil part scaled by
 // 1 / nu (zscale).
+// Two consecutive terms of a sub-step per launch (et_fused.cu)?  Only F32 and
+// DF64 grids whose rows the two-term kernel can address; by default DF64 only,
+// since F32 runs faster one term per launch on the four-voxel kernel
+// (et_quad.cu: 6.1 us per term at 128^3 against 10.4 for half a pair).
+bool use_pairs(const et_grid* g) {
+    if (g->prec == ET_F64 || !g->pair || !pair_preferred(g->op, g->prec)) return false;
+    const int t = resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
+    if (t != 0) return t < 0;
+    return g->prec == ET_DF64;
+}
+
 ChainPlan plan_chain(const et_grid* g, const Schedule& S, double hstep) {
     return et::plan_chain(g->prec, g->nu, S.s, S.m, S.mu, hstep);
 }
@@ -314,9 +326,8 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
     const ChainPlan P = plan_chain(g, S, hstep);
     const int s = S.s;
     if (!rec) {
-        // F32 / DF64: consecutive terms of a sub-step go in pairs (et_fused.cu)
-        const bool pairs = !std::is_same<T, double>::value && g->pair && pair_preferred(g->op, g->prec) &&
-                           !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
+        // consecutive terms of a sub-step in pairs where chosen (use_pairs)
+        const bool pairs = !std::is_same<T, double>::value && use_pairs(g);
         T* const Y[2] = {B.Y[0], B.Y[1]};
         T* const Z[2] = {B.Z[0], B.Z[1]};
         for (const ChainOp<T>& op : chain_ops<T>(P, s, B.b, B.dt, Y, Z, u, pairs)) {
@@ -332,10 +343,9 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
         }
         return cudaSuccess;
     }
-    // recorded chain (adjoint): every term to its own buffer; F32 / DF64 pair
-    // consecutive terms of a sub-step, the pair kernel storing both
-    const bool pairs = !std::is_same<T, double>::value && g->pair && pair_preferred(g->op, g->prec) &&
-                       !resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
+    // recorded chain (adjoint): every term to its own buffer; where pairs are
+    // chosen (use_pairs) the pair kernel stores both terms
+    const bool pairs = !std::is_same<T, double>::value && use_pairs(g);
     const T* zin = nullptr;
     auto rec_args = [&](const PlannedTerm& t) {
         const int k = t.k, j = t.j;

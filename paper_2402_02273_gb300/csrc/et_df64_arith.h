@@ -16,33 +16,36 @@ namespace df64 {
 
 // A pair for an FP64 value, built from its bits with integer instructions
 // only (GB300 runs FP64 conversions at its FP64 rate, 2 per clock per SM):
-// hi = v with the significand cut to 24 bits, lo = the 29 bits below them cut
-// to 24, so |v - (hi + lo)| < 2^-46 |v| for 2^-70 <= |v| < 2^128.  A part
-// below the FP32 normal range becomes a zero of v's sign (absolute error under
-// 2^-126); infinities, NaNs and values beyond the FP32 range give (+-inf or
-// NaN, 0).
+// hi = v rounded to 24 significant bits (half away from zero), lo = the signed
+// remainder v - hi (at most 28 bits) cut to 24, so |v - (hi + lo)| <= 2^-48 |v|
+// for 2^-70 <= |v| < 2^128.  A part below the FP32 normal range becomes a
+// zero (absolute error under 2^-126); infinities, NaNs and values beyond the
+// FP32 range give (+-inf or NaN, 0).
 __device__ __forceinline__ float2 from_double(double v) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    const unsigned h = (unsigned)(bits >> 32), l = (unsigned)bits;
-    const unsigned sign = h & 0x80000000u;
-    const int e = (int)((h >> 20) & 0x7ffu);  // biased FP64 exponent
-    const int ef = e - 896;                   // the same exponent biased for FP32
+    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+    const unsigned long long mag = bits & 0x7fffffffffffffffull;
+    const int e = (int)(mag >> 52);  // biased FP64 exponent
     const float zero = __uint_as_float(sign);
     if (e == 0x7ff) {
-        const bool nan = ((h & 0xfffffu) | l) != 0u;
+        const bool nan = (mag & 0xfffffffffffffull) != 0ull;
         return make_float2(__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
     }
-    if (ef <= 0) return make_float2(zero, zero);
+    if (e - 896 <= 0) return make_float2(zero, zero);
+    const unsigned long long rmag = mag + (1ull << 28);  // rounds at the 24th significant bit; may carry
+    const int ef = (int)(rmag >> 52) - 896;              // biased FP32 exponent of hi
     if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
-    const unsigned m23 = ((h & 0xfffffu) << 3) | (l >> 29);  // top 23 stored significand bits
-    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
-    const unsigned rem = l & 0x1fffffffu;  // the 29 bits below, of weight 2^(e - 1075) each
-    if (rem == 0u) return make_float2(hi, zero);
-    const int p = 31 - __clz((int)rem);  // leading bit of rem, 0..28
-    const int el = ef - 52 + p;          // biased FP32 exponent of lo
-    if (el <= 0) return make_float2(hi, zero);
-    const unsigned mm = p >= 23 ? rem >> (p - 23) : rem << (23 - p);
-    return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | (mm & 0x7fffffu)));
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((unsigned)(rmag >> 29) & 0x7fffffu));
+    const unsigned rem = (unsigned)mag & 0x1fffffffu;  // the 29 bits below hi's, of weight 2^(e - 1075)
+    const bool up = (rem >> 28) != 0u;                 // hi was rounded up: the remainder is negative
+    const unsigned r = up ? 0x20000000u - rem : rem;
+    const unsigned lsign = up ? sign ^ 0x80000000u : sign;
+    if (r == 0u) return make_float2(hi, zero);
+    const int p = 31 - __clz((int)r);  // leading bit of r, 0..28
+    const int el = e - 948 + p;        // biased FP32 exponent of lo
+    if (el <= 0) return make_float2(hi, __uint_as_float(lsign));
+    const unsigned mm = p >= 23 ? r >> (p - 23) : r << (23 - p);
+    return make_float2(hi, __uint_as_float(lsign | ((unsigned)el << 23) | (mm & 0x7fffffu)));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -201,6 +201,11 @@ template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
                             double rho, double dt_shift, double dt_scale, et_scheme scheme, T* b,
                             T* dt, unsigned* flags, cudaStream_t stream);
+// FP32 term with four voxels per thread (et_quad.cu), the same arithmetic as
+// the one-voxel kernel; needs nx % 4 == 0 and 16-byte aligned fields.
+bool quad_eligible(const Geom& G, const Weights<float>& W, const TermArgs<float>& a);
+cudaError_t launch_term_quad(const Geom& G, et_operator op, const Weights<float>& W, const TermArgs<float>& a,
+                             cudaStream_t stream);
 template <typename T>
 cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermArgs<T>& a,
                         cudaStream_t stream);

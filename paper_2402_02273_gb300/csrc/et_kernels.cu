@@ -638,6 +638,9 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermA
             term_kernel_f64<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(G, W, a);
         return cudaGetLastError();
     }
+    if constexpr (std::is_same<T, float>::value) {
+        if (quad_eligible(G, W, a)) return launch_term_quad(G, op, W, a, stream);
+    }
     constexpr int TZ = TermTile<T>::kZ;
     const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
                             ((G.nz + TZ - 1) / TZ);

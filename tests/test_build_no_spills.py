@@ -12,7 +12,7 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2402_02273_gb300", "csrc")
-HOT = ["et_kernels.cu", "et_df64.cu", "et_fused.cu"]
+HOT = ["et_kernels.cu", "et_df64.cu", "et_fused.cu", "et_quad.cu"]
 
 
 def _ptxas_report(src):

@@ -104,9 +104,10 @@ def test_fp32_adjoint_error_is_small(env):
 
 @pytest.mark.parametrize("sched", [{}, {"force_s": 2, "force_m": 5}, {"force_s": 3, "force_m": 4}])
 def test_fp32_recorded_pairs_equal_single_terms(env, sched):
-    """On TMA-eligible rows the FP32 adjoint records its forward chains with the
-    two-term kernel (storing both terms); the gradients equal those of the
-    one-term recording bitwise, and stay within the FP32 bound of the oracle's."""
+    """On TMA-eligible rows the FP32 adjoint can record its forward chains with
+    the two-term kernel (storing both terms); the gradients equal those of the
+    one-term recording (the four-voxel kernel, the default) bitwise, and stay
+    within the FP32 bound of the oracle's."""
     et, torch = env
     shape, tau, K = (18, 20, 24), 7.3, 4
     D, u0, tgt = _problem(shape, seed=4)
@@ -114,9 +115,9 @@ def test_fp32_recorded_pairs_equal_single_terms(env, sched):
     uK, _ = P.run(u0, tau, K)
     o_ub, o_rho, o_ds = oracle.vjp(P, u0, tau, K, uK - tgt)
     got = []
-    for single in (False, True):
+    for two in (True, False):
         g = et.Grid(shape, precision="f32")
-        g.set_coeffs(torch.from_numpy(D).cuda(), single_terms=single, **sched)
+        g.set_coeffs(torch.from_numpy(D).cuda(), two_terms=two, **sched)
         got.append(g.vjp(torch.from_numpy(u0.copy()).cuda(), tau, K,
                          torch.from_numpy((uK - tgt).copy()).cuda(), checkpoint_every=2))
     assert torch.equal(got[0][0], got[1][0]) and got[0][1] == got[1][1] and got[0][2] == got[1][2]

@@ -123,7 +123,7 @@ def _run_states(et, torch, D, u0, tau, nsteps, precision, **kw):
 @pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "rosenbrock"),
                                        ("conservative", "expeuler")])
 @pytest.mark.parametrize("shape", [(5, 17, 33), (9, 8, 40), (1, 1, 45), (3, 70, 2), (40, 12, 36), (7, 19, 68),
-                                   (33, 9, 64), (2, 3, 8)])
+                                   (33, 9, 64), (2, 3, 8), (6, 5, 4), (4, 9, 132)])
 @pytest.mark.parametrize("sched", [{}, {"force_s": 3, "force_m": 5}, {"force_s": 2, "force_m": 4},
                                    {"force_s": 1, "force_m": 2}])
 def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op, scheme, shape, sched):
@@ -132,12 +132,15 @@ def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op
     Rows of a 16-byte multiple take the pair kernel (fewer launches), others run
     one term per launch.  The schedules cover odd and even term counts per
     sub-step, a lone trailing term, s = 1 (the pair finishes the step) and m = 2
-    (no pair); the shapes cover ragged y and z, several x tiles and z segments."""
+    (no pair); the shapes cover ragged y and z, several x tiles and z segments.
+    FP32 single terms on rows of a multiple of 4 voxels run the four-voxel
+    kernel (rows of one quad, rows longer than a warp's 32 quads, rows split
+    between blocks), so this also checks it against the two-term kernel."""
     D = (0.01 + 0.2 * phantom.uniform(5, 7, int(np.prod(shape)))).reshape(shape)
     D = D.astype(np.float32).astype(np.float64)
     u0 = 0.9 * phantom.uniform(5, 8, D.size).reshape(shape)
     kw = dict(op=op, scheme=scheme, **sched)
-    fused, rf = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, **kw)
+    fused, rf = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, two_terms=True, **kw)
     single, rs = _run_states(et_mod, torch_cuda, D, u0, 7.3, 3, precision, single_terms=True, **kw)
     assert (rf["s"], rf["m"]) == (rs["s"], rs["m"])
     # pairs run where TMA can address the rows, except the literal DF64 stage,

@@ -67,18 +67,23 @@ def launch_mix(prec, s, m, pairs):
 # DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of each current kernel (cold cache; a DF64 launch covers
 # two terms); None where the kernel changed after the capture.
-TERM_TRAFFIC = {"term_kernel_f64": 107.0e6, "term2_kernel": 115.1e6, "term_quad_kernel": 50.4e6}
+TERM_TRAFFIC = {("f64", "term_kernel_f64"): 107.0e6, ("df64", "term2_kernel"): 115.1e6,
+                ("f32", "term_quad_kernel"): 50.4e6, ("f32", "term2_kernel"): 50.7e6}
 
 
-def term_kernel_of(prec, single_terms):
-    """The kernel that runs the Taylor terms of a single grid: FP64 one term per
-    launch; DF64 two per launch (one with --single-terms); FP32 one per launch
-    on the four-voxel kernel."""
+def term_kernel_of(prec, single_terms, n):
+    """The kernel that runs the Taylor terms of a single grid (the library's
+    default choice): FP64 one term per launch; DF64 two per launch; FP32 one
+    per launch on the four-voxel kernel while its chain's fields (32 B per
+    voxel) stay within 1.4 L2 sizes, else two per launch.  --single-terms: one
+    everywhere."""
     if prec == "f64":
         return "term_kernel_f64", False
     if prec == "df64":
         return ("term_kernel_df64", False) if single_terms else ("term2_kernel", True)
-    return "term_quad_kernel", False
+    if single_terms or 32.0 * n <= 1.4 * L2_BYTES:
+        return "term_quad_kernel", False
+    return "term2_kernel", True
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
@@ -375,7 +380,7 @@ def main():
         rec = g.sync_info()
         avg_launch_ms = term_ms / max(term_launches, 1)
         s_, m_ = info["s"], info["m"]
-        kname, pairs = term_kernel_of(prec, args.single_terms)
+        kname, pairs = term_kernel_of(prec, args.single_terms, n)
         nl, vb, vf = launch_mix(prec, s_, m_, pairs)
         bytes_per_launch = vb / nl * n
         flops_per_launch = vf / nl * n
@@ -383,7 +388,7 @@ def main():
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         value = whole_job_rate(world, n, args.nsteps, ms)
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
-        traffic = TERM_TRAFFIC.get(kname) if args.grid == N_GRID else None
+        traffic = TERM_TRAFFIC.get((prec, kname)) if args.grid == N_GRID else None
         alu_frac = achieved_tflops / alu_peak
         hbm_frac = achieved_gbs / hbm_peak
         if prec == "f64" and alu_frac >= hbm_frac:

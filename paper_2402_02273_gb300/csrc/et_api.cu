@@ -283,14 +283,18 @@ Buffers<T> typed_buffers(et_grid* g) {
 // On sub-step 0, zeta_1 = b / nu is read as b with the stencil part scaled by
 // 1 / nu (zscale).
 // Two consecutive terms of a sub-step per launch (et_fused.cu)?  Only F32 and
-// DF64 grids whose rows the two-term kernel can address; by default DF64 only,
-// since F32 runs faster one term per launch on the four-voxel kernel
-// (et_quad.cu: 6.1 us per term at 128^3 against 10.4 for half a pair).
+// DF64 grids whose rows the two-term kernel can address.  By default DF64
+// always; F32 only when the fields of its chain (about 32 B per voxel) exceed
+// about 1.4 times the 129 MB L2: while they (largely) fit, the four-voxel
+// one-term kernel is the faster, beyond, the pair's halved HBM traffic wins.
+// Measured, us per term (one-term / half a pair): 128^3 6.1 / 10.4, 160^3
+// 16.5 / 19.5, 192^3 35.5 / 31.1.
 bool use_pairs(const et_grid* g) {
     if (g->prec == ET_F64 || !g->pair || !pair_preferred(g->op, g->prec)) return false;
     const int t = resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
     if (t != 0) return t < 0;
-    return g->prec == ET_DF64;
+    constexpr double kL2Bytes = 129.0e6;
+    return g->prec == ET_DF64 || 32.0 * (double)g->n > 1.4 * kL2Bytes;
 }
 
 ChainPlan plan_chain(const et_grid* g, const Schedule& S, double hstep) {

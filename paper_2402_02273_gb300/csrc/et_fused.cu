@@ -56,8 +56,6 @@ constexpr int kPairThreads = 352;       // 11 warps: one per voxel of the 34 x 1
 constexpr int kHaloX = kBlockX + 2;     // 34
 constexpr int kHaloY = kBlockY + 2;     // 10
 constexpr int kHalo = kHaloX * kHaloY;  // 340
-constexpr int kPrefetch = 1;            // stages loaded ahead of the one consumed
-constexpr int kStages = kPrefetch + 4;  // + planes L - 3 (second term), L - 1, L (first term), L - 2
 constexpr int kRing = 4;                // z_a planes kept: the second term's three and the one being written
 constexpr int kWaitTries = 1 << 24;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
@@ -80,8 +78,13 @@ struct Shape {
     __host__ __device__ static constexpr unsigned tx_bytes(bool literal) {
         return box(12) + box(11) + 4 * box(10) + (literal ? box(10) : 0);
     }
+    // stages loaded ahead of the one consumed: two where three blocks per SM
+    // still fit (FP32, conservative: 68 KB a block), else one
+    __host__ __device__ static constexpr int prefetch(bool literal) { return (ES == 4 && !literal) ? 2 : 1; }
+    // + planes L - 3 (second term), L - 1, L (first term), L - 2
+    __host__ __device__ static constexpr int stages(bool literal) { return prefetch(literal) + 4; }
     __host__ __device__ static constexpr int smem_bytes(bool literal) {
-        return 128 + kStages * stage_bytes(literal) + kRing * kHalo * ES + kStages * 8;
+        return 128 + stages(literal) * stage_bytes(literal) + kRing * kHalo * ES + stages(literal) * 8;
     }
 };
 
@@ -269,6 +272,8 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
     constexpr int BX = S::BX, XO = S::XO;
     constexpr int kStageBytes = S::stage_bytes(kLit);
     constexpr unsigned kTx = S::tx_bytes(kLit);
+    constexpr int kPrefetch = S::prefetch(kLit);
+    constexpr int kStages = S::stages(kLit);
     extern __shared__ unsigned char smem_raw[];
     unsigned char* const base = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
     T* const za = reinterpret_cast<T*>(base + kStages * kStageBytes);  // [kRing][kHalo], slot = plane & 3

@@ -250,6 +250,27 @@ def test_new_coefficients_after_a_captured_run(et_mod, torch_cuda, precision):
         assert torch.equal(u, v), (rho, float((u - v).abs().max()))
 
 
+@pytest.mark.parametrize("precision", ["f32", "df64"])
+def test_state_without_16_byte_alignment(et_mod, torch_cuda, precision):
+    """A state u that is 8- but not 16-byte aligned (a view one element into a
+    buffer) cannot take the vector kernels' 16-byte accesses: its steps run the
+    one-voxel kernels, with identical results."""
+    torch = torch_cuda
+    D, u0 = phantom.case(24, seed=5, noise=0.1)
+    outs = []
+    for offset in (0, 1):
+        g = et_mod.Grid(D.shape, precision=precision)
+        g.set_coeffs(torch.from_numpy(D).cuda())
+        buf = torch.zeros(u0.size + 2, dtype=torch.float64, device="cuda")
+        u = buf[offset:offset + u0.size]
+        assert (u.data_ptr() % 16 == 0) == (offset == 0)
+        u.copy_(torch.from_numpy(u0.ravel()))
+        g.run(u, 7.3, 3)
+        g.sync_info()
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.fixture(scope="module")
 def oracle_128_three_steps():
     D, u0 = phantom.case(128, seed=0, noise=0.1)

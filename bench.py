@@ -68,7 +68,7 @@ def launch_mix(prec, s, m, pairs):
 # from one ncu capture of each current kernel (cold cache; a DF64 launch covers
 # two terms); None where the kernel changed after the capture.
 TERM_TRAFFIC = {("f64", "term_kernel_f64"): 107.0e6, ("df64", "term2_kernel"): 115.1e6,
-                ("f32", "term_quad_kernel"): None, ("f32", "term2_kernel"): None}
+                ("f32", "term_quad_kernel"): 50.4e6, ("f32", "term2_kernel"): None}
 
 
 def term_kernel_of(prec, single_terms, n):

@@ -208,6 +208,7 @@ template <int OP, typename TO>
 __global__ void __launch_bounds__(kThreads)
 residual_df64_kernel(const __grid_constant__ Geom G, const __grid_constant__ PairResidualArgs R, int scheme,
                      TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags) {
+    pdl_begin();  // launched by launch_pdl
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
@@ -222,10 +223,10 @@ cudaError_t launch_residual_df64(const Geom& G, et_operator op, const PairResidu
     const dim3 block(kBlockX, kBlockY, 1);
     const dim3 grid((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
     if (op == ET_OP_CONSERVATIVE)
-        residual_df64_kernel<ET_OP_CONSERVATIVE, TO><<<grid, block, 0, stream>>>(G, R, (int)scheme, b, dt, flags);
-    else
-        residual_df64_kernel<ET_OP_LITERAL, TO><<<grid, block, 0, stream>>>(G, R, (int)scheme, b, dt, flags);
-    return cudaGetLastError();
+        return launch_pdl(residual_df64_kernel<ET_OP_CONSERVATIVE, TO>, grid, block, stream, G, R, (int)scheme, b,
+                          dt, flags);
+    return launch_pdl(residual_df64_kernel<ET_OP_LITERAL, TO>, grid, block, stream, G, R, (int)scheme, b, dt,
+                      flags);
 }
 
 template cudaError_t launch_residual_df64<float2>(const Geom&, et_operator, const PairResidualArgs&, et_scheme,

@@ -7,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 
 #include "et.h"
 
@@ -18,6 +19,32 @@ constexpr double kRangeSlack = 1e-3;
 
 // Thread-block shape of the stencil kernels: 32 voxels along x (one warp per
 // row, coalesced) by 8 rows along y; one z-plane per block.
+// Programmatic dependent launch.  A kernel launched by launch_pdl calls
+// pdl_begin() before its first memory access: it lets the next grid in the
+// stream be scheduled as soon as all of its own blocks run, and waits until
+// the previous grid has finished and its stores are visible (after a plain
+// launch the wait returns at once).  Short kernels then overlap their launch
+// and block set-up with the previous kernel's tail.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 constexpr int kBlockX = 32;
 constexpr int kBlockY = 8;
 constexpr int kThreads = kBlockX * kBlockY;

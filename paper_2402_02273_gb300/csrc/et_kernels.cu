@@ -440,6 +440,7 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
 
 __global__ void __launch_bounds__(kStatsThreads) stats_kernel(long long n, const double* __restrict__ u,
                                                               StatsSink s) {
+    pdl_begin();  // launched by launch_pdl
     stats_body(n, u, s, blockIdx.x);
 }
 
@@ -741,8 +742,7 @@ template cudaError_t launch_batch_residual<float2>(et_operator, int, const Batch
                                                    unsigned*, cudaStream_t);
 
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream) {
-    stats_kernel<<<kStatsBlocks, kStatsThreads, 0, stream>>>(G.n, u, sink);
-    return cudaGetLastError();
+    return launch_pdl(stats_kernel, dim3(kStatsBlocks), dim3(kStatsThreads), stream, G.n, u, sink);
 }
 
 template cudaError_t launch_residual<double>(const Geom&, et_operator, const double*, Weights<double>,

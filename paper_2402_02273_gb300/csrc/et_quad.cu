@@ -72,12 +72,7 @@ term_quad_kernel(const __grid_constant__ Geom G, const __grid_constant__ Weights
     const bool need_b = a.has_beta || (!a.horner && a.base_mode == 1);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // Programmatic dependent launch: the next term's blocks may be scheduled
-    // as soon as all of this grid's blocks run; each waits here until the
-    // previous grid has finished and its stores are visible (without the
-    // launch attribute the wait returns at once)
-    asm volatile("griddepcontrol.launch_dependents;");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_begin();  // launched as a programmatic dependent launch (launch_pdl)
 
     int p = i + sy * j + sz * k0;
     float4 zc = ld4(z + p);
@@ -212,18 +207,10 @@ cudaError_t launch_term_quad(const Geom& G, et_operator op, const Weights<float>
                              cudaStream_t stream) {
     const int tz = quad_planes(G);
     const long long nq = (long long)(G.nx / 4) * G.ny;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((nq + kQuadThreads - 1) / kQuadThreads), (unsigned)((G.nz + tz - 1) / tz), 1);
-    cfg.blockDim = dim3(kQuadThreads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (op == ET_OP_CONSERVATIVE) return cudaLaunchKernelEx(&cfg, term_quad_kernel<ET_OP_CONSERVATIVE>, G, W, a, tz);
-    return cudaLaunchKernelEx(&cfg, term_quad_kernel<ET_OP_LITERAL>, G, W, a, tz);
+    const dim3 grid((unsigned)((nq + kQuadThreads - 1) / kQuadThreads), (unsigned)((G.nz + tz - 1) / tz), 1);
+    const dim3 block(kQuadThreads, 1, 1);
+    if (op == ET_OP_CONSERVATIVE) return launch_pdl(term_quad_kernel<ET_OP_CONSERVATIVE>, grid, block, stream, G, W, a, tz);
+    return launch_pdl(term_quad_kernel<ET_OP_LITERAL>, grid, block, stream, G, W, a, tz);
 }
 
 }  // namespace et

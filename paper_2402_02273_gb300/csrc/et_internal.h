@@ -222,8 +222,9 @@ cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], floa
                                    double scale, cudaStream_t stream);
 cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float2* const wd[4],
                                    double scale, cudaStream_t stream);
-// dt_shift: rho - mu (folded scheme) or -mu (exponential Euler); the diagonal
-// is stored times dt_scale (1 / nu for the FP32 and DF64 forms).
+// The FP64 residual of the F64 form (instantiated for double): dt_shift is
+// rho - mu (folded scheme) or -mu (exponential Euler); the diagonal is stored
+// times dt_scale.
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
                             double rho, double dt_shift, double dt_scale, et_scheme scheme, T* b,

@@ -748,12 +748,6 @@ cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, 
 template cudaError_t launch_residual<double>(const Geom&, et_operator, const double*, Weights<double>,
                                              double, double, double, et_scheme, double*, double*, unsigned*,
                                              cudaStream_t);
-template cudaError_t launch_residual<float>(const Geom&, et_operator, const double*, Weights<double>,
-                                            double, double, double, et_scheme, float*, float*, unsigned*,
-                                            cudaStream_t);
-template cudaError_t launch_residual<float2>(const Geom&, et_operator, const double*, Weights<double>,
-                                             double, double, double, et_scheme, float2*, float2*, unsigned*,
-                                             cudaStream_t);
 template cudaError_t launch_term<double>(const Geom&, et_operator, Weights<double>,
                                          const TermArgs<double>&, cudaStream_t);
 template cudaError_t launch_term<float>(const Geom&, et_operator, Weights<float>, const TermArgs<float>&,

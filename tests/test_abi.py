@@ -150,3 +150,36 @@ def test_selected_schedule_meets_tolerance_on_dense_model(shift, op):
     got = _shifted_recurrence(A, b, tau, s, m, mu)
     want, _, _ = P.phi1_action(u0, b.reshape(D.shape), tau)
     assert np.abs(got - want.ravel()).max() <= 1e-13 * max(1.0, np.abs(u0).max())
+
+
+def test_terms_per_launch_option():
+    """single_terms / two_terms map to the et_options field (1 / -1, 0 = the
+    form's own choice) and exclude each other."""
+    assert et.make_options().single_terms == 0
+    assert et.make_options(single_terms=True).single_terms == 1
+    assert et.make_options(two_terms=True).single_terms == -1
+    with pytest.raises(ValueError):
+        et.make_options(single_terms=True, two_terms=True)
+
+
+def test_bench_launch_mix_and_kernel_choice():
+    """The bench's bookkeeping: launches and algorithmic bytes of a chain with
+    and without pairs, and the kernel each form runs at a grid size."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    # s = 1, m = 31: 30 Horner terms, one launch each or fifteen pairs
+    nl, nb, nf = bench.launch_mix("f32", 1, 31, False)
+    assert nl == 30 and nb == 30 * bench.HORNER_BYTES["f32"] and nf == 30 * bench.HORNER_FLOPS["f32"]
+    nl, nb, nf = bench.launch_mix("f32", 1, 31, True)
+    assert nl == 15 and nb == 15 * bench.HORNER_BYTES["f32"] and nf == 30 * bench.HORNER_FLOPS["f32"]
+    # s = 2, m = 5: 4 Horner terms then 5 running-sum terms (2 pairs + 1 single)
+    nl, nb, _ = bench.launch_mix("df64", 2, 5, True)
+    assert nl == 2 + 3 and nb == 2 * bench.HORNER_BYTES["df64"] + 3 * bench.TERM_BYTES["df64"]
+    assert bench.term_kernel_of("f64", False, 128 ** 3) == ("term_kernel_f64", False)
+    assert bench.term_kernel_of("df64", False, 128 ** 3) == ("term2_kernel", True)
+    assert bench.term_kernel_of("df64", True, 128 ** 3) == ("term_kernel_df64", False)
+    assert bench.term_kernel_of("f32", False, 160 ** 3) == ("term_quad_kernel", False)
+    assert bench.term_kernel_of("f32", False, 192 ** 3) == ("term2_kernel", True)
+    assert bench.term_kernel_of("f32", True, 192 ** 3) == ("term_quad_kernel", False)

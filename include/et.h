@@ -55,7 +55,7 @@ typedef enum {
     ET_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has details */
     ET_ERR_NUMERIC = 4,     /* D < 0 or not finite; u out of range or non-finite */
     ET_ERR_TIMEOUT = 5,     /* reserved for bounded device waits */
-    ET_ERR_UNSUPPORTED = 6  /* combination not provided by this build */
+    ET_ERR_UNSUPPORTED = 6  /* combination the library does not provide */
 } et_status;
 
 /* Arithmetic of the Taylor-term kernels.  The state u is always FP64, and the

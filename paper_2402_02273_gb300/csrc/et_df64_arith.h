@@ -11,8 +11,38 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 namespace et {
 namespace df64 {
+
+// Bit casts and the leading-bit count, on the device by intrinsics and on the
+// host (where tests check from_double) by memcpy and the compiler builtin.
+__host__ __device__ __forceinline__ unsigned long long bits_of(double v) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &v, sizeof(b));
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ int leading_bit(unsigned r) {  // r != 0
+#ifdef __CUDA_ARCH__
+    return 31 - __clz((int)r);
+#else
+    return 31 - __builtin_clz(r);
+#endif
+}
 
 // A pair for an FP64 value, built from its bits with integer instructions
 // only (GB300 runs FP64 conversions at its FP64 rate, 2 per clock per SM):
@@ -21,31 +51,31 @@ namespace df64 {
 // for 2^-70 <= |v| < 2^128.  A part below the FP32 normal range becomes a
 // zero (absolute error under 2^-126); infinities, NaNs and values beyond the
 // FP32 range give (+-inf or NaN, 0).
-__device__ __forceinline__ float2 from_double(double v) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+__host__ __device__ __forceinline__ float2 from_double(double v) {
+    const unsigned long long bits = bits_of(v);
     const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
     const unsigned long long mag = bits & 0x7fffffffffffffffull;
     const int e = (int)(mag >> 52);  // biased FP64 exponent
-    const float zero = __uint_as_float(sign);
+    const float zero = float_of(sign);
     if (e == 0x7ff) {
         const bool nan = (mag & 0xfffffffffffffull) != 0ull;
-        return make_float2(__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
+        return make_float2(float_of(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
     }
     if (e - 896 <= 0) return make_float2(zero, zero);
     const unsigned long long rmag = mag + (1ull << 28);  // rounds at the 24th significant bit; may carry
     const int ef = (int)(rmag >> 52) - 896;              // biased FP32 exponent of hi
-    if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
-    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((unsigned)(rmag >> 29) & 0x7fffffu));
+    if (ef >= 255) return make_float2(float_of(sign | 0x7f800000u), 0.f);
+    const float hi = float_of(sign | ((unsigned)ef << 23) | ((unsigned)(rmag >> 29) & 0x7fffffu));
     const unsigned rem = (unsigned)mag & 0x1fffffffu;  // the 29 bits below hi's, of weight 2^(e - 1075)
     const bool up = (rem >> 28) != 0u;                 // hi was rounded up: the remainder is negative
     const unsigned r = up ? 0x20000000u - rem : rem;
     const unsigned lsign = up ? sign ^ 0x80000000u : sign;
     if (r == 0u) return make_float2(hi, zero);
-    const int p = 31 - __clz((int)r);  // leading bit of r, 0..28
-    const int el = e - 948 + p;        // biased FP32 exponent of lo
-    if (el <= 0) return make_float2(hi, __uint_as_float(lsign));
+    const int p = leading_bit(r);  // leading bit of r, 0..28
+    const int el = e - 948 + p;    // biased FP32 exponent of lo
+    if (el <= 0) return make_float2(hi, float_of(lsign));
     const unsigned mm = p >= 23 ? r >> (p - 23) : r << (23 - p);
-    return make_float2(hi, __uint_as_float(lsign | ((unsigned)el << 23) | (mm & 0x7fffffu)));
+    return make_float2(hi, float_of(lsign | ((unsigned)el << 23) | (mm & 0x7fffffu)));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -164,7 +164,10 @@ ET_API et_status et_step(et_grid* g, double* u, double tau, et_step_info* info);
 
 /* nsteps >= 1 steps of size tau, in place.  info: device array of nsteps
  * records, or NULL.  Asynchronous; replayed as one CUDA graph per
- * (u, info, tau, nsteps) after the first call. */
+ * (u, info, tau, nsteps) after the first call (up to 8 kept per grid).  A
+ * later et_set_coeffs keeps the graphs; a run replays one only if the new
+ * coefficients give the same scalars (bound, rho, operator, scheme, options),
+ * since the weights themselves are read from the workspace when it runs. */
 ET_API et_status et_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info);
 
 /* et_run on host buffers: copies u_host to the device, runs, copies u back

@@ -3,7 +3,6 @@
 Tolerance (FP64 kernels): max |u_gpu - u_oracle| <= 1e-10 * max|u_oracle| and the
 same for the L2 norm, after every step.  FP32 kernels: errors are reported and
 bounded by 1e-5 relative (their own arithmetic limit, not a parity claim)."""
-import os
 
 import numpy as np
 import pytest
@@ -329,8 +328,6 @@ def oracle_128_hundred_steps():
     return D, u0, states, ost
 
 
-@pytest.mark.skipif(os.environ.get("ET_FULL_ORACLE") != "1",
-                    reason="100-step 128^3 oracle run takes minutes; set ET_FULL_ORACLE=1")
 @pytest.mark.parametrize("precision", ["f64", "df64", "f32"])
 def test_full_size_128cubed_100_steps_match_oracle(et_mod, torch_cuda, oracle_128_hundred_steps, precision):
     """The whole bench run, every step against the oracle: FP64 forms to 1e-10; the

@@ -36,8 +36,9 @@ def test_adjoint_gradients_match_central_differences(op, scheme):
 
 
 def test_adjoint_of_pure_diffusion_is_transpose_of_the_step():
-    """rho = 0, conservative: the step is exp(tau L) u (symmetric), so the adjoint
-    of a unit cotangent e_q is the q-th column of the step's matrix."""
+    """rho = 0: the step is the linear map u -> exp(tau L) u, so the adjoint of a
+    unit cotangent e_q is row q of that map's matrix.  The literal operator is
+    not symmetric, so row and column differ and a transposition mistake fails."""
     D, _ = phantom.case((4, 4, 5), seed=1, noise=0.1)
     D[D == 0] = 0.08
     P = oracle.Problem(D, rho=0.0, op="literal", scheme="rosenbrock")

@@ -132,6 +132,36 @@ def test_density_stays_in_unit_interval(op):
     assert min(x["umin"] for x in st) >= -1e-14
 
 
+@pytest.mark.parametrize("shape", [(6, 5, 7), (1, 1, 9), (4, 3, 1)])
+def test_step_records_are_min_max_and_sum_of_the_returned_state(shape):
+    """The per-step record (tumour mass, Sec. 3.5, and the extremes of u) is a
+    plain reduction of the state the step returns: umin and umax equal numpy's
+    min and max exactly, the mass its sum up to summation order.  The fields sit
+    strictly inside (0, 1), and their extremes lie in planes other than the
+    first, so neither a 0 / 1 start value nor a reduction over one plane nor a
+    swapped comparison can pass."""
+    n = shape[0] * shape[1] * shape[2]
+    u0 = (0.2 + 0.6 * phantom.uniform(11, 3, n)).reshape(shape)
+    D = 0.05 * phantom.uniform(11, 4, n).reshape(shape)
+    for scheme in ("rosenbrock", "expeuler"):
+        P = oracle.Problem(D, rho=0.025, op="conservative", scheme=scheme)
+        states, st = P.run(u0, 7.3, 3, every=True)
+        for t in range(3):
+            u = states[t + 1]
+            assert st[t]["umin"] == u.min() and st[t]["umax"] == u.max()
+            assert st[t]["umin"] > 0.1 and st[t]["umax"] < 0.95
+            assert abs(st[t]["mass"] - u.sum()) <= 1e-14 * u.sum()
+    # extremes planted in the last and a middle plane of a pure-reaction step
+    # (D = 0): the step is monotone per voxel, so they stay where they were put
+    u1 = np.full(shape, 0.5)
+    u1.reshape(-1)[n - 1] = 0.3
+    u1.reshape(-1)[n // 2] = 0.7
+    P = oracle.Problem(np.zeros(shape), rho=0.025)
+    u, st = P.run(u1, 7.3, 1)
+    assert np.argmin(u) == n - 1 and np.argmax(u) == n // 2
+    assert st[0]["umin"] == u.min() and st[0]["umax"] == u.max()
+
+
 def _order(errs):
     return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
 

@@ -287,13 +287,14 @@ ET_API void et_batch_destroy(et_batch* b);
  * all scratch in one static device array of the library (22 MiB, held by
  * every GPU that loads it until exit) instead of a workspace.
  *  nx, ny, nz, h, rho, op, scheme, tau: as for et_create_grid / et_set_coeffs
- *      / et_step; at most 64^3 = 262144 voxels and 65536 blocks of the 32 x 8
- *      tile, else ET_ERR_ARG.
+ *      / et_step; at most 64^3 = 262144 voxels, nz <= 65535 and 65536 blocks
+ *      of the 32 x 8 tile, else ET_ERR_ARG.
  *  D    device, n FP64 values (read); u device, n FP64 values (in/out).
  *  cuda_stream  stream to run on; msg/msg_len optional buffer for an error
  *      message (may be NULL).
- * The first call on a device looks up the array's address (cudaGetSymbolAddress)
- * with that device current; make it before any stream capture.  Calls share the
+ * The first call in each CUDA context of a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current and caches it by the
+ * context's id; make that first call before any stream capture.  Calls share the
  * array: calls that overlap on the GPU race.  Synchronises the stream and
  * returns ET_ERR_NUMERIC for bad D or a non-finite / out-of-range density. */
 ET_API et_status et_step_static(int nx, int ny, int nz, double h, const double* D, double rho,

@@ -12,11 +12,14 @@
 // Limits and behaviour:
 //  - at most kStaticMaxVoxels = 64^3 = 262144 voxels and at most 65536 thread
 //    blocks of the 32 x 8 stencil tile; larger grids are rejected with
-//    ET_ERR_ARG.  The array is 11 FP64 fields of 64^3 voxels plus 48 KiB of
-//    partials: 22 MiB held on every GPU that loads it until exit.
-//  - the first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress while that device is current, and caches it; make
-//    that first call before any stream capture.
+//    ET_ERR_ARG, and so are grids with nz > 65535 (the z extent of a launch).
+//    The array is 11 FP64 fields of 64^3 voxels plus 3 x 8 x kStatsBlocks
+//    bytes of reduction partials (about 14 KiB) and 256 bytes of counters:
+//    22 MiB held on every GPU that loads it until exit.
+//  - the first call in a CUDA context of a device (the primary context, or a
+//    new one after cudaDeviceReset) looks up the array's device address with
+//    cudaGetSymbolAddress while that device is current, and caches it keyed by
+//    the context's unique id; make that first call before any stream capture.
 //  - every call shares the array: two calls whose work overlaps on the GPU
 //    (different streams, or different host threads) race and corrupt each
 //    other.  Counters are cleared at the start of each call; every other
@@ -53,6 +56,33 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // id of the context the address belongs to
+
+// Unique id of the current CUDA context (0 if the driver cannot say).  Ids are
+// never reused, unlike context handles, so an address cached for a context
+// that was destroyed (cudaDeviceReset) is never taken for its successor.
+unsigned long long current_context_id() {
+    typedef int (*ctx_current_fn)(void**);
+    typedef int (*ctx_id_fn)(void*, unsigned long long*);
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<ctx_current_fn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<ctx_id_fn>(p);
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 et_status report(char* msg, size_t msg_len, et_status st, const char* fmt, ...) {
     if (msg && msg_len) {
@@ -64,14 +94,18 @@ et_status report(char* msg, size_t msg_len, et_status st, const char* fmt, ...) 
     return st;
 }
 
-// Device address of the static array on the current device (looked up once).
+// Device address of the static array in the current context of device `dev`:
+// looked up once per context and cached; looked up on every call if the
+// driver gives no context id.
 cudaError_t scratch_address(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = (unsigned char*)p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -90,6 +124,9 @@ extern "C" ET_API et_status et_step_static(int nx, int ny, int nz, double h, con
         return report(msg, msg_len, ET_ERR_ARG,
                       "grid %d x %d x %d has %lld voxels; the static scratch holds at most %lld (64^3)",
                       nx, ny, nz, n, kStaticMaxVoxels);
+    if (nz > 65535)
+        return report(msg, msg_len, ET_ERR_ARG, "grid %d x %d x %d: nz = %d exceeds 65535, the z extent of a launch",
+                      nx, ny, nz, nz);
     const unsigned long long nblocks = (unsigned long long)((nx + kBlockX - 1) / kBlockX) *
                                        ((ny + kBlockY - 1) / kBlockY) * (unsigned long long)nz;
     if (nblocks > kStaticMaxBlocks)

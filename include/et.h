@@ -54,7 +54,7 @@ typedef enum {
     ET_ERR_STATE = 2,       /* call order (e.g. et_step before et_set_coeffs) */
     ET_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has details */
     ET_ERR_NUMERIC = 4,     /* D < 0 or not finite; u out of range or non-finite */
-    ET_ERR_TIMEOUT = 5,     /* reserved for bounded device waits */
+    ET_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
     ET_ERR_UNSUPPORTED = 6  /* combination the library does not provide */
 } et_status;
 
@@ -108,6 +108,12 @@ typedef struct {
                          DF64; about half the memory traffic).  0 (default):
                          DF64 two, F32 one (its four-voxel one-term kernel is
                          the faster), F64 always one */
+    int timeout_probe_us; /* test hook, 0 (default): off.  1 .. 1000000: every
+                         two-term launch (F32, DF64) first waits this many
+                         microseconds on a device barrier that nothing
+                         completes, so its bounded wait runs out: the run
+                         stops early and the next synchronising call returns
+                         ET_ERR_TIMEOUT (the state u is then not valid) */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */
@@ -308,6 +314,18 @@ ET_API et_status et_step_static(int nx, int ny, int nz, double h, const double* 
 ET_API size_t et_probe_alu_scratch_bytes(void);
 ET_API et_status et_probe_alu(void* scratch, size_t scratch_bytes, void* cuda_stream,
                               double* fp64_tflops, double* fp32_tflops);
+/* Diagnostic, not part of the method: best streaming bandwidth (bytes read
+ * plus bytes written per second, GB/s) of a plain device kernel that writes
+ * dst[i] = the sum of nin input buffers at i (16-byte vectors), over a few
+ * launch shapes, each timed over `reps` back-to-back passes with CUDA events on
+ * cuda_stream.  nin = 1 is a copy; nin = 6 has the read/write mix of a stencil
+ * term.  With buffers inside the L2 this is the L2 roofline of an L2-resident
+ * kernel; with buffers far beyond it, the HBM roofline.
+ *  src: device, nin consecutive buffers of `bytes` each; dst: device, `bytes`,
+ *  not overlapping src; both 16-byte aligned; bytes a positive multiple of 16;
+ *  1 <= nin <= 8.  Synchronises the stream. */
+ET_API et_status et_probe_stream(const void* src, void* dst, size_t bytes, int nin, int reps, void* cuda_stream,
+                                 double* gbs);
 
 ET_API const char* et_last_error(const et_grid* g); /* g may be NULL: last create error */
 ET_API const char* et_status_string(et_status status);

@@ -38,7 +38,7 @@ SCHEMES = {"rosenbrock": ET_SCHEME_ROSENBROCK, "expeuler": ET_SCHEME_EXPEULER}
 class et_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("theta_max", ctypes.c_double), ("shift", ctypes.c_int),
                 ("force_s", ctypes.c_int), ("force_m", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("single_terms", ctypes.c_int)]
+                ("single_terms", ctypes.c_int), ("timeout_probe_us", ctypes.c_int)]
 
 
 class et_step_info(ctypes.Structure):
@@ -97,6 +97,7 @@ _SIGS = {
     "et_step_static": ([_I, _I, _I, _D, _VP, _D, _I, _I, _VP, _D, _VP, ctypes.c_char_p, ctypes.c_size_t], _I),
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+    "et_probe_stream": ([_VP, _VP, ctypes.c_size_t, _I, _I, _VP, ctypes.POINTER(_D)], _I),
 }
 
 _lock = threading.Lock()
@@ -145,13 +146,15 @@ def _check(rc: int, handle=None):
 
 
 def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True, single_terms=False,
-                 two_terms=False):
+                 two_terms=False, timeout_probe_us=0):
     """et_options; single_terms / two_terms force one / two Taylor terms per
-    launch (default: the form's own choice)."""
+    launch (default: the form's own choice); timeout_probe_us is the test hook
+    of the two-term kernel's bounded waits."""
     if single_terms and two_terms:
         raise ValueError("single_terms and two_terms exclude each other")
     return et_options(float(tol), float(theta_max), int(shift), int(force_s), int(force_m),
-                      1 if use_graph else -1, 1 if single_terms else (-1 if two_terms else 0))
+                      1 if use_graph else -1, 1 if single_terms else (-1 if two_terms else 0),
+                      int(timeout_probe_us))
 
 
 def select_schedule(tau, rmax, rho, scheme="rosenbrock", precision="f64", **opts):
@@ -347,6 +350,22 @@ def probe_alu(stream=None):
     f64, f32 = _D(), _D()
     _check(lib.et_probe_alu(buf.data_ptr(), nbytes, st.cuda_stream, ctypes.byref(f64), ctypes.byref(f32)))
     return f64.value, f32.value
+
+
+def probe_stream(nbytes, nin=1, reps=50, stream=None):
+    """Best read + write bandwidth (GB/s) of the library's streaming probe:
+    nin input buffers and one output of nbytes each (inside the L2: the L2
+    roofline; far beyond it: the HBM roofline)."""
+    import torch
+    lib = load()
+    nbytes = int(nbytes) // 16 * 16
+    src = torch.ones(nin * nbytes // 4, dtype=torch.float32, device="cuda")
+    dst = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    gbs = _D()
+    _check(lib.et_probe_stream(src.data_ptr(), dst.data_ptr(), nbytes, int(nin), int(reps), st.cuda_stream,
+                               ctypes.byref(gbs)))
+    return gbs.value
 
 
 class Batch:

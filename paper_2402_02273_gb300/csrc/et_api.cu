@@ -95,7 +95,8 @@ bool same_coeffs(const CoeffKey& a, const CoeffKey& b) {
     if (!a.opt_set) return true;
     const et_options &x = a.opt, &y = b.opt;
     return eq(x.tol, y.tol) && eq(x.theta_max, y.theta_max) && x.shift == y.shift && x.force_s == y.force_s &&
-           x.force_m == y.force_m && x.use_graph == y.use_graph && x.single_terms == y.single_terms;
+           x.force_m == y.force_m && x.use_graph == y.use_graph && x.single_terms == y.single_terms &&
+           x.timeout_probe_us == y.timeout_probe_us;
 }
 
 struct GraphEntry {
@@ -119,6 +120,7 @@ struct ResolvedOptions {
     double tol, theta_max;
     int shift, force_s, force_m, use_graph;
     int single_terms;  // 1: one term per launch; -1: two where possible; 0: per form
+    unsigned long long probe_ns;  // test hook of the two-term kernel's bounded waits (0: off)
 };
 
 ResolvedOptions resolve(const et_options* o, et_precision prec) {
@@ -136,6 +138,7 @@ ResolvedOptions resolve(const et_options* o, et_precision prec) {
     r.force_m = (o && o->force_m > 0) ? o->force_m : 0;
     r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
     r.single_terms = !o ? 0 : (o->single_terms > 0 ? 1 : (o->single_terms < 0 ? -1 : 0));
+    r.probe_ns = (o && o->timeout_probe_us > 0) ? 1000ull * (unsigned long long)o->timeout_probe_us : 0;
     return r;
 }
 
@@ -293,9 +296,16 @@ bool use_pairs(const et_grid* g) {
     if (g->prec == ET_F64 || !g->pair || !pair_preferred(g->op, g->prec)) return false;
     const int t = resolve(g->opt_set ? &g->opt : nullptr, g->prec).single_terms;
     if (t != 0) return t < 0;
+    // FP32: one term per launch (four-voxel kernel) while the Horner chain's
+    // seven fields (28 B a voxel) stay well inside the L2, two per launch
+    // beyond (us per term, one / two per launch: 128^3 5.8 / 8.2, 160^3
+    // 17.4 / 14.2, 192^3 35.0 / 23.5)
     constexpr double kL2Bytes = 129.0e6;
-    return g->prec == ET_DF64 || 32.0 * (double)g->n > 1.4 * kL2Bytes;
+    return g->prec == ET_DF64 || 28.0 * (double)g->n > 0.75 * kL2Bytes;
 }
+
+// Test hook of the two-term kernel's bounded waits (et_options.timeout_probe_us).
+unsigned long long probe_ns(const et_grid* g) { return g->opt_set ? resolve(&g->opt, g->prec).probe_ns : 0; }
 
 ChainPlan plan_chain(const et_grid* g, const Schedule& S, double hstep) {
     return et::plan_chain(g->prec, g->nu, S.s, S.m, S.mu, hstep);
@@ -339,8 +349,18 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
             if constexpr (std::is_same<T, double>::value) {
                 e = launch_term(g->G, g->op, B.W, op.a1, st);
             } else {
-                e = op.pair ? launch_term_pair(g->pair, g->G, g->op, op.a1, op.a2, g->flags, st)
-                            : launch_term(g->G, g->op, B.W, op.a1, st);
+                bool done = false;
+                if constexpr (std::is_same<T, float>::value) {
+                    // FP32 Horner pairs on the four-voxel two-term kernel where
+                    // it applies, other pairs on the TMA-fed one
+                    if (op.pair && quad_pair_eligible(g->G, B.W, op.a1, op.a2)) {
+                        e = launch_term_quad_pair(g->G, g->op, B.W, op.a1, op.a2, st);
+                        done = true;
+                    }
+                }
+                if (!done)
+                    e = op.pair ? launch_term_pair(g->pair, g->G, g->op, op.a1, op.a2, g->flags, st, probe_ns(g))
+                                : launch_term(g->G, g->op, B.W, op.a1, st);
             }
             if (e != cudaSuccess) return e;
             ++*launches;
@@ -386,7 +406,7 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
                     ++ti;
                     PairMaps M;
                     if (!pair_maps_for(g->pair, g->G, g->prec, a1.zin, B.b, B.dt, &M)) return cudaErrorInvalidValue;
-                    e = launch_term_pair_maps(M, g->G, g->op, a1, a2, g->flags, st);
+                    e = launch_term_pair_maps(M, g->G, g->op, a1, a2, g->flags, st, probe_ns(g));
                     if (!a2.last) zin = a2.zout;
                 } else {
                     const TermArgs<T> a = rec_args(t);
@@ -595,6 +615,8 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
             return fail(g, ET_ERR_ARG, "options.theta_max must be >= 0");
         if (opt->force_m == 1) return fail(g, ET_ERR_ARG, "options.force_m must be 0 or >= 2");
         if (opt->force_s < 0 || opt->force_m < 0) return fail(g, ET_ERR_ARG, "forced s, m must be >= 0");
+        if (opt->timeout_probe_us < 0 || opt->timeout_probe_us > 1000000)
+            return fail(g, ET_ERR_ARG, "options.timeout_probe_us must be in [0, 1000000]");
     }
     // cached graphs stay: a run reuses one only if its coefficient scalars match
     g->coeffs_set = false;

@@ -44,13 +44,16 @@ size_t term_desc_bytes(et_precision prec) {
 size_t pair_desc_bytes(et_precision prec) {
     return prec == ET_F64 ? 0 : (prec == ET_F32 ? sizeof(BatchPair<float>) : sizeof(BatchPair<float2>));
 }
+// F32 Horner pairs on the four-voxel two-term kernel
+size_t qpair_desc_bytes(et_precision prec) { return prec == ET_F32 ? sizeof(QuadPairGrid) : 0; }
 // Per grid: up to kMaxTermLaunches single terms, or half as many pairs, plus
 // its residual and stats descriptors.
 size_t desc_bytes_per_instance(et_precision prec) {
     const size_t res = prec == ET_F64 ? sizeof(BatchResidual<double>)
                                       : (prec == ET_F32 ? sizeof(BatchResidual<float>) : sizeof(BatchResidual<float2>));
-    return (size_t)kMaxTermLaunches * term_desc_bytes(prec) + (size_t)(kMaxTermLaunches / 2) * pair_desc_bytes(prec) +
-           res + sizeof(BatchStats) + 64;
+    return (size_t)kMaxTermLaunches * term_desc_bytes(prec) +
+           (size_t)(kMaxTermLaunches / 2) * (pair_desc_bytes(prec) + qpair_desc_bytes(prec)) + res +
+           sizeof(BatchStats) + 128;
 }
 
 struct BatchLayout {
@@ -89,7 +92,7 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
     L->ush = (prec != ET_F64) ? take(8ull * ntot) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks * count);
     L->desc = take(desc_bytes_per_instance(prec) * count);
-    L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec)) * count + 256);
+    L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec) + qpair_desc_bytes(prec)) * count + 256);
     L->misc = take(misc_bytes(count));
     L->total = off;
     return true;
@@ -127,9 +130,10 @@ struct et_batch {
     int nlaunch;                         // term launches per step
     // per launch index of a step: single-term descriptors (count, tiles, first)
     // and two-term descriptors (count, tiles, first)
-    std::vector<int> single_count, pair_count;
-    std::vector<long long> single_tiles, pair_tiles, single_first, pair_first;
+    std::vector<int> single_count, pair_count, qpair_count;
+    std::vector<long long> single_tiles, pair_tiles, single_first, pair_first, qpair_tiles, qpair_first;
     size_t pair_table_offset;              // byte offset of the two-term descriptors
+    size_t qpair_table_offset;             // byte offset of the four-voxel two-term descriptors (F32)
     std::vector<PairPlan*> pair_plans;     // per grid (F32 / DF64), nullptr: one term per launch
     long long res_tiles;
     double graph_tau;
@@ -293,15 +297,33 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
     b->pair_tiles.assign(nl, 0);
     b->single_first.assign(nl, 0);
     b->pair_first.assign(nl, 0);
+    b->qpair_count.assign(nl, 0);
+    b->qpair_tiles.assign(nl, 0);
+    b->qpair_first.assign(nl, 0);
     std::vector<BatchTerm<T>> singles;
     std::vector<BatchPair<T>> pairs;
+    std::vector<QuadPairGrid> qpairs;
     for (int l = 0; l < nl; ++l) {
         b->single_first[l] = (long long)singles.size();
         b->pair_first[l] = (long long)pairs.size();
-        long long st = 0, pt = 0;
+        b->qpair_first[l] = (long long)qpairs.size();
+        long long st = 0, pt = 0, qt = 0;
         for (int i = 0; i < C; ++i) {
             if (l >= (int)ops[i].size()) continue;
             const ChainOp<T>& op = ops[i][l];
+            bool quad = false;
+            if constexpr (std::is_same<T, float>::value) {
+                // FP32 Horner pairs: the four-voxel two-term kernel where it applies
+                const Geom G = geom_of(b, i);
+                const Weights<float> W = typed_weights<float>(b, i);
+                if (op.pair && quad_pair_eligible(G, W, op.a1, op.a2)) {
+                    const int tz = G.nz < 32 ? G.nz : 32;
+                    qpairs.push_back(quad_pair_grid(G, W, op.a1, op.a2, tz, qt));
+                    qt += quad_pair_tiles(G, tz);
+                    quad = true;
+                }
+            }
+            if (quad) continue;
             if (op.pair) {
                 BatchPair<T> d;
                 std::memset(&d, 0, sizeof(d));
@@ -329,6 +351,8 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         b->pair_count[l] = (int)((long long)pairs.size() - b->pair_first[l]);
         b->single_tiles[l] = st;
         b->pair_tiles[l] = pt;
+        b->qpair_count[l] = (int)((long long)qpairs.size() - b->qpair_first[l]);
+        b->qpair_tiles[l] = qt;
     }
     // stats descriptors
     std::vector<BatchStats> stv(C);
@@ -348,21 +372,26 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         sk.ush = b->prec != ET_F64 ? field<float2>(b, b->L.ush, i) : nullptr;
     }
     // [residual x C][stats x C][single terms][pad to 64 bytes][two-term]
+    // [pad][four-voxel two-term]
     const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
     b->pair_table_offset = align64(head + sizeof(BatchTerm<T>) * singles.size());
-    bytes.assign(b->pair_table_offset + sizeof(BatchPair<T>) * pairs.size(), 0);
+    b->qpair_table_offset = align64(b->pair_table_offset + sizeof(BatchPair<T>) * pairs.size());
+    bytes.assign(b->qpair_table_offset + sizeof(QuadPairGrid) * qpairs.size(), 0);
     char* p = bytes.data();
     std::memcpy(p, res.data(), sizeof(BatchResidual<T>) * C);
     std::memcpy(p + sizeof(BatchResidual<T>) * C, stv.data(), sizeof(BatchStats) * C);
     if (!singles.empty()) std::memcpy(p + head, singles.data(), sizeof(BatchTerm<T>) * singles.size());
     if (!pairs.empty()) std::memcpy(p + b->pair_table_offset, pairs.data(), sizeof(BatchPair<T>) * pairs.size());
+    if (!qpairs.empty())
+        std::memcpy(p + b->qpair_table_offset, qpairs.data(), sizeof(QuadPairGrid) * qpairs.size());
     return ET_OK;
 }
 
 // The launches of launch index l from a table at dtab (single terms at
 // dtab + head, two-term descriptors at dtab + pair_table_offset).
 template <typename T>
-cudaError_t launch_index(et_batch* b, const char* dsingles, const char* dpairs, int l, int variant, cudaStream_t st) {
+cudaError_t launch_index(et_batch* b, const char* dsingles, const char* dpairs, const char* dqpairs, int l,
+                         int variant, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (b->single_count[l] > 0)
         e = launch_batch_term(b->op, single_variant(b->prec, variant),
@@ -371,7 +400,13 @@ cudaError_t launch_index(et_batch* b, const char* dsingles, const char* dpairs, 
     if constexpr (!std::is_same<T, double>::value) {
         if (e == cudaSuccess && b->pair_count[l] > 0)
             e = launch_batch_term_pair<T>(b->op, reinterpret_cast<const BatchPair<T>*>(dpairs) + b->pair_first[l],
-                                          b->pair_count[l], b->pair_tiles[l], b->sms, flags_of(b), st);
+                                          b->pair_count[l], b->pair_tiles[l], b->sms, flags_of(b), st,
+                                          b->opt_set && b->opt.timeout_probe_us > 0
+                                              ? 1000ull * (unsigned long long)b->opt.timeout_probe_us
+                                              : 0ull);
+        if (e == cudaSuccess && b->qpair_count[l] > 0)
+            e = launch_batch_term_quad_pair(b->op, reinterpret_cast<const QuadPairGrid*>(dqpairs) + b->qpair_first[l],
+                                            b->qpair_count[l], b->qpair_tiles[l], b->sms, st);
     }
     return e;
 }
@@ -383,10 +418,11 @@ et_status enqueue_batch_step(et_batch* b, char* dtab, cudaStream_t st) {
     const BatchStats* sts = (const BatchStats*)(dtab + sizeof(BatchResidual<T>) * C);
     const char* dsingles = dtab + sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
     const char* dpairs = dtab + b->pair_table_offset;
+    const char* dqpairs = dtab + b->qpair_table_offset;
     cudaError_t e = launch_batch_residual<T>(b->op, (int)b->scheme, res, C, b->res_tiles, flags_of(b), st);
     if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched residual: %s", cudaGetErrorString(e));
     for (int l = 0; l < b->nlaunch; ++l) {
-        e = launch_index<T>(b, dsingles, dpairs, l, b->table_variant, st);
+        e = launch_index<T>(b, dsingles, dpairs, dqpairs, l, b->table_variant, st);
         if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "batched term: %s", cudaGetErrorString(e));
     }
     e = launch_batch_stats(sts, C, st);
@@ -440,13 +476,18 @@ et_status autotune(et_batch* b, double tau, double* us_out) {
         // the descriptors of launch index 0 only
         const size_t ns = sizeof(BatchTerm<T>) * b->single_count[0];
         const size_t np = pair_desc_bytes(b->prec) * b->pair_count[0];
+        const size_t nq = qpair_desc_bytes(b->prec) * b->qpair_count[0];
         char* dst = b->ws + b->L.tune_desc;
         const size_t poff = align64(ns);
+        const size_t qoff = align64(poff + np);
         cudaError_t ce = cudaSuccess;
         if (ns) ce = cudaMemcpyAsync(dst, bytes.data() + head + sizeof(BatchTerm<T>) * b->single_first[0], ns,
                                      cudaMemcpyHostToDevice, b->stream);
         if (ce == cudaSuccess && np)
             ce = cudaMemcpyAsync(dst + poff, bytes.data() + b->pair_table_offset, np, cudaMemcpyHostToDevice,
+                                 b->stream);
+        if (ce == cudaSuccess && nq)
+            ce = cudaMemcpyAsync(dst + qoff, bytes.data() + b->qpair_table_offset, nq, cudaMemcpyHostToDevice,
                                  b->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
         // voxel-terms advanced by launch index 0
@@ -458,15 +499,18 @@ et_status autotune(et_batch* b, double tau, double* us_out) {
             if constexpr (!std::is_same<T, double>::value) {
                 const BatchPair<T>* pd = reinterpret_cast<const BatchPair<T>*>(bytes.data() + b->pair_table_offset);
                 for (int q = 0; q < b->pair_count[0]; ++q) vterms += 2.0 * (double)pd[q].G.n;
+                const QuadPairGrid* qd = reinterpret_cast<const QuadPairGrid*>(bytes.data() + b->qpair_table_offset);
+                for (int q = 0; q < b->qpair_count[0]; ++q) vterms += 2.0 * (double)qd[q].G.n;
             }
         }
         // launch_index reads single_first / pair_first: point them at the copies
         b->single_first[0] = 0;
         b->pair_first[0] = 0;
+        b->qpair_first[0] = 0;
         float ms = 0.f;
         for (int r = 0; r < 4 && ce == cudaSuccess; ++r) {  // one warm-up launch, then three timed
             if (r == 1) ce = cudaEventRecord(e0, b->stream);
-            if (ce == cudaSuccess) ce = launch_index<T>(b, dst, dst + poff, 0, v, b->stream);
+            if (ce == cudaSuccess) ce = launch_index<T>(b, dst, dst + poff, dst + qoff, 0, v, b->stream);
         }
         if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
         if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -615,6 +659,7 @@ et_status et_batch_create(int count, const int* dims, double h, et_precision pre
     b->variant = -1;
     b->err[0] = 0;
     b->pair_table_offset = 0;
+    b->qpair_table_offset = 0;
     b->pair_plans.assign(count, nullptr);
     if (precision != ET_F64) {
         // tensor maps of every grid's fields for the two-term kernel (nullptr:
@@ -653,6 +698,8 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
             return bfail(b, ET_ERR_ARG, "options.theta_max must be >= 0");
         if (options->force_m == 1) return bfail(b, ET_ERR_ARG, "options.force_m must be 0 or >= 2");
         if (options->force_s < 0 || options->force_m < 0) return bfail(b, ET_ERR_ARG, "forced s, m must be >= 0");
+        if (options->timeout_probe_us < 0 || options->timeout_probe_us > 1000000)
+            return bfail(b, ET_ERR_ARG, "options.timeout_probe_us must be in [0, 1000000]");
     }
     BDeviceGuard dg(b->device);
     clear_graph(b);

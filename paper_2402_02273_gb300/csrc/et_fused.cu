@@ -30,6 +30,9 @@
 //
 // Every mbarrier wait is bounded; a wait that runs out sets ET_FLAG_TIMEOUT,
 // waits (bounded) for the block's copies still in flight and ends the block.
+// A test hook (probe_ns > 0) makes every block's first wait also wait, for at
+// most probe_ns, on a barrier that nothing completes, so that this path runs
+// without stalling the device.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -84,7 +87,8 @@ struct Shape {
     // + planes L - 3 (second term), L - 1, L (first term), L - 2
     __host__ __device__ static constexpr int stages(bool literal) { return prefetch(literal) + 4; }
     __host__ __device__ static constexpr int smem_bytes(bool literal) {
-        return 128 + stages(literal) * stage_bytes(literal) + kRing * kHalo * ES + stages(literal) * 8;
+        // + one mbarrier per stage and the probe barrier
+        return 128 + stages(literal) * stage_bytes(literal) + kRing * kHalo * ES + (stages(literal) + 1) * 8;
     }
 };
 
@@ -173,13 +177,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait for the phase of the given parity to complete, for at most about
-// kWaitNs of the global timer (and kWaitTries polls).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// limit_ns of the global timer (and kWaitTries polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = kWaitNs) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (int i = 0; i < kWaitTries; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -264,7 +268,7 @@ __device__ __forceinline__ TileGeom tile_of(const Src& src, int gi, long long ti
 }
 
 template <int OP, typename T, int MODE, typename Src>
-__device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
+__device__ __forceinline__ void pair_body(const Src& src, unsigned* flags, unsigned long long probe_ns) {
     using S = Shape<T>;
     using A = Arith<T>;
     constexpr bool kLit = OP == ET_OP_LITERAL;
@@ -280,7 +284,7 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
     uint64_t* const full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes + kRing * kHalo * sizeof(T));
     const int t = threadIdx.x;
     if (t == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s <= kStages; ++s) mbar_init(&full[s], 1);  // full[kStages]: the probe's
         mbar_fence_init();
     }
     __syncthreads();
@@ -512,8 +516,11 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags) {
         // plane L - 3, whose z_a neighbours were all written in earlier
         // iterations, so one barrier per plane separates the two.  Planes
         // k0 - 2 .. k0 + 2 fill the carries and the z_a ring.
-        if (timed_out(advance())) return;
         bool ok = advance();
+        // test hook: a wait that nothing ends, bounded by probe_ns
+        if (probe_ns && tile == blockIdx.x) ok = mbar_wait(&full[kStages], 0, probe_ns) && ok;
+        if (timed_out(ok)) return;
+        ok = advance();
         if (ok && has_b) {
             b_zm = reinterpret_cast<const T*>(sp + S::kZj)[bz];
             b_w2m = reinterpret_cast<const T*>(sp + S::kW2)[b10];
@@ -549,18 +556,19 @@ template <int OP, typename T, int MODE>
 __global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 3 : 2)
 term2_kernel(const __grid_constant__ PairMaps M, const __grid_constant__ Geom G,
              const __grid_constant__ TermArgs<T> a1, const __grid_constant__ TermArgs<T> a2, int tz,
-             unsigned* flags) {
+             unsigned* flags, unsigned long long probe_ns) {
     const long long total = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
                             ((G.nz + tz - 1) / tz);
     const OneGrid<T> src{&M, &G, &a1, &a2, tz, total};
-    pair_body<OP, T, MODE>(src, flags);
+    pair_body<OP, T, MODE>(src, flags, probe_ns);
 }
 
 template <int OP, typename T>
 __global__ void __launch_bounds__(kPairThreads, sizeof(T) == 4 ? 3 : 2)
-batch_term2_kernel(const BatchPair<T>* __restrict__ d, int count, long long total, unsigned* flags) {
+batch_term2_kernel(const BatchPair<T>* __restrict__ d, int count, long long total, unsigned* flags,
+                   unsigned long long probe_ns) {
     const GridTable<T> src{d, count, total};
-    pair_body<OP, T, kModeTable>(src, flags);
+    pair_body<OP, T, kModeTable>(src, flags, probe_ns);
 }
 
 template <typename K>
@@ -645,30 +653,38 @@ bool pair_shape_ok(const TermArgs<T>& a1, const TermArgs<T>& a2) {
 
 template <int OP, typename T, int MODE>
 cudaError_t launch_pair_mode(const PairMaps& M, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
-                             unsigned* flags, cudaStream_t stream) {
+                             unsigned* flags, unsigned long long probe_ns, cudaStream_t stream) {
     const long long cap = (long long)(G.sms > 0 ? G.sms : 1) * pair_blocks_per_sm<OP, T, MODE>();
     const int tz = choose_tz(G, cap);
     const long long tiles = (long long)((G.nx + kBlockX - 1) / kBlockX) * ((G.ny + kBlockY - 1) / kBlockY) *
                             ((G.nz + tz - 1) / tz);
     const int smem = Shape<T>::smem_bytes(OP == ET_OP_LITERAL);
-    term2_kernel<OP, T, MODE><<<(unsigned)(tiles < cap ? tiles : cap), kPairThreads, smem, stream>>>(M, G, a1, a2,
-                                                                                                    tz, flags);
+    term2_kernel<OP, T, MODE><<<(unsigned)(tiles < cap ? tiles : cap), kPairThreads, smem, stream>>>(
+        M, G, a1, a2, tz, flags, probe_ns);
     return cudaGetLastError();
+}
+
+// The kernel variant for the term shapes of a1 and a2.
+template <int OP, typename T>
+cudaError_t launch_pair_shape(const PairMaps& M, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
+                              unsigned* flags, unsigned long long probe_ns, cudaStream_t stream) {
+    if (!pair_shape_ok(a1, a2)) return cudaErrorInvalidValue;
+    if (a1.horner) {
+        if (a1.has_zscale)
+            return launch_pair_mode<OP, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, probe_ns, stream);
+        return launch_pair_mode<OP, T, kModeHorner>(M, G, a1, a2, flags, probe_ns, stream);
+    }
+    if (a1.has_zscale) return cudaErrorInvalidValue;  // only the chain's first (Horner) term is scaled
+    if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeBaseZ>(M, G, a1, a2, flags, probe_ns, stream);
+    return launch_pair_mode<OP, T, 0>(M, G, a1, a2, flags, probe_ns, stream);
 }
 
 template <int OP, typename T>
 cudaError_t launch_pair_op(const PairPlan* P, const Geom& G, const TermArgs<T>& a1, const TermArgs<T>& a2,
-                           unsigned* flags, cudaStream_t stream) {
-    if (!pair_shape_ok(a1, a2)) return cudaErrorInvalidValue;
+                           unsigned* flags, unsigned long long probe_ns, cudaStream_t stream) {
     PairMaps M;
     if (!pair_maps(P, a1.zin, &M)) return cudaErrorInvalidValue;
-    if (a1.horner) {
-        if (a1.has_zscale) return launch_pair_mode<OP, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream);
-        return launch_pair_mode<OP, T, kModeHorner>(M, G, a1, a2, flags, stream);
-    }
-    if (a1.has_zscale) return cudaErrorInvalidValue;  // only the chain's first (Horner) term is scaled
-    if (a1.base_mode == 2) return launch_pair_mode<OP, T, kModeBaseZ>(M, G, a1, a2, flags, stream);
-    return launch_pair_mode<OP, T, 0>(M, G, a1, a2, flags, stream);
+    return launch_pair_shape<OP, T>(M, G, a1, a2, flags, probe_ns, stream);
 }
 
 template <int OP, typename T>
@@ -742,31 +758,19 @@ bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const vo
 
 template <typename T>
 cudaError_t launch_term_pair_maps(const PairMaps& M, const Geom& G, et_operator op, const TermArgs<T>& a1,
-                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream) {
-    if (!pair_shape_ok(a1, a2)) return cudaErrorInvalidValue;
-    if (op == ET_OP_CONSERVATIVE) {
-        if (a1.horner)
-            return a1.has_zscale ? launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeHorner | kModeZscale>(M, G, a1, a2,
-                                                                                                    flags, stream)
-                                 : launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeHorner>(M, G, a1, a2, flags, stream);
-        if (a1.has_zscale) return cudaErrorInvalidValue;
-        return a1.base_mode == 2 ? launch_pair_mode<ET_OP_CONSERVATIVE, T, kModeBaseZ>(M, G, a1, a2, flags, stream)
-                                 : launch_pair_mode<ET_OP_CONSERVATIVE, T, 0>(M, G, a1, a2, flags, stream);
-    }
-    if (a1.horner)
-        return a1.has_zscale
-                   ? launch_pair_mode<ET_OP_LITERAL, T, kModeHorner | kModeZscale>(M, G, a1, a2, flags, stream)
-                   : launch_pair_mode<ET_OP_LITERAL, T, kModeHorner>(M, G, a1, a2, flags, stream);
-    if (a1.has_zscale) return cudaErrorInvalidValue;
-    return a1.base_mode == 2 ? launch_pair_mode<ET_OP_LITERAL, T, kModeBaseZ>(M, G, a1, a2, flags, stream)
-                             : launch_pair_mode<ET_OP_LITERAL, T, 0>(M, G, a1, a2, flags, stream);
+                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream,
+                                  unsigned long long probe_ns) {
+    if (op == ET_OP_CONSERVATIVE)
+        return launch_pair_shape<ET_OP_CONSERVATIVE, T>(M, G, a1, a2, flags, probe_ns, stream);
+    return launch_pair_shape<ET_OP_LITERAL, T>(M, G, a1, a2, flags, probe_ns, stream);
 }
 
 template cudaError_t launch_term_pair_maps<float>(const PairMaps&, const Geom&, et_operator, const TermArgs<float>&,
-                                                  const TermArgs<float>&, unsigned*, cudaStream_t);
+                                                  const TermArgs<float>&, unsigned*, cudaStream_t,
+                                                  unsigned long long);
 template cudaError_t launch_term_pair_maps<float2>(const PairMaps&, const Geom&, et_operator,
                                                    const TermArgs<float2>&, const TermArgs<float2>&, unsigned*,
-                                                   cudaStream_t);
+                                                   cudaStream_t, unsigned long long);
 
 // Batched launches hold many grids, so every block has several tiles even
 // with whole columns: segments of up to 64 planes.
@@ -774,30 +778,33 @@ int batch_pair_tz(const Geom& G) { return G.nz < 64 ? (G.nz > 0 ? G.nz : 1) : 64
 
 template <typename T>
 cudaError_t launch_batch_term_pair(et_operator op, const BatchPair<T>* d, int count, long long tiles, int sms,
-                                   unsigned* flags, cudaStream_t stream) {
+                                   unsigned* flags, cudaStream_t stream, unsigned long long probe_ns) {
     const int smem = Shape<T>::smem_bytes(op == ET_OP_LITERAL);
     const int per_sm = op == ET_OP_CONSERVATIVE ? batch_pair_blocks_per_sm<ET_OP_CONSERVATIVE, T>()
                                                 : batch_pair_blocks_per_sm<ET_OP_LITERAL, T>();
     const long long cap = (long long)(sms > 0 ? sms : 1) * per_sm;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
     if (op == ET_OP_CONSERVATIVE)
-        batch_term2_kernel<ET_OP_CONSERVATIVE, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags);
+        batch_term2_kernel<ET_OP_CONSERVATIVE, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags,
+                                                                                         probe_ns);
     else
-        batch_term2_kernel<ET_OP_LITERAL, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags);
+        batch_term2_kernel<ET_OP_LITERAL, T><<<grid, kPairThreads, smem, stream>>>(d, count, tiles, flags, probe_ns);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_batch_term_pair<float>(et_operator, const BatchPair<float>*, int, long long, int,
-                                                   unsigned*, cudaStream_t);
+                                                   unsigned*, cudaStream_t, unsigned long long);
 template cudaError_t launch_batch_term_pair<float2>(et_operator, const BatchPair<float2>*, int, long long, int,
-                                                    unsigned*, cudaStream_t);
+                                                    unsigned*, cudaStream_t, unsigned long long);
 
 template <typename T>
 cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
-                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream) {
+                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream,
+                             unsigned long long probe_ns) {
     if (!P) return cudaErrorInvalidValue;
-    if (op == ET_OP_CONSERVATIVE) return launch_pair_op<ET_OP_CONSERVATIVE, T>(P, G, a1, a2, flags, stream);
-    return launch_pair_op<ET_OP_LITERAL, T>(P, G, a1, a2, flags, stream);
+    if (op == ET_OP_CONSERVATIVE)
+        return launch_pair_op<ET_OP_CONSERVATIVE, T>(P, G, a1, a2, flags, probe_ns, stream);
+    return launch_pair_op<ET_OP_LITERAL, T>(P, G, a1, a2, flags, probe_ns, stream);
 }
 
 bool pair_preferred(et_operator op, et_precision prec) {
@@ -823,8 +830,9 @@ cudaError_t prime_launch_limits_pair() {
 }
 
 template cudaError_t launch_term_pair<float>(const PairPlan*, const Geom&, et_operator, const TermArgs<float>&,
-                                             const TermArgs<float>&, unsigned*, cudaStream_t);
+                                             const TermArgs<float>&, unsigned*, cudaStream_t, unsigned long long);
 template cudaError_t launch_term_pair<float2>(const PairPlan*, const Geom&, et_operator, const TermArgs<float2>&,
-                                              const TermArgs<float2>&, unsigned*, cudaStream_t);
+                                              const TermArgs<float2>&, unsigned*, cudaStream_t,
+                                              unsigned long long);
 
 }  // namespace et

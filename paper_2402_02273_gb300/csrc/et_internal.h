@@ -257,7 +257,9 @@ struct BatchPair {
 };
 
 // Two consecutive terms of one sub-step (a1 not last) in one TMA-fed launch
-// (et_fused.cu): a1's outputs are not written, a2's are.  The plan holds the
+// (et_fused.cu): a1's outputs are not written, a2's are.  probe_ns > 0 (a test
+// hook, et_options.timeout_probe_us) makes each block first wait that long on
+// a barrier nothing completes, so the launch reports ET_FLAG_TIMEOUT.  The plan holds the
 // tensor maps of one grid's fields: typed weights wt[0..3], b, the diagonal
 // dt and the vectors Y0, Y1, Z0, Z1 (a1.zin must be b or one of these).
 // pair_plan_create returns nullptr where TMA cannot address the rows.
@@ -267,7 +269,8 @@ PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const w
 void pair_plan_destroy(PairPlan* P);
 template <typename T>
 cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
-                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
+                             const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream,
+                             unsigned long long probe_ns = 0);
 // Fills the tensor maps of a pair launch (a1.zin selects the z_j map); false
 // if a1.zin is none of the plan's vectors.
 bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out);
@@ -279,7 +282,8 @@ bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const vo
 // first term (a recorded chain).
 template <typename T>
 cudaError_t launch_term_pair_maps(const PairMaps& M, const Geom& G, et_operator op, const TermArgs<T>& a1,
-                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream);
+                                  const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream,
+                                  unsigned long long probe_ns = 0);
 // Whether two terms per launch beat two one-term launches for this operator
 // and form (resident blocks per SM of the pair kernel: at least 2).
 bool pair_preferred(et_operator op, et_precision prec);
@@ -288,7 +292,31 @@ int batch_pair_tz(const Geom& G);
 // Batched two-term launch over count grids (device table d, tiles in all).
 template <typename T>
 cudaError_t launch_batch_term_pair(et_operator op, const BatchPair<T>* d, int count, long long tiles, int sms,
-                                   unsigned* flags, cudaStream_t stream);
+                                   unsigned* flags, cudaStream_t stream, unsigned long long probe_ns = 0);
+// Two consecutive Horner terms of sub-step 0 in one launch, FP32, four voxels
+// per thread on full-width tiles of th rows and tz planes, fed by asynchronous
+// copies (et_quadpair.cu); the per-voxel arithmetic of the one-term kernels.
+// Eligible: nx % 4 == 0, nx <= 256, 16-byte aligned fields, n < 2^31, a1 and a2 Horner terms
+// (a1 not last, a2 not scaled) on the same b and diagonal.
+struct QuadPairGrid {
+    Geom G;
+    Weights<float> W;
+    TermArgs<float> a1, a2;
+    long long tile_begin;  // first tile of this grid in a batched launch
+    int th, tz;            // rows and planes of a tile
+};
+bool quad_pair_eligible(const Geom& G, const Weights<float>& W, const TermArgs<float>& a1,
+                        const TermArgs<float>& a2);
+int quad_pair_rows(const Geom& G);
+long long quad_pair_tiles(const Geom& G, int tz);
+QuadPairGrid quad_pair_grid(const Geom& G, const Weights<float>& W, const TermArgs<float>& a1,
+                            const TermArgs<float>& a2, int tz, long long tile_begin);
+cudaError_t launch_term_quad_pair(const Geom& G, et_operator op, const Weights<float>& W, const TermArgs<float>& a1,
+                                  const TermArgs<float>& a2, cudaStream_t stream);
+// Batched launch over count grids (device table d, tiles in all).
+cudaError_t launch_batch_term_quad_pair(et_operator op, const QuadPairGrid* d, int count, long long tiles, int sms,
+                                        cudaStream_t stream);
+cudaError_t prime_launch_limits_quad_pair();
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);
 // Adjoint launchers (et_adjoint.cu).

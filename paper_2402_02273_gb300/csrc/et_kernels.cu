@@ -663,6 +663,7 @@ cudaError_t prime_launch_limits() {
     term_blocks_per_sm<ET_OP_LITERAL, float>();
     prime_launch_limits_df64();
     prime_launch_limits_pair();
+    prime_launch_limits_quad_pair();
     return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 // only; no part of the integrator uses it.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "et.h"
 
 namespace {
@@ -72,4 +74,119 @@ extern "C" ET_API size_t et_probe_alu_scratch_bytes(void) {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     return (size_t)sms * 8 * kProbeThreads * sizeof(double);
+}
+
+// ---- streaming-bandwidth probe ----------------------------------------------
+// A plain device stream: dst[i] = sum of nin input buffers at i (16-byte loads
+// and stores, four in flight per input, grid-stride over all SMs).  nin = 1 is
+// a copy; nin = 6 reads six fields for one written, the mix of a stencil term
+// (z, three weights, the diagonal, b in; one term out).  With every buffer far
+// larger than the L2 it measures HBM; with all of them inside the L2 (the FP32
+// chain of a 128^3 grid keeps its fields there) it measures the L2.
+
+namespace {
+
+constexpr int kStreamUnroll = 4;
+constexpr int kStreamMaxIn = 8;
+
+template <int NIN>
+__global__ void stream_probe_kernel(const float4* __restrict__ src, float4* __restrict__ dst, long long n4) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kStreamUnroll - 1) * stride < n4; i += kStreamUnroll * stride) {
+        float4 v[kStreamUnroll];
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) v[u] = src[i + u * stride];
+#pragma unroll
+        for (int f = 1; f < NIN; ++f) {
+#pragma unroll
+            for (int u = 0; u < kStreamUnroll; ++u) {
+                const float4 w = src[f * n4 + i + u * stride];
+                v[u].x += w.x;
+                v[u].y += w.y;
+                v[u].z += w.z;
+                v[u].w += w.w;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) dst[i + u * stride] = v[u];
+    }
+    for (; i < n4; i += stride) {
+        float4 v = src[i];
+        for (int f = 1; f < NIN; ++f) {
+            const float4 w = src[f * n4 + i];
+            v.x += w.x;
+            v.y += w.y;
+            v.z += w.z;
+            v.w += w.w;
+        }
+        dst[i] = v;
+    }
+}
+
+template <int NIN>
+void launch_stream(int blocks, int threads, cudaStream_t st, const float4* src, float4* dst, long long n4) {
+    stream_probe_kernel<NIN><<<blocks, threads, 0, st>>>(src, dst, n4);
+}
+
+void launch_stream_n(int nin, int blocks, int threads, cudaStream_t st, const float4* src, float4* dst,
+                     long long n4) {
+    switch (nin) {
+        case 1: launch_stream<1>(blocks, threads, st, src, dst, n4); break;
+        case 2: launch_stream<2>(blocks, threads, st, src, dst, n4); break;
+        case 3: launch_stream<3>(blocks, threads, st, src, dst, n4); break;
+        case 4: launch_stream<4>(blocks, threads, st, src, dst, n4); break;
+        case 5: launch_stream<5>(blocks, threads, st, src, dst, n4); break;
+        case 6: launch_stream<6>(blocks, threads, st, src, dst, n4); break;
+        case 7: launch_stream<7>(blocks, threads, st, src, dst, n4); break;
+        default: launch_stream<8>(blocks, threads, st, src, dst, n4); break;
+    }
+}
+
+}  // namespace
+
+extern "C" ET_API et_status et_probe_stream(const void* src, void* dst, size_t bytes, int nin, int reps,
+                                            void* cuda_stream, double* gbs) {
+    if (!src || !dst || !gbs || reps < 1 || nin < 1 || nin > kStreamMaxIn || bytes < 16 || (bytes & 15u) ||
+        ((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u))
+        return ET_ERR_ARG;
+    const char* s = (const char*)src;
+    char* d = (char*)dst;
+    const size_t in_bytes = bytes * (size_t)nin;
+    if (!(s + in_bytes <= d || d + bytes <= s)) return ET_ERR_ARG;  // the output must not overlap the inputs
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ET_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ET_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return ET_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ET_ERR_CUDA;
+    }
+    const long long n4 = (long long)(bytes / 16);
+    // launch shapes: threads per block x blocks per SM; the best one counts
+    const int shapes[][2] = {{256, 4}, {256, 8}, {512, 4}, {1024, 2}};
+    double best = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (const auto& sh : shapes) {
+        const int blocks = sms * sh[1];
+        for (int w = 0; w < 3; ++w) launch_stream_n(nin, blocks, sh[0], st, (const float4*)src, (float4*)dst, n4);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r) launch_stream_n(nin, blocks, sh[0], st, (const float4*)src, (float4*)dst, n4);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const double rate = (double)(nin + 1) * (double)bytes * reps / (ms * 1e-3) / 1e9;
+        if (rate > best) best = rate;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return ET_ERR_CUDA;
+    *gbs = best;
+    return ET_OK;
 }

@@ -180,6 +180,7 @@ def test_bench_launch_mix_and_kernel_choice():
     assert bench.term_kernel_of("f64", False, 128 ** 3) == ("term_kernel_f64", False)
     assert bench.term_kernel_of("df64", False, 128 ** 3) == ("term2_kernel", True)
     assert bench.term_kernel_of("df64", True, 128 ** 3) == ("term_kernel_df64", False)
-    assert bench.term_kernel_of("f32", False, 160 ** 3) == ("term_quad_kernel", False)
-    assert bench.term_kernel_of("f32", False, 192 ** 3) == ("term2_kernel", True)
+    assert bench.term_kernel_of("f32", False, 128 ** 3) == ("term_quad_kernel", False)
+    assert bench.term_kernel_of("f32", False, 160 ** 3) == ("term2_quad_kernel", True)
+    assert bench.term_kernel_of("f32", False, 192 ** 3) == ("term2_quad_kernel", True)
     assert bench.term_kernel_of("f32", True, 192 ** 3) == ("term_quad_kernel", False)

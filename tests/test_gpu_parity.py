@@ -122,7 +122,8 @@ def _run_states(et, torch, D, u0, tau, nsteps, precision, **kw):
 @pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "rosenbrock"),
                                        ("conservative", "expeuler")])
 @pytest.mark.parametrize("shape", [(5, 17, 33), (9, 8, 40), (1, 1, 45), (3, 70, 2), (40, 12, 36), (7, 19, 68),
-                                   (33, 9, 64), (2, 3, 8), (6, 5, 4), (4, 9, 132)])
+                                   (33, 9, 64), (2, 3, 8), (6, 5, 4), (4, 9, 132), (6, 40, 128), (11, 23, 160),
+                                   (5, 31, 96)])
 @pytest.mark.parametrize("sched", [{}, {"force_s": 3, "force_m": 5}, {"force_s": 2, "force_m": 4},
                                    {"force_s": 1, "force_m": 2}])
 def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op, scheme, shape, sched):
@@ -134,7 +135,10 @@ def test_term_pairs_match_single_terms_bitwise(et_mod, torch_cuda, precision, op
     (no pair); the shapes cover ragged y and z, several x tiles and z segments.
     FP32 single terms on rows of a multiple of 4 voxels run the four-voxel
     kernel (rows of one quad, rows longer than a warp's 32 quads, rows split
-    between blocks), so this also checks it against the two-term kernel."""
+    between blocks), so this also checks it against the two-term kernels.  FP32
+    Horner pairs on such rows take the four-voxel two-term kernel (full-width
+    tiles; the last three shapes have several tiles in y), running-sum pairs
+    the TMA-fed one."""
     D = (0.01 + 0.2 * phantom.uniform(5, 7, int(np.prod(shape)))).reshape(shape)
     D = D.astype(np.float32).astype(np.float64)
     u0 = 0.9 * phantom.uniform(5, 8, D.size).reshape(shape)

@@ -64,26 +64,58 @@ def launch_mix(prec, s, m, pairs):
     return launches, nbytes, flops
 
 
-# DRAM bytes per term launch at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of each current kernel (cold cache; a DF64 launch covers
-# two terms); None where the kernel changed after the capture.
-TERM_TRAFFIC = {("f64", "term_kernel_f64"): 107.0e6, ("df64", "term2_kernel"): 115.1e6,
-                ("f32", "term_quad_kernel"): 50.4e6, ("f32", "term2_kernel"): None}
+# DRAM bytes per voxel of one term launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over the voxels of the launch) from one ncu capture of
+# each kernel in its steady state (--cache-control none, a launch in the middle
+# of a run; a two-term launch covers two terms), keyed by (form, kernel, grid
+# edge or "batch"), with the SHA-256 prefix of the kernel's source file at the
+# capture: a kernel changed since then reports null.  The batched launch is
+# captured on the first 8 grids of the batch (19.0 M voxels) and scaled to the
+# whole launch by its voxels (traffic grows with them: no re-reads across grids).
+TERM_TRAFFIC = {
+    ("f64", "term_kernel_f64", 128): (133101312 / 128 ** 3, "41309fa9a1cf"),
+    ("f32", "term_quad_kernel", 128): (356608 / 128 ** 3, "a6bae89026da"),
+    ("df64", "term2_kernel", 128): (98716672 / 128 ** 3, "6b1e73fcb9ec"),
+    ("df64", "term2_kernel", 192): (414701056 / 192 ** 3, "6b1e73fcb9ec"),
+    ("f32", "term2_quad_kernel", 160): (74726144 / 160 ** 3, "6ba6fd188ae6"),
+    ("f32", "term2_quad_kernel", 192): (201267456 / 192 ** 3, "6ba6fd188ae6"),
+    ("f32", "batch_term2_quad_kernel", "batch"): (561275904 / 19017728, "6ba6fd188ae6"),
+}
+KERNEL_SOURCE = {"term_kernel_f64": "et_kernels.cu", "term2_kernel": "et_fused.cu",
+                 "term_quad_kernel": "et_quad.cu", "term_kernel_df64": "et_df64.cu",
+                 "term2_quad_kernel": "et_quadpair.cu", "batch_term2_quad_kernel": "et_quadpair.cu"}
+
+
+def source_sha(kernel):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2402_02273_gb300", "csrc", KERNEL_SOURCE.get(kernel, ""))
+    if not os.path.isfile(path):
+        return None
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+
+
+def term_traffic(prec, kernel, grid, voxels):
+    """Steady-state DRAM bytes of one launch over `voxels` voxels, or None (no
+    capture of this kernel as it stands at this size)."""
+    entry = TERM_TRAFFIC.get((prec, kernel, grid))
+    if not entry or entry[1] != source_sha(kernel):
+        return None
+    return entry[0] * voxels
 
 
 def term_kernel_of(prec, single_terms, n):
     """The kernel that runs the Taylor terms of a single grid (the library's
-    default choice): FP64 one term per launch; DF64 two per launch; FP32 one
-    per launch on the four-voxel kernel while its chain's fields (32 B per
-    voxel) stay within 1.4 L2 sizes, else two per launch.  --single-terms: one
-    everywhere."""
+    default choice): FP64 one term per launch; DF64 two per launch (TMA-fed);
+    FP32 one per launch on the four-voxel kernel while the Horner chain's
+    fields (28 B per voxel) stay within 0.75 L2 sizes, else two per launch on
+    the four-voxel two-term kernel.  --single-terms: one everywhere."""
     if prec == "f64":
         return "term_kernel_f64", False
     if prec == "df64":
         return ("term_kernel_df64", False) if single_terms else ("term2_kernel", True)
-    if single_terms or 32.0 * n <= 1.4 * L2_BYTES:
+    if single_terms or 28.0 * n <= 0.75 * L2_BYTES:
         return "term_quad_kernel", False
-    return "term2_kernel", True
+    return "term2_quad_kernel", True
 L2_FLUSH_BYTES = 256 << 20
 ADJ_STEPS = 50  # the adjoint workload: 128^3, 50 steps, checkpoints every 10
 ADJ_CK = 10
@@ -109,6 +141,9 @@ def parse():
     ap.add_argument("--batch-forms", default="f64,df64,f32")
     ap.add_argument("--forms", default="f64,df64,f32",
                     help="comma-separated precision forms to time (the first one is the headline)")
+    ap.add_argument("--large-grid", type=int, default=192,
+                    help="edge of the grid beyond the L2 on which the FP32 / DF64 forms are also timed (0: skip)")
+    ap.add_argument("--large-forms", default="f32,df64")
     return ap.parse_args()
 
 
@@ -232,6 +267,15 @@ def cpu_baseline(D, u0, seconds=12.0, extra_seconds=6.0):
             "variants": variants}
 
 
+def run_config(args, world, precision):
+    """The workload as both arms state it (the same keys and values)."""
+    return {"workload": WORKLOAD, "grid": [args.grid] * 3, "steps_per_run": args.nsteps, "tau_days": TAU,
+            "operator": "conservative", "scheme": "rosenbrock", "precision": precision,
+            "l2": "GPU arm: 256 MiB buffer written between bench steps (inside the timed region); "
+                  "CPU arm: not applicable",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -254,8 +298,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [args.grid] * 3, "tau_days": TAU,
-                   "step": "one time step of the run per bench step (sample of the 100-step run)"},
+        "config": run_config(args, world, "f64"),
+        "sample": "one time step of the 100-step run per bench step",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                          "sample": f"time steps {args.warmup + 1}..{args.warmup + args.steps} of the "
                                    f"{args.grid}^3 run, one per bench step"},
@@ -266,24 +310,24 @@ def run_reference(args):
 
 
 L2_BYTES = 129e6  # GB300 L2
+# bytes of one value of each form; a term chain works on three weight fields,
+# the diagonal, b and two term vectors (Horner sub-step), plus two running-sum
+# vectors when there are later sub-steps
+VALUE_BYTES = {"f64": 8, "df64": 8, "f32": 4}
+# a chain counts as L2-resident when its fields fit in half the L2: the L2 is
+# two partitions, one per die, and lines read from both dies are held in both
+L2_RESIDENT_BYTES = L2_BYTES / 2
 
 
-def l2_copy_gbs(torch, stream, nbytes=32 << 20, reps=200):
-    """Copy bandwidth of a buffer pair that stays in L2 (read + write bytes per
-    second, CUDA events): the denominator for kernels whose working set is
+def l2_peak_gbs(et, stream):
+    """Best streaming bandwidth (read + write bytes per second) of the
+    library's probe with every buffer in the L2 (working sets of 24 to 56 MB,
+    under half the L2): a copy, and six inputs to one output, the read/write
+    mix of a stencil term.  The denominator for kernels whose working set is
     L2-resident, beside the HBM copy peak."""
-    a = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
-    b = torch.empty_like(a)
-    with torch.cuda.stream(stream):
-        for _ in range(20):
-            b.copy_(a)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            b.copy_(a)
-        e1.record(stream)
-    e1.synchronize()
-    return 2.0 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    copy = max(et.probe_stream(mb << 20, 1, reps=100, stream=stream) for mb in (12, 16, 24, 28))
+    mix = max(et.probe_stream(mb << 20, 6, reps=100, stream=stream) for mb in (4, 6, 8))
+    return max(copy, mix), {"copy": copy, "six_in_one_out": mix}
 
 
 def measure_form(et, torch, D, u0, precision, args, stream, flush, timing=True):
@@ -344,7 +388,8 @@ def main():
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    l2_peak = l2_copy_gbs(torch, stream)
+    l2_peak, l2_probes = l2_peak_gbs(et, stream)
+    hbm_probe = et.probe_stream(1 << 30, 1, reps=5, stream=stream)  # this run's own HBM copy, for context
 
     def barrier():
         if world > 1:
@@ -371,52 +416,73 @@ def main():
         barrier()
         return ms, clocks
 
-    results = {}
-    forms = ["f64"] if args.no_forms else [f for f in args.forms.split(",") if f]
-    for prec in forms:
-        g, step_fn, info = measure_form(et, torch, D, u0, prec, args, stream, flush)
+    def time_form(Dg, ug, prec):
+        """K timed runs of one precision form on grid Dg from ug; a result dict."""
+        ng = Dg.size
+        edge = Dg.shape[0]
+        g, step_fn, info = measure_form(et, torch, Dg, ug, prec, args, stream, flush)
         ms, clocks = timed(step_fn)
         term_ms, term_launches, other_launches = g.timing()  # last run of the timed region
         rec = g.sync_info()
         avg_launch_ms = term_ms / max(term_launches, 1)
         s_, m_ = info["s"], info["m"]
-        kname, pairs = term_kernel_of(prec, args.single_terms, n)
+        kname, pairs = term_kernel_of(prec, args.single_terms, ng)
         nl, vb, vf = launch_mix(prec, s_, m_, pairs)
-        bytes_per_launch = vb / nl * n
-        flops_per_launch = vf / nl * n
+        bytes_per_launch = vb / nl * ng
+        flops_per_launch = vf / nl * ng
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
         achieved_tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
-        value = whole_job_rate(world, n, args.nsteps, ms)
+        value = whole_job_rate(world, ng, args.nsteps, ms)
         alu_peak = fp64_peak if prec == "f64" else fp32_peak
-        traffic = TERM_TRAFFIC.get((prec, kname)) if args.grid == N_GRID else None
+        traffic = term_traffic(prec, kname, edge, ng)
         alu_frac = achieved_tflops / alu_peak
         hbm_frac = achieved_gbs / hbm_peak
+        # the fields of the term chain (the weights, diagonal, b and the
+        # vectors) against the L2: where they fit, the chain runs from the L2
+        # and its bandwidth is set against the L2 copy peak of this run
+        chain_bytes = VALUE_BYTES[prec] * (7 if s_ == 1 else 9) * ng
+        l2_resident = chain_bytes < L2_RESIDENT_BYTES
         if prec == "f64" and alu_frac >= hbm_frac:
             roof = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": alu_frac, "traffic": traffic,
                     "peak_source": "measured FP64 FMA rate (et_probe_alu, this run)"}
+        elif l2_resident:
+            roof = {"bound": "l2", "achieved": achieved_gbs, "peak": l2_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / l2_peak, "traffic": traffic,
+                    "peak_source": "measured L2-resident streaming probe (et_probe_stream, this run)"}
         else:
             roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_frac, "traffic": traffic, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"}
-        # the fields one term launch touches against the L2: where they fit, the
-        # chain runs largely from L2 (the HBM fraction can then exceed 1), and
-        # its bandwidth is also set against an L2-resident copy
-        if bytes_per_launch < L2_BYTES:
-            roof.update({"l2_resident": True, "l2_copy_gbs": l2_peak, "l2_frac": achieved_gbs / l2_peak})
-        roof.update({"kernel": kname + (" (two terms per launch)" if pairs else ""), "avg_launch_us": avg_launch_ms * 1e3,
-                     "launches_per_run": term_launches, "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "algorithmic_flops_per_launch": flops_per_launch,
+        roof.update({"kernel": kname + (" (two terms per launch)" if pairs else ""),
+                     "avg_launch_us": avg_launch_ms * 1e3, "launches_per_run": term_launches,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "algorithmic_flops_per_launch": flops_per_launch, "chain_field_bytes": chain_bytes,
+                     "l2_resident": l2_resident, "l2_peak_gbs": l2_peak, "l2_frac": achieved_gbs / l2_peak,
                      "hbm_frac": hbm_frac, "hbm_achieved_gbs": achieved_gbs, "alu_frac": alu_frac})
         # stencil applications per time step: the residual and s m - 1 Taylor terms
         matvecs = s_ * m_
         roof["matvecs_per_step"] = matvecs
-        roof["gvoxel_matvecs_per_s"] = n * matvecs * args.nsteps / (ms * 1e-3) / 1e9
-        results[prec] = {"value": value, "ms_per_step": ms, "clocks": clocks, "roofline": roof,
-                         "launches_per_run": term_launches + other_launches, "info": info,
-                         "final_mass": rec["mass"], "final_umax": rec["umax"]}
+        roof["gvoxel_matvecs_per_s"] = ng * matvecs * args.nsteps / (ms * 1e-3) / 1e9
         g.enable_timing(False)
         del g
         torch.cuda.empty_cache()
+        return {"value": value, "ms_per_step": ms, "clocks": clocks, "roofline": roof,
+                "launches_per_run": term_launches + other_launches, "info": info,
+                "final_mass": rec["mass"], "final_umax": rec["umax"], "grid": [edge] * 3}
+
+    results = {}
+    forms = ["f64"] if args.no_forms else [f for f in args.forms.split(",") if f]
+    for prec in forms:
+        results[prec] = time_form(D, u0, prec)
+
+    # the FP32 and DF64 forms on a grid whose chain is far beyond the L2, where
+    # the HBM fraction applies (the same phantom type and run, larger grid)
+    large = {}
+    if args.large_grid and not args.no_forms:
+        Dl, ul = phantom.case(args.large_grid, seed=rank, noise=NOISE)
+        for prec in [f for f in args.large_forms.split(",") if f]:
+            large[prec] = time_form(Dl, ul, prec)
+        del Dl, ul
 
     # adjoint form: one gradient = forward run of ADJ_STEPS steps keeping
     # checkpoints every ADJ_CK steps + the reverse pass from them (the misfit
@@ -505,8 +571,15 @@ def main():
                 per_term = HORNER_BYTES[prec] / (2.0 if pairs else 1.0)
                 ach = per_term * nb / (t_us * 1e-6) / 1e9
                 broof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
-            broof.update({"kernel": "batched " + ("two-term" if pairs else "one-term") + " launch (first, all grids)",
-                          "us_per_term": t_us, "traffic": None})
+            if not pairs:
+                bkernel = "batch_term_kernel"
+            else:
+                bkernel = "batch_term2_quad_kernel" if prec == "f32" else "batch_term2_kernel"
+            broof.update({"kernel": bkernel + (" (two terms per launch" if pairs else " (one term per launch")
+                          + ", first launch of every grid)", "us_per_term": t_us,
+                          "traffic": term_traffic(prec, bkernel, "batch", nb),
+                          "algorithmic_bytes_per_launch": HORNER_BYTES[prec] * nb,
+                          "launch_us": t_us * (2.0 if pairs else 1.0)})
             batch[prec] = {"value": whole_job_rate(world, nb, args.nsteps, ms), "unit": UNIT,
                            "ms_per_run": ms, "voxels": nb, "grids": len(shapes), "steps": args.nsteps,
                            "setup_ms": setup_ms, "variant": variant, "two_terms_per_launch": pairs,
@@ -560,12 +633,9 @@ def main():
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [args.grid] * 3, "steps_per_run": args.nsteps,
-                       "tau_days": TAU, "operator": "conservative", "scheme": "rosenbrock",
-                       "precision": head, "s": r["info"]["s"], "m": r["info"]["m"],
-                       "theta": r["info"]["theta"], "tol": 1e-7 if head == "f32" else 1e-13, "setup_ms": r["info"]["setup_ms"],
-                       "l2": "256 MiB buffer written between bench steps (inside the timed region)",
-                       "parallelism": f"replicas x{world}"},
+            "config": run_config(args, world, head),
+            "schedule": {"s": r["info"]["s"], "m": r["info"]["m"], "theta": r["info"]["theta"],
+                         "tol": 1e-7 if head == "f32" else 1e-13, "setup_ms": r["info"]["setup_ms"]},
             "roofline": r["roofline"],
             "clocks": r["clocks"],
             "gpu_launches": args.steps * r["launches_per_run"],
@@ -578,6 +648,12 @@ def main():
                           "dtype": p, "s": results[p]["info"]["s"], "m": results[p]["info"]["m"],
                           "roofline": results[p]["roofline"], "clocks": results[p]["clocks"]}
                       for p in results},
+            "forms_large_grid": {p: {"value": large[p]["value"], "ms_per_step": large[p]["ms_per_step"],
+                                     "grid": large[p]["grid"], "dtype": p, "s": large[p]["info"]["s"],
+                                     "m": large[p]["info"]["m"], "roofline": large[p]["roofline"],
+                                     "clocks": large[p]["clocks"]}
+                                 for p in large},
+            "stream_probe_gbs": {"l2": l2_peak, "l2_probes": l2_probes, "hbm_copy_1gib": hbm_probe},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

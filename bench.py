@@ -586,6 +586,14 @@ def main():
                            "autotune_us_per_term": tune_us,
                            "s_range": [min(s_list), max(s_list)], "m_range": [min(m_list), max(m_list)],
                            "roofline": broof, "term_gbs_whole_run": gbs, "term_hbm_frac_whole_run": gbs / hbm_peak,
+                           # stencil applications (residual + s m - 1 terms) per step over all grids,
+                           # and their rate over the whole run: the batch's own schedules differ
+                           # from the single grid's (m from its rho and D scale)
+                           "matvecs_per_voxel_step": sum(n_i * s_i * m_i for n_i, s_i, m_i
+                                                         in zip(sizes, s_list, m_list)) / nb,
+                           "gvoxel_matvecs_per_s": sum(n_i * s_i * m_i for n_i, s_i, m_i
+                                                       in zip(sizes, s_list, m_list)) * args.nsteps
+                                                   / (ms * 1e-3) / 1e9,
                            # per step: residual, the longest chain's launches, stats
                            "launches_per_run": args.nsteps * (max(launch_mix(prec, si, mi, pairs)[0]
                                                                   for si, mi in zip(s_list, m_list)) + 2),

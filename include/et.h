@@ -131,6 +131,10 @@ typedef struct {
 #define ET_FLAG_D_INVALID 4u /* D < 0 or not finite (et_set_coeffs) */
 #define ET_FLAG_TIMEOUT   8u /* a bounded device-side wait ran out (a TMA load
                                 that never completed); the step is not valid */
+#define ET_FLAG_TRUNCATION 16u /* the a-posteriori truncation estimate of a step
+                                exceeded options.tol (see et_get_truncation);
+                                informational: synchronising calls report it in
+                                the record's flags, not as an error status */
 
 /* Bytes of device workspace a grid of this size needs (256-byte aligned
  * start required).  Returns 0 for non-positive sizes. */
@@ -215,6 +219,21 @@ ET_API et_status et_set_stream(et_grid* g, void* cuda_stream);
 ET_API et_status et_enable_timing(et_grid* g, int enable);
 ET_API et_status et_get_timing(et_grid* g, double* term_ms, long long* term_launches,
                         long long* other_launches);
+
+/* A-posteriori truncation estimate of the latest step (Sec. 2.2: the Taylor
+ * series of the step is cut after m terms in each of s sub-steps).  Every
+ * warp of a step's residual launch writes max|b| and max|u^n| of its voxels
+ * (warp shuffles); the stats launch that ends the step reduces them with its
+ * pass over u and evaluates
+ *     est = C(s, m) max|b| / max|u^n|,
+ *     C = tau e^{2 tau rho'} theta^m / m! (1 + tau nu / (m + 1)) / (1 - theta / (m + 1))
+ * (the remainder bound behind et_select_schedule with the measured max|b| in
+ * place of its a-priori bound (2 rmax + rho') max|u|; infinite if
+ * theta >= m + 1) and raises ET_FLAG_TRUNCATION in the step's record when est
+ * exceeds options.tol.  With the library's own schedules est <= tol whenever
+ * u^n lies in [0, 1]; forced (s, m) can exceed it.  Synchronises the stream
+ * and copies the latest step's estimate (relative to max|u^n|) to *estimate. */
+ET_API et_status et_get_truncation(et_grid* g, double* estimate);
 
 /* Grid facts: n voxels, bytes of the workspace actually used, and the
  * diffusion bound rmax (0 before et_set_coeffs). */

@@ -28,7 +28,7 @@ ET_OK, ET_ERR_ARG, ET_ERR_STATE, ET_ERR_CUDA, ET_ERR_NUMERIC, ET_ERR_TIMEOUT, ET
 ET_F64, ET_F32, ET_DF64 = 0, 1, 2
 ET_OP_CONSERVATIVE, ET_OP_LITERAL = 0, 1
 ET_SCHEME_ROSENBROCK, ET_SCHEME_EXPEULER = 0, 1
-ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID, ET_FLAG_TIMEOUT = 1, 2, 4, 8
+ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID, ET_FLAG_TIMEOUT, ET_FLAG_TRUNCATION = 1, 2, 4, 8, 16
 
 PRECISIONS = {"f64": ET_F64, "f32": ET_F32, "df64": ET_DF64}
 OPS = {"conservative": ET_OP_CONSERVATIVE, "literal": ET_OP_LITERAL}
@@ -97,6 +97,7 @@ _SIGS = {
     "et_step_static": ([_I, _I, _I, _D, _VP, _D, _I, _I, _VP, _D, _VP, ctypes.c_char_p, ctypes.c_size_t], _I),
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+    "et_get_truncation": ([_VP, ctypes.POINTER(_D)], _I),
     "et_probe_stream": ([_VP, _VP, ctypes.c_size_t, _I, _I, _VP, ctypes.POINTER(_D)], _I),
 }
 
@@ -278,6 +279,12 @@ class Grid:
         self._chk(self.lib.et_get_schedule(self.handle, float(tau), ctypes.byref(s), ctypes.byref(m),
                                            ctypes.byref(mu), ctypes.byref(th)))
         return s.value, m.value, mu.value, th.value
+
+    def truncation(self):
+        """A-posteriori truncation estimate of the latest step (relative to max|u^n|)."""
+        est = _D()
+        self._chk(self.lib.et_get_truncation(self.handle, ctypes.byref(est)))
+        return est.value
 
     def rmax(self):
         n, ws, r = ctypes.c_longlong(), ctypes.c_size_t(), _D()

@@ -39,13 +39,15 @@ struct Layout {
     size_t vec[6];    // b, dt, Y0, Y1, Z0, Z1 in the kernels' value type
     size_t stage;     // n doubles for host transfers
     size_t ushadow;   // F32, DF64: the pair of each u, read by the pair-arithmetic residual
-    size_t partial;   // 3 * nblocks doubles
+    size_t partial;   // 3 * kStatsBlocks doubles
+    size_t wnorm;     // 2 * kBlockY * nblocks: the residual warps' max |b|, max |u^n|
+    size_t npartial;  // 2 * kStatsBlocks doubles: the stats blocks' maxima of those
     size_t misc;      // counters, flags, info slots
     size_t total;
     unsigned nblocks;
 };
 
-constexpr size_t kMiscBytes = 1024;
+constexpr size_t kMiscBytes = 2048;  // counters, flags, info slot; the truncation estimate at 1024
 
 bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     if (nx <= 0 || ny <= 0 || nz <= 0) return false;
@@ -71,6 +73,8 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     L->stage = take(8ull * n);
     L->ushadow = prec != ET_F64 ? take(8ull * n) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks);
+    L->wnorm = take(2ull * 8ull * kBlockY * nb);
+    L->npartial = take(2ull * 8ull * kStatsBlocks);
     L->misc = take(kMiscBytes);
     L->total = off;
     return true;
@@ -170,6 +174,9 @@ struct et_grid {
     unsigned* ticket;
     unsigned* step_counter;
     et_step_info* info_slot;
+    unsigned long long* wnorm;  // residual warps' norm slots of the truncation estimate
+    double* npartial;           // the stats blocks' maxima of those
+    double* trunc_est;          // the latest step's estimate
     // model state
     bool coeffs_set;
     et_operator op;
@@ -432,9 +439,9 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
 // b and the shifted diagonal of the F32 / DF64 forms from the pair copy ush of u.
 template <typename T>
 cudaError_t enqueue_pair_residual(et_grid* g, const float2* ush, const Buffers<T>& B, double dt_shift,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, unsigned long long* wnorm = nullptr) {
     const PairResidualArgs R = pair_residual_args(ush, g->wres, g->nu, g->rho, dt_shift, g->scheme);
-    return launch_residual_df64<T>(g->G, g->op, R, g->scheme, const_cast<T*>(B.b), B.dt, g->flags, st);
+    return launch_residual_df64<T>(g->G, g->op, R, g->scheme, const_cast<T*>(B.b), B.dt, g->flags, st, wnorm);
 }
 
 template <typename T>
@@ -446,12 +453,12 @@ et_status enqueue_form(et_grid* g, double* u, const Schedule& S, double hstep, d
     if constexpr (!std::is_same<T, double>::value) {
         // F32, DF64: the residual in pair arithmetic from the pair copy of u, on
         // the FP32 pipes (the FP64 residual is bound by GB300's FP64 rate)
-        e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st);
+        e = enqueue_pair_residual<T>(g, g->ush, B, dt_shift, st, g->wnorm);
     } else {
         Weights<double> W64;
         for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
         e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
-                               g->flags, st);
+                               g->flags, st, g->wnorm);
     }
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "residual launch: %s", cudaGetErrorString(e));
     ++*other_launches;
@@ -476,6 +483,13 @@ et_status enqueue_step(et_grid* g, double* u, double tau, const Schedule& S, et_
     sink.s = S.s;
     sink.m = S.m;
     sink.ush = g->ush;
+    sink.wnorm = g->wnorm;
+    sink.nwarps = (long long)g->G.nblocks * kBlockY;
+    sink.npartial = g->npartial;
+    sink.trunc_c = truncation_factor(tau, g->rmax, g->rho, g->scheme, g->prec, g->opt_set ? &g->opt : nullptr, S.s,
+                                     S.m);
+    sink.trunc_tol = resolve(g->opt_set ? &g->opt : nullptr, g->prec).tol;
+    sink.trunc_est = g->trunc_est;
     const double hstep = tau / S.s;
     const double dt_shift = (g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0) - S.mu;
     const unsigned evflags = external_events ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -948,6 +962,32 @@ et_status adjoint_setup(et_grid* g, double tau, int nsteps, int checkpoint_every
 
 }  // namespace
 
+namespace et {
+
+// The factor C of the a-posteriori truncation estimate C max|b| / max|u^n| of
+// a step with s sub-steps of degree m: the remainder bound that
+// et_select_schedule holds below tol, tau e^{2 tau rho'} theta^m / m!
+// (1 + tau nu / (m + 1)) / (1 - theta / (m + 1)), without the a-priori bound
+// (2 rmax + rho') max|u| on max|b| (which the device measures instead).
+// Infinite where theta >= m + 1 (the bound does not converge).
+double truncation_factor(double tau, double rmax, double rho, et_scheme scheme, et_precision precision,
+                         const et_options* options, int s, int m) {
+    const ResolvedOptions o = resolve(options, precision);
+    const double rho_c = (scheme == ET_SCHEME_ROSENBROCK) ? rho * (1.0 + 2.0 * kRangeSlack) : 0.0;
+    const double nu = o.shift ? rmax + rho_c : 2.0 * rmax + rho_c;
+    const double beta = tau * nu;
+    const double theta = beta / s;
+    if (theta == 0.0) return 0.0;
+    if (theta >= m + 1) return INFINITY;
+    const double logc = std::log(tau) + 2.0 * tau * rho_c + m * std::log(theta) - std::lgamma(m + 1.0) +
+                        std::log1p(beta / (m + 1)) - std::log1p(-theta / (m + 1));
+    return std::exp(logc);
+}
+
+double resolved_tol(const et_options* options, et_precision precision) { return resolve(options, precision).tol; }
+
+}  // namespace et
+
 extern "C" {
 
 int et_version(void) { return ET_VERSION; }
@@ -1092,6 +1132,9 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->ticket = (unsigned*)(misc + 12);
     g->step_counter = (unsigned*)(misc + 16);
     g->info_slot = (et_step_info*)(misc + 64);
+    g->wnorm = (unsigned long long*)(g->ws + L.wnorm);
+    g->npartial = (double*)(g->ws + L.npartial);
+    g->trunc_est = (double*)(misc + 1024);
     g->coeffs_set = false;
     g->rmax = 0.0;
     g->nu = 1.0;
@@ -1177,6 +1220,17 @@ et_status et_sync_info(et_grid* g, et_step_info* host_out) {
     if (flags & ET_FLAG_NONFINITE) return fail(g, ET_ERR_NUMERIC, "non-finite density met");
     if (flags & ET_FLAG_RANGE_IN)
         return fail(g, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3): the step bound does not hold");
+    return ET_OK;
+}
+
+et_status et_get_truncation(et_grid* g, double* estimate) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!estimate) return fail(g, ET_ERR_ARG, "estimate must not be NULL");
+    DeviceGuard dg(g->device);
+    double est = 0.0;
+    ET_CUDA(g, cudaMemcpyAsync(&est, g->trunc_est, sizeof(est), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaStreamSynchronize(g->stream));
+    *estimate = est;
     return ET_OK;
 }
 

@@ -34,8 +34,10 @@ thread_local char g_batch_error[512] = "";
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 size_t value_bytes(et_precision prec) { return prec == ET_F32 ? 4 : 8; }
-// flags, per-grid rmax bits, tickets and step counters, per-grid step records
-size_t misc_bytes(int count) { return 128ull * count + 1024; }
+// flags, per-grid rmax bits, tickets and step counters, per-grid step records,
+// then per grid the truncation estimate
+size_t misc_head_bytes(int count) { return 128ull * count + 1024; }
+size_t misc_bytes(int count) { return misc_head_bytes(count) + 64ull * count; }
 
 size_t term_desc_bytes(et_precision prec) {
     return prec == ET_F64 ? sizeof(BatchTerm<double>)
@@ -58,14 +60,17 @@ size_t desc_bytes_per_instance(et_precision prec) {
 
 struct BatchLayout {
     // wpair: F32 pair weights of the residual; ush: F32 / DF64 pair copy of u
-    size_t w[5], wt[5], wpair[5], vec[6], stage, ush, partial, desc, tune_desc, misc;
+    // wnorm: the residual warps' norm slots (2 per warp, 8 warps per residual
+    // tile of every grid); npartial: per grid the stats blocks' maxima of them
+    size_t w[5], wt[5], wpair[5], vec[6], stage, ush, partial, wnorm, npartial, desc, tune_desc, misc;
     size_t total;
     long long ntot;
+    long long res_tiles;  // 32 x 8 residual tiles of all grids
 };
 
 bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L, std::vector<long long>* offs) {
     if (count < 1 || count > kMaxBatch || !dims) return false;
-    long long ntot = 0;
+    long long ntot = 0, res_tiles = 0;
     offs->assign(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
@@ -73,7 +78,9 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
         const long long n = (long long)nx * ny * nz;
         (*offs)[i] = ntot;
         ntot += n;
+        res_tiles += (long long)((nx + kBlockX - 1) / kBlockX) * ((ny + kBlockY - 1) / kBlockY) * nz;
     }
+    L->res_tiles = res_tiles;
     (*offs)[count] = ntot;
     if (ntot >= (1ll << 40)) return false;
     L->ntot = ntot;
@@ -91,6 +98,8 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
     L->stage = take(8ull * ntot);
     L->ush = (prec != ET_F64) ? take(8ull * ntot) : SIZE_MAX;
     L->partial = take(3ull * 8ull * kStatsBlocks * count);
+    L->wnorm = take(2ull * 8ull * kBlockY * (unsigned long long)L->res_tiles);
+    L->npartial = take(2ull * 8ull * kStatsBlocks * count);
     L->desc = take(desc_bytes_per_instance(prec) * count);
     L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec) + qpair_desc_bytes(prec)) * count + 256);
     L->misc = take(misc_bytes(count));
@@ -196,6 +205,7 @@ long long tiles_of(const Geom& G, int tz) {
 char* misc(et_batch* b) { return b->ws + b->L.misc; }
 unsigned* flags_of(et_batch* b) { return (unsigned*)(misc(b) + 0); }
 unsigned long long* rmax_bits_of(et_batch* b, int i) { return (unsigned long long*)(misc(b) + 64 + 8ull * i); }
+double* trunc_est_of(et_batch* b, int i) { return (double*)(misc(b) + misc_head_bytes(b->count) + 64ull * i); }
 unsigned* ticket_of(et_batch* b, int i) { return (unsigned*)(misc(b) + 64 + 8ull * b->count + 8ull * i); }
 unsigned* counter_of(et_batch* b, int i) { return ticket_of(b, i) + 1; }
 et_step_info* slot_of(et_batch* b, int i) {
@@ -274,6 +284,7 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         }
         r.b = field<T>(b, b->L.vec[0], i);
         r.dt = field<T>(b, b->L.vec[1], i);
+        r.wnorm = tuning ? nullptr : (unsigned long long*)(b->ws + b->L.wnorm);
         r.tile_begin = rt;
         rt += tiles_of(r.G, 1);
     }
@@ -370,6 +381,13 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         sk.s = S[i].s;
         sk.m = S[i].m;
         sk.ush = b->prec != ET_F64 ? field<float2>(b, b->L.ush, i) : nullptr;
+        sk.wnorm = tuning ? nullptr : (unsigned long long*)(b->ws + b->L.wnorm) + 2ll * kBlockY * res[i].tile_begin;
+        sk.nwarps = (long long)kBlockY * tiles_of(res[i].G, 1);
+        sk.npartial = (double*)(b->ws + b->L.npartial) + 2ull * kStatsBlocks * i;
+        sk.trunc_c = truncation_factor(tau, b->rmax[i], b->rho[i], b->scheme, b->prec, b->opt_set ? &b->opt : nullptr,
+                                       S[i].s, S[i].m);
+        sk.trunc_tol = resolved_tol(b->opt_set ? &b->opt : nullptr, b->prec);
+        sk.trunc_est = trunc_est_of(b, i);
     }
     // [residual x C][stats x C][single terms][pad to 64 bytes][two-term]
     // [pad][four-voxel two-term]

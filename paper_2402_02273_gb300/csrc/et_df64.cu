@@ -207,32 +207,37 @@ int df64_blocks_per_sm() {
 template <int OP, typename TO>
 __global__ void __launch_bounds__(kThreads)
 residual_df64_kernel(const __grid_constant__ Geom G, const __grid_constant__ PairResidualArgs R, int scheme,
-                     TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags) {
+                     TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags, unsigned long long* wnorm) {
     pdl_begin();  // launched by launch_pdl
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    residual_pair_point<OP, TO>(G, R, scheme, b, dt, flags, i, j, blockIdx.z);
+    float babs = 0.f, uabs = 0.f;
+    if (i < G.nx && j < G.ny) residual_pair_point<OP, TO>(G, R, scheme, b, dt, flags, i, j, blockIdx.z, &babs, &uabs);
+    // one warp per row of the 32 x 8 block
+    if (wnorm)
+        warp_norms(babs, uabs,
+                   wnorm + 2 * ((blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)) * kBlockY +
+                                threadIdx.y));
 }
 
 }  // namespace
 
 template <typename TO>
 cudaError_t launch_residual_df64(const Geom& G, et_operator op, const PairResidualArgs& R, et_scheme scheme, TO* b,
-                                 TO* dt, unsigned* flags, cudaStream_t stream) {
+                                 TO* dt, unsigned* flags, cudaStream_t stream, unsigned long long* wnorm) {
     const dim3 block(kBlockX, kBlockY, 1);
     const dim3 grid((G.nx + kBlockX - 1) / kBlockX, (G.ny + kBlockY - 1) / kBlockY, G.nz);
     if (op == ET_OP_CONSERVATIVE)
         return launch_pdl(residual_df64_kernel<ET_OP_CONSERVATIVE, TO>, grid, block, stream, G, R, (int)scheme, b,
-                          dt, flags);
+                          dt, flags, wnorm);
     return launch_pdl(residual_df64_kernel<ET_OP_LITERAL, TO>, grid, block, stream, G, R, (int)scheme, b, dt,
-                      flags);
+                      flags, wnorm);
 }
 
 template cudaError_t launch_residual_df64<float2>(const Geom&, et_operator, const PairResidualArgs&, et_scheme,
-                                                  float2*, float2*, unsigned*, cudaStream_t);
+                                                  float2*, float2*, unsigned*, cudaStream_t, unsigned long long*);
 template cudaError_t launch_residual_df64<float>(const Geom&, et_operator, const PairResidualArgs&, et_scheme, float*,
-                                                 float*, unsigned*, cudaStream_t);
+                                                 float*, unsigned*, cudaStream_t, unsigned long long*);
 
 cudaError_t prime_launch_limits_df64() {
     df64_blocks_per_sm<ET_OP_CONSERVATIVE>();

@@ -77,6 +77,10 @@ struct Geom {
 // counter for the last-block reduction, the step index and the flag word.
 constexpr int kStatsBlocks = 608;  // 4 per SM; fixed, so the summation order is fixed
 constexpr int kStatsThreads = 256;
+// Norms of a step for its a-posteriori truncation estimate: every warp of the
+// residual launch writes max |b| and max |u^n| of its voxels (bit patterns of
+// non-negative doubles) to its own slot; the stats launch that ends the step
+// reduces the slots with its pass over u (two more partials a block).
 struct StatsSink {
     double* partial;        // 3 * kStatsBlocks: sum, min key, max key
     unsigned* ticket;       // last-block counter, returns to 0 after each step
@@ -87,7 +91,46 @@ struct StatsSink {
     et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
     int s, m;               // recorded in the info
     float2* ush;            // F32 / DF64: receives the pair of each u (nullptr: none)
+    // truncation estimate (nullptr wnorm: none): est = trunc_c max|b| / max|u^n|,
+    // ET_FLAG_TRUNCATION when est > trunc_tol; est is stored to *trunc_est
+    const unsigned long long* wnorm = nullptr;  // [nwarps][2]: max |b|, max |u^n| of each residual warp
+    long long nwarps = 0;
+    double* npartial = nullptr;                 // 2 * kStatsBlocks: the blocks' maxima of the slots
+    double trunc_c = 0.0, trunc_tol = 0.0;
+    double* trunc_est = nullptr;
 };
+
+// Writes the maxima of |b| and |u| over the calling warp's lanes to the warp's
+// slot (lanes without a voxel pass 0).  Every lane of the warp must call it.
+// (the FP32 / DF64 residual passes the high parts as floats: their maxima are
+// taken on the float bits and widened once, off GB300's slow FP64 pipe)
+__device__ __forceinline__ void warp_norms(float babs, float uabs, unsigned long long* slot) {
+    unsigned kb = __float_as_uint(babs), ku = __float_as_uint(uabs);
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned ob = __shfl_down_sync(0xffffffffu, kb, off);
+        const unsigned ou = __shfl_down_sync(0xffffffffu, ku, off);
+        kb = ob > kb ? ob : kb;
+        ku = ou > ku ? ou : ku;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slot[0] = (unsigned long long)__double_as_longlong((double)__uint_as_float(kb));
+        slot[1] = (unsigned long long)__double_as_longlong((double)__uint_as_float(ku));
+    }
+}
+__device__ __forceinline__ void warp_norms(double babs, double uabs, unsigned long long* slot) {
+    unsigned long long kb = (unsigned long long)__double_as_longlong(babs);
+    unsigned long long ku = (unsigned long long)__double_as_longlong(uabs);
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, kb, off);
+        const unsigned long long ou = __shfl_down_sync(0xffffffffu, ku, off);
+        kb = ob > kb ? ob : kb;
+        ku = ou > ku ? ou : ku;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slot[0] = kb;
+        slot[1] = ku;
+    }
+}
 
 // Scalars of the kernels' value types: double (FP64), float (FP32) and
 // float2 = (hi, lo) double-float pairs (DF64, value hi + lo).
@@ -184,6 +227,7 @@ struct BatchResidual {
     PairResidualArgs P;
     T* b;
     T* dt;
+    unsigned long long* wnorm;  // the batch's warp norm slots, indexed by tile (nullptr: none)
     long long tile_begin;
 };
 
@@ -228,7 +272,7 @@ cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], floa
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W,
                             double rho, double dt_shift, double dt_scale, et_scheme scheme, T* b,
-                            T* dt, unsigned* flags, cudaStream_t stream);
+                            T* dt, unsigned* flags, cudaStream_t stream, unsigned long long* wnorm = nullptr);
 // FP32 term with four voxels per thread (et_quad.cu), the same arithmetic as
 // the one-voxel kernel; needs nx % 4 == 0 and 16-byte aligned fields.
 bool quad_eligible(const Geom& G, const Weights<float>& W, const TermArgs<float>& a);
@@ -353,10 +397,16 @@ inline PairResidualArgs pair_residual_args(const float2* ush, float2* const w[5]
 }
 template <typename TO>
 cudaError_t launch_residual_df64(const Geom& G, et_operator op, const PairResidualArgs& R, et_scheme scheme, TO* b,
-                                 TO* dt, unsigned* flags, cudaStream_t stream);
+                                 TO* dt, unsigned* flags, cudaStream_t stream, unsigned long long* wnorm = nullptr);
 // dst[p] = (float)(src[p] * scale)
 cudaError_t launch_cast(long long n, const double* src, double scale, float* dst, cudaStream_t stream);
 
+// Factor C of the a-posteriori truncation estimate C max|b| / max|u^n| of one
+// step with s sub-steps of degree m (et_api.cu).
+double truncation_factor(double tau, double rmax, double rho, et_scheme scheme, et_precision precision,
+                         const et_options* options, int s, int m);
+// The truncation tolerance the options resolve to (options.tol or the form's default).
+double resolved_tol(const et_options* options, et_precision precision);
 // Looks up launch limits (resident blocks per SM) before any stream capture.
 cudaError_t prime_launch_limits();
 cudaError_t prime_launch_limits_df64();

@@ -149,11 +149,12 @@ __device__ __forceinline__ T minus_weight(const Weights<T>& W, int axis, long lo
 // residual: b = L u + rho u (1 - u), diag = rho(1 - 2u) - R - mu (or -R - mu).
 // L u = sum_e w_e u_e - R u_p with R from the coefficient pass: 12 FP64
 // operations per voxel; the range test on u runs on the integer bits.
+// Returns |b| and |u| of the voxel in *babs, *uabs (the step's norms).
 template <int OP, typename T>
 __device__ __forceinline__ void residual_point(const Geom& G, const double* __restrict__ u, const Weights<double>& W,
                                                double rho, double dt_shift, double dt_scale, int scheme,
                                                T* __restrict__ b, T* __restrict__ dt, unsigned* flags, int i, int j,
-                                               int k) {
+                                               int k, double* babs, double* uabs) {
     const long long p = i + G.sy * j + G.sz * k;
     const double up = u[p];
     const double negR = W.w[4][p];
@@ -170,6 +171,8 @@ __device__ __forceinline__ void residual_point(const Geom& G, const double* __re
     else dp = negR + dt_shift;
     store_value(&b[p], bp);
     store_value(&dt[p], dp * dt_scale);
+    *babs = fabs(bp);
+    *uabs = fabs(up);
     const long long bits = __double_as_longlong(up);
     if (nonfinite_bits(bits)) atomicOr(flags, ET_FLAG_NONFINITE);
     if (scheme == ET_SCHEME_ROSENBROCK) {
@@ -184,12 +187,19 @@ __device__ __forceinline__ void residual_point(const Geom& G, const double* __re
 template <int OP, typename T>
 __global__ void __launch_bounds__(kThreads)
 residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double rho, double dt_shift,
-                double dt_scale, int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags) {
+                double dt_scale, int scheme, T* __restrict__ b, T* __restrict__ dt, unsigned* flags,
+                unsigned long long* wnorm) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
-    if (i >= G.nx || j >= G.ny) return;
-    residual_point<OP, T>(G, u, W, rho, dt_shift, dt_scale, scheme, b, dt, flags, i, j, k);
+    double babs = 0.0, uabs = 0.0;
+    if (i < G.nx && j < G.ny)
+        residual_point<OP, T>(G, u, W, rho, dt_shift, dt_scale, scheme, b, dt, flags, i, j, k, &babs, &uabs);
+    // one warp per row of the 32 x 8 block
+    if (wnorm)
+        warp_norms(babs, uabs,
+                   wnorm + 2 * ((blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)) * kBlockY +
+                                threadIdx.y));
 }
 
 // gamma * sum, rounded to the value type and widened, then added to u: the
@@ -344,13 +354,25 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
 __device__ __forceinline__ void stats_body(long long n, const double* __restrict__ u, const StatsSink& s, int blk) {
     constexpr int kWarps = kStatsThreads / 32;
     __shared__ double ssum[kWarps];
-    __shared__ unsigned long long smin[kWarps], smax[kWarps];
+    __shared__ unsigned long long smin[kWarps], smax[kWarps], snb[kWarps], snu[kWarps];
     __shared__ bool is_last;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     double sum = 0.0;
     unsigned long long kmin = ~0ull, kmax = 0ull;
     bool bad = false;
+    // the residual's warp norm slots of this step (read first, so their
+    // latency overlaps the pass over u)
+    unsigned long long nb = 0ull, nu = 0ull;
+    if (s.wnorm) {
+        for (long long q = blk * (long long)kStatsThreads + tid; q < s.nwarps;
+             q += (long long)kStatsBlocks * kStatsThreads) {
+            const unsigned long long b0 = __ldcg(&s.wnorm[2 * q + 0]);
+            const unsigned long long u0 = __ldcg(&s.wnorm[2 * q + 1]);
+            nb = b0 > nb ? b0 : nb;
+            nu = u0 > nu ? u0 : nu;
+        }
+    }
 #pragma unroll 4
     for (long long p = blk * (long long)kStatsThreads + tid; p < n; p += (long long)kStatsBlocks * kStatsThreads) {
         const double v = u[p];
@@ -366,13 +388,19 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
         sum += __shfl_down_sync(0xffffffffu, sum, off);
         const unsigned long long omin = __shfl_down_sync(0xffffffffu, kmin, off);
         const unsigned long long omax = __shfl_down_sync(0xffffffffu, kmax, off);
+        const unsigned long long onb = __shfl_down_sync(0xffffffffu, nb, off);
+        const unsigned long long onu = __shfl_down_sync(0xffffffffu, nu, off);
         kmin = omin < kmin ? omin : kmin;
         kmax = omax > kmax ? omax : kmax;
+        nb = onb > nb ? onb : nb;
+        nu = onu > nu ? onu : nu;
     }
     if (lane == 0) {
         ssum[warp] = sum;
         smin[warp] = kmin;
         smax[warp] = kmax;
+        snb[warp] = nb;
+        snu[warp] = nu;
     }
     __syncthreads();
     if (tid == 0) {
@@ -380,10 +408,16 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
             sum += ssum[w];
             kmin = smin[w] < kmin ? smin[w] : kmin;
             kmax = smax[w] > kmax ? smax[w] : kmax;
+            nb = snb[w] > nb ? snb[w] : nb;
+            nu = snu[w] > nu ? snu[w] : nu;
         }
         s.partial[3 * blk + 0] = sum;
         s.partial[3 * blk + 1] = __longlong_as_double((long long)kmin);
         s.partial[3 * blk + 2] = __longlong_as_double((long long)kmax);
+        if (s.wnorm) {
+            s.npartial[2 * blk + 0] = __longlong_as_double((long long)nb);
+            s.npartial[2 * blk + 1] = __longlong_as_double((long long)nu);
+        }
         __threadfence();
         const unsigned ticket = atomicAdd(s.ticket, 1u);
         is_last = (ticket == kStatsBlocks - 1);
@@ -401,18 +435,34 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
         kmin = a < kmin ? a : kmin;
         kmax = b > kmax ? b : kmax;
     }
+    nb = 0ull;
+    nu = 0ull;
+    if (s.wnorm) {
+        for (int q = tid; q < kStatsBlocks; q += kStatsThreads) {
+            const unsigned long long b0 = (unsigned long long)__double_as_longlong(__ldcg(&s.npartial[2 * q + 0]));
+            const unsigned long long u0 = (unsigned long long)__double_as_longlong(__ldcg(&s.npartial[2 * q + 1]));
+            nb = b0 > nb ? b0 : nb;
+            nu = u0 > nu ? u0 : nu;
+        }
+    }
     for (int off = 16; off > 0; off >>= 1) {
         sum += __shfl_down_sync(0xffffffffu, sum, off);
         const unsigned long long omin = __shfl_down_sync(0xffffffffu, kmin, off);
         const unsigned long long omax = __shfl_down_sync(0xffffffffu, kmax, off);
+        const unsigned long long onb = __shfl_down_sync(0xffffffffu, nb, off);
+        const unsigned long long onu = __shfl_down_sync(0xffffffffu, nu, off);
         kmin = omin < kmin ? omin : kmin;
         kmax = omax > kmax ? omax : kmax;
+        nb = onb > nb ? onb : nb;
+        nu = onu > nu ? onu : nu;
     }
     __syncthreads();
     if (lane == 0) {
         ssum[warp] = sum;
         smin[warp] = kmin;
         smax[warp] = kmax;
+        snb[warp] = nb;
+        snu[warp] = nu;
     }
     __syncthreads();
     if (tid == 0) {
@@ -420,6 +470,8 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
             sum += ssum[w];
             kmin = smin[w] < kmin ? smin[w] : kmin;
             kmax = smax[w] > kmax ? smax[w] : kmax;
+            nb = snb[w] > nb ? snb[w] : nb;
+            nu = snu[w] > nu ? snu[w] : nu;
         }
         const unsigned step = *s.step_counter;
         et_step_info rec;
@@ -428,6 +480,15 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
         rec.mass = sum;
         rec.s = s.s;
         rec.m = s.m;
+        if (s.wnorm) {
+            // a-posteriori truncation estimate of the step: the remainder bound
+            // of its (s, m) with the measured max |b| in place of its a-priori
+            // bound, relative to max |u^n|
+            const double bmax = __longlong_as_double((long long)nb), umax = __longlong_as_double((long long)nu);
+            const double est = umax > 0.0 ? s.trunc_c * bmax / umax : (bmax > 0.0 ? INFINITY : 0.0);
+            if (est > s.trunc_tol) atomicOr(s.flags, ET_FLAG_TRUNCATION);
+            if (s.trunc_est) *s.trunc_est = est;
+        }
         rec.flags = atomicOr(s.flags, 0u);
         rec.step = step;
         s.info[(size_t)step * (unsigned)s.info_stride] = rec;
@@ -483,11 +544,17 @@ batch_residual_kernel(const BatchResidual<T>* __restrict__ d, int count, int sch
     const long long rest = lt / tiles_x;
     const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
     const int k = (int)(rest / tiles_y);
-    if (i >= sd.G.nx || j >= sd.G.ny) return;
-    if constexpr (std::is_same<T, double>::value)
-        residual_point<OP, T>(sd.G, sd.u, sd.W, sd.rho, sd.dt_shift, sd.dt_scale, scheme, sd.b, sd.dt, flags, i, j, k);
-    else
-        residual_pair_point<OP, T>(sd.G, sd.P, scheme, sd.b, sd.dt, flags, i, j, k);
+    // |b| and |u| as doubles (FP64 form) or as the floats of their high parts
+    using NormT = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+    NormT babs = 0, uabs = 0;
+    if (i < sd.G.nx && j < sd.G.ny) {
+        if constexpr (std::is_same<T, double>::value)
+            residual_point<OP, T>(sd.G, sd.u, sd.W, sd.rho, sd.dt_shift, sd.dt_scale, scheme, sd.b, sd.dt, flags, i,
+                                  j, k, &babs, &uabs);
+        else
+            residual_pair_point<OP, T>(sd.G, sd.P, scheme, sd.b, sd.dt, flags, i, j, k, &babs, &uabs);
+    }
+    if (sd.wnorm) warp_norms(babs, uabs, sd.wnorm + 2 * (tile * kBlockY + threadIdx.y));
 }
 
 // FP64, one tile (32 x 8 x 1) per block.
@@ -617,14 +684,14 @@ cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], floa
 template <typename T>
 cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weights<double> W, double rho,
                             double dt_shift, double dt_scale, et_scheme scheme, T* b, T* dt, unsigned* flags,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, unsigned long long* wnorm) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
         residual_kernel<ET_OP_CONSERVATIVE, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags);
+            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags, wnorm);
     else
         residual_kernel<ET_OP_LITERAL, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags);
+            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags, wnorm);
     return cudaGetLastError();
 }
 
@@ -748,7 +815,7 @@ cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, 
 
 template cudaError_t launch_residual<double>(const Geom&, et_operator, const double*, Weights<double>,
                                              double, double, double, et_scheme, double*, double*, unsigned*,
-                                             cudaStream_t);
+                                             cudaStream_t, unsigned long long*);
 template cudaError_t launch_term<double>(const Geom&, et_operator, Weights<double>,
                                          const TermArgs<double>&, cudaStream_t);
 template cudaError_t launch_term<float>(const Geom&, et_operator, Weights<float>, const TermArgs<float>&,

@@ -23,10 +23,11 @@ namespace et {
 __device__ __forceinline__ void store_pair(float2* d, float2 v) { *d = v; }
 __device__ __forceinline__ void store_pair(float* d, float2 v) { *d = v.x; }
 
+// Returns |b| and |u| of the voxel (their high parts) in *babs, *uabs.
 template <int OP, typename TO>
 __device__ __forceinline__ void residual_pair_point(const Geom& G, const PairResidualArgs& R, int scheme,
                                                     TO* __restrict__ b, TO* __restrict__ dt, unsigned* flags, int i,
-                                                    int j, int k) {
+                                                    int j, int k, float* babs, float* uabs) {
     using namespace df64;
     const long long p = i + G.sy * j + G.sz * k;
     const float2* __restrict__ ush = R.ush;
@@ -43,8 +44,11 @@ __device__ __forceinline__ void residual_pair_point(const Geom& G, const PairRes
                                     W.w[2][p], (k + 1 < G.nz) ? ush[p + G.sz] : zero, wzm, zmk ? ush[p - G.sz] : zero,
                                     zero, false, zero, zero);
     const float2 one_minus_u = df_add(make_float2(1.f, 0.f), make_float2(-uc.x, -uc.y));
-    store_pair(&b[p], df_add(df_mul(R.nu, S), df_mul(R.rho, df_mul(uc, one_minus_u))));
+    const float2 bp = df_add(df_mul(R.nu, S), df_mul(R.rho, df_mul(uc, one_minus_u)));
+    store_pair(&b[p], bp);
     store_pair(&dt[p], df_add(w4, df_fma(R.k_u, uc, R.shift)));
+    *babs = fabsf(bp.x);
+    *uabs = fabsf(uc.x);
     const float uh = uc.x;
     if (!isfinite(uh)) atomicOr(flags, ET_FLAG_NONFINITE);
     if (scheme == ET_SCHEME_ROSENBROCK && (uh < (float)-kRangeSlack || uh > (float)(1.0 + kRangeSlack)))

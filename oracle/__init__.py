@@ -75,6 +75,7 @@ def _load():
             lib.oracle_apply_A.argtypes = [pp, dp, dp, dp]
             lib.oracle_apply_L.argtypes = [pp, dp, dp]
             lib.oracle_row_A.argtypes = [pp, dp, ctypes.c_long, dp]
+            lib.oracle_assemble_A.argtypes = [pp, dp, dp]
             lib.oracle_norm_inf_A.argtypes = [pp, dp]
             lib.oracle_norm_inf_A.restype = ctypes.c_double
             lib.oracle_residual.argtypes = [pp, dp, dp]
@@ -143,6 +144,14 @@ class Problem:
         un = self._vec(un)
         e = np.empty(7)
         self._lib.oracle_row_A(ctypes.byref(self._p), _dptr(un), int(p), _dptr(e))
+        return e
+
+    def rows_A(self, un):
+        """(n, 7) entries of A_n: diagonal, then the -x, +x, -y, +y, -z, +z
+        off-diagonals (0 where the neighbour lies outside the box)."""
+        un = self._vec(un)
+        e = np.empty((self.D.size, 7))
+        self._lib.oracle_assemble_A(ctypes.byref(self._p), _dptr(un), _dptr(e))
         return e
 
     def norm_inf_A(self, un):

@@ -138,6 +138,12 @@ void oracle_row_A(const oracle_problem* P, const double* un, long p, double e[7]
     e[0] = -offsum + c_at(P, un, p);
 }
 
+void oracle_assemble_A(const oracle_problem* P, const double* un, double* entries) {
+    const long n = nvox(P);
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < n; ++p) oracle_row_A(P, un, p, entries + 7 * p);
+}
+
 double oracle_norm_inf_A(const oracle_problem* P, const double* un) {
     const long n = nvox(P);
     const long sz = (long)P->nx * P->ny;

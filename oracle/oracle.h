@@ -58,6 +58,9 @@ void oracle_apply_L(const oracle_problem* P, const double* v, double* out);
 void oracle_row_A(const oracle_problem* P, const double* un, long p, double entries[7]);
 /* ||A||_inf from the row entries (Gershgorin row sums). */
 double oracle_norm_inf_A(const oracle_problem* P, const double* un);
+/* The rows of A_n for every voxel p, as oracle_row_A writes them, at
+ * entries[7 p .. 7 p + 6] (for assembling a sparse matrix). */
+void oracle_assemble_A(const oracle_problem* P, const double* un, double* entries);
 /* b = A u^n + f(u^n). */
 void oracle_residual(const oracle_problem* P, const double* un, double* b);
 /* x = tau * phi1(tau A) b through exp(tau B) v_1 (augmented matrix, s sub-steps). */

@@ -144,6 +144,8 @@ def parse():
     ap.add_argument("--large-grid", type=int, default=192,
                     help="edge of the grid beyond the L2 on which the FP32 / DF64 forms are also timed (0: skip)")
     ap.add_argument("--large-forms", default="f32,df64")
+    ap.add_argument("--no-cn", action="store_true", help="skip the Crank-Nicolson comparison line")
+    ap.add_argument("--cn-rtol", type=float, default=1e-12)
     return ap.parse_args()
 
 
@@ -605,6 +607,55 @@ def main():
         del Dcat, ucat0
         torch.cuda.empty_cache()
 
+    # Crank-Nicolson comparison (Sec. 2.3 / Table 2 of the paper): the same
+    # 128^3 run of 100 steps by Crank-Nicolson steps (FP64 conjugate gradients
+    # to a relative residual of --cn-rtol), and the time-discretisation error
+    # of both schemes at the end of the run against the exponential step at
+    # tau / 16 (untimed)
+    crank = None
+    if not args.no_cn and not args.no_forms:
+        g = et.Grid(D.shape, precision="f64", stream=stream)
+        g.set_coeffs(torch.from_numpy(D).to("cuda"), rho=RHO)
+        u0d = torch.from_numpy(u0).to("cuda")
+        u = torch.empty_like(u0d)
+        info = g.info_buffer(args.nsteps)
+
+        def cn_step():
+            u.copy_(u0d)
+            g.cn_run(u, TAU, args.nsteps, rtol=args.cn_rtol, info=info)
+            flush.add_(1)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                cn_step()
+        g.sync_info()
+        ms, clocks = timed(cn_step)
+        g.sync_info()
+        iters = g.decode_info(info)["m"]
+        u_cn = u.cpu().numpy()
+        # the exponential step's run and the fine reference, untimed
+        with torch.cuda.stream(stream):
+            v = u0d.clone()
+            g.run(v, TAU, args.nsteps)
+            ref = u0d.clone()
+            g.run(ref, TAU / 16, 16 * args.nsteps)
+        g.sync_info()
+        u_exp, u_ref = v.cpu().numpy(), ref.cpu().numpy()
+        scale = np.abs(u_ref).max()
+        value = whole_job_rate(world, n, args.nsteps, ms)
+        crank = {"value": value, "unit": UNIT, "ms_per_run": ms, "rtol": args.cn_rtol,
+                 "cg_iterations_per_step": [int(iters.min()), int(iters.max())],
+                 "cg_iteration_cap": g.cn_iteration_cap(TAU, args.cn_rtol),
+                 # stencil applications per step: the residual and one per iteration
+                 "gvoxel_matvecs_per_s": n * (float(iters.mean()) + 1) * args.nsteps / (ms * 1e-3) / 1e9,
+                 "exponential_value": results["f64"]["value"] if "f64" in results else None,
+                 "max_error_vs_tau16_reference": {"crank_nicolson": float(np.abs(u_cn - u_ref).max() / scale),
+                                                  "exponential": float(np.abs(u_exp - u_ref).max() / scale)},
+                 "clocks": clocks,
+                 "note": "FP64 both; errors at t = 730 d relative to max|u|, reference = exponential step, tau/16"}
+        del g
+        torch.cuda.empty_cache()
+
     # end to end through the public API with host buffers (pinned): H2D of D and
     # u0, coefficient setup, the 100-step run, D2H of u and of the last record
     e2e = None
@@ -662,6 +713,7 @@ def main():
                                      "clocks": large[p]["clocks"]}
                                  for p in large},
             "stream_probe_gbs": {"l2": l2_peak, "l2_probes": l2_probes, "hbm_copy_1gib": hbm_probe},
+            "crank_nicolson": crank,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

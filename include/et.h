@@ -135,6 +135,8 @@ typedef struct {
                                 exceeded options.tol (see et_get_truncation);
                                 informational: synchronising calls report it in
                                 the record's flags, not as an error status */
+#define ET_FLAG_CG_CAP    32u /* a Crank-Nicolson solve stopped at its iteration
+                                cap before reaching its tolerance */
 
 /* Bytes of device workspace a grid of this size needs (256-byte aligned
  * start required).  Returns 0 for non-positive sizes. */
@@ -219,6 +221,32 @@ ET_API et_status et_set_stream(et_grid* g, void* cuda_stream);
 ET_API et_status et_enable_timing(et_grid* g, int enable);
 ET_API et_status et_get_timing(et_grid* g, double* term_ms, long long* term_launches,
                         long long* other_launches);
+
+/* Crank-Nicolson steps (Sec. 2.3, the paper's comparison method), in place.
+ * The printed scheme is read as the trapezoidal rule on the same linearised
+ * system as the exponential step:
+ *     (I - tau/2 A_n) u^{n+1} = (I + tau/2 A_n) u^n + tau f_n,
+ * solved for delta = u^{n+1} - u^n from (I - tau/2 A_n) delta = tau b_n by
+ * matrix-free conjugate gradients in FP64, every scalar on the device, from
+ * delta = 0 until ||r||_2 <= rtol ||tau b_n||_2 or max_iter iterations
+ * (0: the a-priori cap of et_cn_iteration_cap).  A step that stops at the cap
+ * raises ET_FLAG_CG_CAP (ET_ERR_NUMERIC at the next synchronising call).  One
+ * step is captured as a CUDA graph (unless options.use_graph is -1) and
+ * replayed nsteps times; iterations past convergence are empty launches.
+ *  g       an ET_F64 grid with the conservative operator (the system is then
+ *          symmetric positive definite when tau rho < 2), else
+ *          ET_ERR_UNSUPPORTED; tau rho >= 2 in the folded scheme is ET_ERR_ARG.
+ *  u, info as for et_run; a step's record has s = 0 and m = its iterations.
+ *  rtol    in (0, 1).  Asynchronous.  Uses the grid's workspace (the
+ *          exponential step's vectors), so it does not run concurrently with
+ *          et_run on the same grid. */
+ET_API et_status et_cn_run(et_grid* g, double* u, double tau, int nsteps, double rtol, int max_iter,
+                           et_step_info* info);
+/* The iteration cap et_cn_run takes for max_iter = 0: from Gershgorin bounds
+ * on the spectrum of I - tau/2 A_n and the classical conjugate-gradient bound
+ * ||r_k|| <= 2 sqrt(kappa) ((sqrt(kappa) - 1)/(sqrt(kappa) + 1))^k ||r_0||, plus
+ * two.  0 for invalid arguments or before et_set_coeffs. */
+ET_API int et_cn_iteration_cap(const et_grid* g, double tau, double rtol);
 
 /* A-posteriori truncation estimate of the latest step (Sec. 2.2: the Taylor
  * series of the step is cut after m terms in each of s sub-steps).  Every

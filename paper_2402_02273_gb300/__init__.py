@@ -28,7 +28,8 @@ ET_OK, ET_ERR_ARG, ET_ERR_STATE, ET_ERR_CUDA, ET_ERR_NUMERIC, ET_ERR_TIMEOUT, ET
 ET_F64, ET_F32, ET_DF64 = 0, 1, 2
 ET_OP_CONSERVATIVE, ET_OP_LITERAL = 0, 1
 ET_SCHEME_ROSENBROCK, ET_SCHEME_EXPEULER = 0, 1
-ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID, ET_FLAG_TIMEOUT, ET_FLAG_TRUNCATION = 1, 2, 4, 8, 16
+ET_FLAG_NONFINITE, ET_FLAG_RANGE_IN, ET_FLAG_D_INVALID, ET_FLAG_TIMEOUT, ET_FLAG_TRUNCATION, ET_FLAG_CG_CAP = (
+    1, 2, 4, 8, 16, 32)
 
 PRECISIONS = {"f64": ET_F64, "f32": ET_F32, "df64": ET_DF64}
 OPS = {"conservative": ET_OP_CONSERVATIVE, "literal": ET_OP_LITERAL}
@@ -98,6 +99,8 @@ _SIGS = {
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "et_get_truncation": ([_VP, ctypes.POINTER(_D)], _I),
+    "et_cn_run": ([_VP, _VP, _D, _I, _D, _I, _VP], _I),
+    "et_cn_iteration_cap": ([_VP, _D, _D], _I),
     "et_probe_stream": ([_VP, _VP, ctypes.c_size_t, _I, _I, _VP, ctypes.POINTER(_D)], _I),
 }
 
@@ -279,6 +282,14 @@ class Grid:
         self._chk(self.lib.et_get_schedule(self.handle, float(tau), ctypes.byref(s), ctypes.byref(m),
                                            ctypes.byref(mu), ctypes.byref(th)))
         return s.value, m.value, mu.value, th.value
+
+    def cn_run(self, u, tau, nsteps, rtol=1e-12, max_iter=0, info=None):
+        """nsteps Crank-Nicolson steps (Sec. 2.3) of u in place, by conjugate gradients."""
+        self._chk(self.lib.et_cn_run(self.handle, self._dev_f64(u, "u"), float(tau), int(nsteps), float(rtol),
+                                     int(max_iter), None if info is None else info.data_ptr()))
+
+    def cn_iteration_cap(self, tau, rtol=1e-12):
+        return int(self.lib.et_cn_iteration_cap(self.handle, float(tau), float(rtol)))
 
     def truncation(self):
         """A-posteriori truncation estimate of the latest step (relative to max|u^n|)."""

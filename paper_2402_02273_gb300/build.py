@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libet.so")
 SOURCES = ["et_api.cu", "et_batch_api.cu", "et_kernels.cu", "et_df64.cu", "et_adjoint.cu", "et_fused.cu", "et_probe.cu",
-           "et_noalloc.cu", "et_quad.cu", "et_quadpair.cu"]
+           "et_noalloc.cu", "et_quad.cu", "et_quadpair.cu",
+           "et_cn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

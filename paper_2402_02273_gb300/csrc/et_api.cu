@@ -17,6 +17,7 @@
 
 #include "et.h"
 #include "et_chain.h"
+#include "et_cn.h"
 #include "et_internal.h"
 #include "et_plan.h"
 
@@ -47,7 +48,7 @@ struct Layout {
     unsigned nblocks;
 };
 
-constexpr size_t kMiscBytes = 2048;  // counters, flags, info slot; the truncation estimate at 1024
+constexpr size_t kMiscBytes = 2048;  // counters, flags, info slot; truncation estimate at 1024, CN scalars at 1536
 
 bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     if (nx <= 0 || ny <= 0 || nz <= 0) return false;
@@ -177,6 +178,14 @@ struct et_grid {
     unsigned long long* wnorm;  // residual warps' norm slots of the truncation estimate
     double* npartial;           // the stats blocks' maxima of those
     double* trunc_est;          // the latest step's estimate
+    // Crank-Nicolson: device scalars of the solve and the captured step
+    CnScalars* cn_sc;
+    cudaGraphExec_t cn_exec;
+    CoeffKey cn_key;
+    double* cn_u;
+    et_step_info* cn_info;
+    double cn_tau, cn_rtol;
+    int cn_cap;
     // model state
     bool coeffs_set;
     et_operator op;
@@ -988,6 +997,63 @@ double resolved_tol(const et_options* options, et_precision precision) { return 
 
 }  // namespace et
 
+namespace {
+
+// Conjugate-gradient iterations that reach a relative residual rtol for
+// M = I - tau/2 A_n: with Gershgorin, the eigenvalues of A_n lie in
+// [-(2 rmax + rho'), rho'], so those of M in [1 - tau rho'/2, 1 + tau (rmax + rho'/2)];
+// the classical bound ||r_k|| <= 2 sqrt(kappa) ((sqrt(kappa) - 1) / (sqrt(kappa) + 1))^k ||r_0||
+// then gives the cap (two iterations of margin for rounding).
+int cn_cap_of(const et_grid* g, double tau, double rtol) {
+    const double rho_c = (g->scheme == ET_SCHEME_ROSENBROCK) ? g->rho * (1.0 + 2.0 * kRangeSlack) : 0.0;
+    const double lo = 1.0 - 0.5 * tau * rho_c;
+    const double hi = 1.0 + tau * (g->rmax + 0.5 * rho_c);
+    const double sk = std::sqrt(hi / lo);
+    if (sk <= 1.0 + 1e-12) return 2;
+    const double k = std::log(2.0 * sk / rtol) / std::log((sk + 1.0) / (sk - 1.0));
+    return (int)std::ceil(k) + 2;
+}
+
+// One Crank-Nicolson step on stream st: residual (b_n and the diagonal of
+// A_n), the solve of M delta = tau b_n, u += delta, the step record.
+et_status enqueue_cn_step(et_grid* g, double* u, double tau, double rtol, int cap, et_step_info* info,
+                          int info_stride, cudaStream_t st) {
+    double* r = (double*)g->vec[0];
+    double* diag = (double*)g->vec[1];
+    double* p = (double*)g->vec[2];
+    double* q = (double*)g->vec[3];
+    double* delta = (double*)g->vec[4];
+    Weights<double> W64;
+    for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+    const double dt_shift = g->scheme == ET_SCHEME_ROSENBROCK ? g->rho : 0.0;  // the diagonal of A_n itself
+    cudaError_t e = launch_residual<double>(g->G, g->op, u, W64, g->rho, dt_shift, 1.0, g->scheme, r, diag,
+                                            g->flags, st);
+    if (e == cudaSuccess) e = launch_cn_init(g->n, tau, r, p, delta, g->cn_sc, g->partial, g->ticket, st);
+    const double* w[3] = {g->w[0], g->w[1], g->w[2]};
+    for (int it = 0; it < cap && e == cudaSuccess; ++it)
+        e = launch_cn_iteration(g->G, w, diag, tau, rtol, r, p, q, delta, g->cn_sc, (double*)g->wnorm, g->partial,
+                                g->ticket, st);
+    if (e == cudaSuccess) e = launch_cn_finish(g->n, delta, u, g->cn_sc, g->flags, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "Crank-Nicolson launch: %s", cudaGetErrorString(e));
+    StatsSink sink;
+    sink.partial = g->partial;
+    sink.ticket = g->ticket;
+    sink.step_counter = g->step_counter;
+    sink.flags = g->flags;
+    sink.info = info;
+    sink.info_stride = info_stride;
+    sink.last = g->info_slot;
+    sink.s = 0;  // a Crank-Nicolson step: m is its conjugate-gradient iterations
+    sink.m = 0;
+    sink.m_dev = &g->cn_sc->iters;
+    sink.ush = nullptr;
+    e = launch_stats(g->G, u, sink, st);
+    if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "stats launch: %s", cudaGetErrorString(e));
+    return ET_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int et_version(void) { return ET_VERSION; }
@@ -1135,6 +1201,12 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->wnorm = (unsigned long long*)(g->ws + L.wnorm);
     g->npartial = (double*)(g->ws + L.npartial);
     g->trunc_est = (double*)(misc + 1024);
+    g->cn_sc = (CnScalars*)(misc + 1536);
+    g->cn_exec = nullptr;
+    g->cn_u = nullptr;
+    g->cn_info = nullptr;
+    g->cn_tau = g->cn_rtol = 0.0;
+    g->cn_cap = 0;
     g->coeffs_set = false;
     g->rmax = 0.0;
     g->nu = 1.0;
@@ -1218,9 +1290,77 @@ et_status et_sync_info(et_grid* g, et_step_info* host_out) {
     if (host_out) *host_out = rec;
     if (flags & ET_FLAG_TIMEOUT) return fail(g, ET_ERR_TIMEOUT, "a device-side wait ran out; the run is not valid");
     if (flags & ET_FLAG_NONFINITE) return fail(g, ET_ERR_NUMERIC, "non-finite density met");
+    if (flags & ET_FLAG_CG_CAP)
+        return fail(g, ET_ERR_NUMERIC, "a Crank-Nicolson solve reached its iteration cap before its tolerance");
     if (flags & ET_FLAG_RANGE_IN)
         return fail(g, ET_ERR_NUMERIC, "density outside [0, 1] (+-1e-3): the step bound does not hold");
     return ET_OK;
+}
+
+et_status et_cn_run(et_grid* g, double* u, double tau, int nsteps, double rtol, int max_iter, et_step_info* info) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    if (g->prec != ET_F64) return fail(g, ET_ERR_UNSUPPORTED, "Crank-Nicolson steps run on ET_F64 grids");
+    if (g->op != ET_OP_CONSERVATIVE)
+        return fail(g, ET_ERR_UNSUPPORTED, "Crank-Nicolson steps need the conservative (symmetric) operator");
+    if (!u || !aligned8(u)) return fail(g, ET_ERR_ARG, "u must be a non-NULL 8-byte aligned device pointer");
+    if (info && !aligned8(info)) return fail(g, ET_ERR_ARG, "info must be 8-byte aligned");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(g, ET_ERR_ARG, "tau must be finite and > 0");
+    if (g->scheme == ET_SCHEME_ROSENBROCK && !(0.5 * tau * g->rho * (1.0 + 2.0 * kRangeSlack) < 1.0))
+        return fail(g, ET_ERR_ARG, "tau rho must be below 2 (I - tau/2 A is then positive definite)");
+    if (nsteps < 1) return fail(g, ET_ERR_ARG, "nsteps must be >= 1");
+    if (!(rtol > 0.0 && rtol < 1.0)) return fail(g, ET_ERR_ARG, "rtol must be in (0, 1)");
+    if (max_iter < 0 || max_iter > 100000) return fail(g, ET_ERR_ARG, "max_iter must be in [0, 100000]");
+    DeviceGuard dg(g->device);
+    const int cap = max_iter > 0 ? max_iter : cn_cap_of(g, tau, rtol);
+    et_step_info* dst = info ? info : g->info_slot;
+    const int stride = info ? 1 : 0;
+    ET_CUDA(g, cudaMemsetAsync(g->step_counter, 0, sizeof(unsigned), g->stream));
+    ET_CUDA(g, prime_launch_limits());
+    const ResolvedOptions ro = resolve(g->opt_set ? &g->opt : nullptr, g->prec);
+    if (!ro.use_graph) {
+        for (int t = 0; t < nsteps; ++t) {
+            const et_status rc = enqueue_cn_step(g, u, tau, rtol, cap, dst, stride, g->stream);
+            if (rc != ET_OK) return rc;
+        }
+        return ET_OK;
+    }
+    // one step captured once and replayed: the step index comes from the device
+    const CoeffKey key = coeff_key(g);
+    const bool same = g->cn_exec && g->cn_u == u && g->cn_info == dst && g->cn_tau == tau && g->cn_rtol == rtol &&
+                      g->cn_cap == cap && same_coeffs(g->cn_key, key);
+    if (!same) {
+        if (g->cn_exec) cudaGraphExecDestroy(g->cn_exec);
+        g->cn_exec = nullptr;
+        ET_CUDA(g, cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+        const et_status rc = enqueue_cn_step(g, u, tau, rtol, cap, dst, stride, g->capture);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(g->capture, &graph);
+        if (rc != ET_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(g, ET_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&g->cn_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            g->cn_exec = nullptr;
+            return fail(g, ET_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        g->cn_u = u;
+        g->cn_info = dst;
+        g->cn_tau = tau;
+        g->cn_rtol = rtol;
+        g->cn_cap = cap;
+        g->cn_key = key;
+    }
+    for (int t = 0; t < nsteps; ++t) ET_CUDA(g, cudaGraphLaunch(g->cn_exec, g->stream));
+    return ET_OK;
+}
+
+int et_cn_iteration_cap(const et_grid* g, double tau, double rtol) {
+    if (!g || !g->coeffs_set || !(tau > 0.0) || !(rtol > 0.0 && rtol < 1.0)) return 0;
+    return cn_cap_of(g, tau, rtol);
 }
 
 et_status et_get_truncation(et_grid* g, double* estimate) {
@@ -1356,6 +1496,7 @@ void et_destroy(et_grid* g) {
         DeviceGuard dg(g->device);
         clear_graphs(g);
         clear_events(g);
+        if (g->cn_exec) cudaGraphExecDestroy(g->cn_exec);
         if (g->capture) cudaStreamDestroy(g->capture);
     }
     pair_plan_destroy(g->pair);

@@ -90,6 +90,7 @@ struct StatsSink {
     int info_stride;        // records step t at info[t * info_stride] (0: always info[0])
     et_step_info* last;     // internal copy of the latest record (read by et_sync_info)
     int s, m;               // recorded in the info
+    const int* m_dev = nullptr;  // non-null: m is read from here (iterations of a Crank-Nicolson solve)
     float2* ush;            // F32 / DF64: receives the pair of each u (nullptr: none)
     // truncation estimate (nullptr wnorm: none): est = trunc_c max|b| / max|u^n|,
     // ET_FLAG_TRUNCATION when est > trunc_tol; est is stored to *trunc_est

@@ -479,7 +479,7 @@ __device__ __forceinline__ void stats_body(long long n, const double* __restrict
         rec.umax = order_key_inv(kmax);
         rec.mass = sum;
         rec.s = s.s;
-        rec.m = s.m;
+        rec.m = s.m_dev ? *s.m_dev : s.m;
         if (s.wnorm) {
             // a-posteriori truncation estimate of the step: the remainder bound
             // of its (s, m) with the measured max |b| in place of its a-priori

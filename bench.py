@@ -73,13 +73,13 @@ def launch_mix(prec, s, m, pairs):
 # captured on the first 8 grids of the batch (19.0 M voxels) and scaled to the
 # whole launch by its voxels (traffic grows with them: no re-reads across grids).
 TERM_TRAFFIC = {
-    ("f64", "term_kernel_f64", 128): (133101312 / 128 ** 3, "41309fa9a1cf"),
-    ("f32", "term_quad_kernel", 128): (356608 / 128 ** 3, "a6bae89026da"),
+    ("f64", "term_kernel_f64", 128): (131120128 / 128 ** 3, "3bc61db3f5b7"),
+    ("f32", "term_quad_kernel", 128): (403712 / 128 ** 3, "a6bae89026da"),
     ("df64", "term2_kernel", 128): (98716672 / 128 ** 3, "6b1e73fcb9ec"),
     ("df64", "term2_kernel", 192): (414701056 / 192 ** 3, "6b1e73fcb9ec"),
-    ("f32", "term2_quad_kernel", 160): (74726144 / 160 ** 3, "6ba6fd188ae6"),
-    ("f32", "term2_quad_kernel", 192): (201267456 / 192 ** 3, "6ba6fd188ae6"),
-    ("f32", "batch_term2_quad_kernel", "batch"): (561275904 / 19017728, "6ba6fd188ae6"),
+    ("f32", "term2_quad_kernel", 160): (80283136 / 160 ** 3, "6ba6fd188ae6"),
+    ("f32", "term2_quad_kernel", 192): (200293888 / 192 ** 3, "6ba6fd188ae6"),
+    ("f32", "batch_term2_quad_kernel", "batch"): (560431104 / 19017728, "6ba6fd188ae6"),
 }
 KERNEL_SOURCE = {"term_kernel_f64": "et_kernels.cu", "term2_kernel": "et_fused.cu",
                  "term_quad_kernel": "et_quad.cu", "term_kernel_df64": "et_df64.cu",

@@ -162,6 +162,13 @@ ET_API et_status et_create_grid(int nx, int ny, int nz, double h, et_precision p
  * ET_ERR_NUMERIC if some D is negative or not finite. */
 ET_API et_status et_set_coeffs(et_grid* g, const double* D, double rho, et_operator op,
                         et_scheme scheme, const et_options* options);
+/* Same as et_set_coeffs with the diffusion field dscale * D (dscale >= 0;
+ * each product rounded once, in the coefficient kernel: the same weights as
+ * et_set_coeffs on a field scaled beforehand in FP64).  For a uniform D scale
+ * as a model parameter (its gradient comes from et_vjp) without a scaled
+ * copy of D. */
+ET_API et_status et_set_coeffs_scaled(et_grid* g, const double* D, double dscale, double rho, et_operator op,
+                                      et_scheme scheme, const et_options* options);
 /* Same as et_set_coeffs with D in host memory (copied through the workspace). */
 ET_API et_status et_set_coeffs_host(et_grid* g, const double* D_host, double rho, et_operator op,
                              et_scheme scheme, const et_options* options);

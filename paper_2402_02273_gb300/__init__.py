@@ -99,6 +99,7 @@ _SIGS = {
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "et_get_truncation": ([_VP, ctypes.POINTER(_D)], _I),
+    "et_set_coeffs_scaled": ([_VP, _VP, _D, _D, _I, _I, _VP], _I),
     "et_cn_run": ([_VP, _VP, _D, _I, _D, _I, _VP], _I),
     "et_cn_iteration_cap": ([_VP, _D, _D], _I),
     "et_probe_stream": ([_VP, _VP, ctypes.c_size_t, _I, _I, _VP, ctypes.POINTER(_D)], _I),
@@ -229,11 +230,15 @@ class Grid:
                                       f"elements on {self.device}")
         return t.data_ptr()
 
-    def set_coeffs(self, D, rho=0.025, op="conservative", scheme="rosenbrock", **opts):
-        """D: float64 device tensor (n values) or a numpy array (copied through the host path)."""
+    def set_coeffs(self, D, rho=0.025, op="conservative", scheme="rosenbrock", dscale=None, **opts):
+        """D: float64 device tensor (n values) or a numpy array (copied through the host
+        path).  dscale: the field is read as dscale * D (device tensors only)."""
         o = make_options(**opts)
         self.options = o
-        if isinstance(D, np.ndarray):
+        if dscale is not None:
+            rc = self.lib.et_set_coeffs_scaled(self.handle, self._dev_f64(D, "D"), float(dscale), float(rho),
+                                               OPS[op], SCHEMES[scheme], ctypes.byref(o))
+        elif isinstance(D, np.ndarray):
             Dh = np.ascontiguousarray(D, dtype=np.float64)
             if Dh.size != self.n:
                 raise EtError(ET_ERR_ARG, "D has the wrong size")
@@ -508,7 +513,7 @@ def tumour_run(u0, rho, dscale, D0, tau, nsteps, grid=None, checkpoint_every=10,
             g = grid if grid is not None else Grid(D0.shape)
             r = float(rho_)
             ds = float(dscale_)
-            g.set_coeffs(D0 * ds, rho=r, **coeff_opts)
+            g.set_coeffs(D0, rho=r, dscale=ds, **coeff_opts)
             u = u0_.detach().clone().contiguous()
             # the forward run keeps the checkpoints the backward pass starts from
             ctx.ws = g.run_checkpointed(u, tau, nsteps, checkpoint_every)

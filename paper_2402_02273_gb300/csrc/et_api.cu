@@ -627,7 +627,8 @@ et_status run_impl(et_grid* g, double* u, double tau, int nsteps, et_step_info* 
 }
 
 et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator op, et_scheme scheme,
-                          const et_options* opt) {
+                          const et_options* opt, double dscale = 1.0) {
+    if (!(dscale >= 0.0) || !std::isfinite(dscale)) return fail(g, ET_ERR_ARG, "dscale must be finite and >= 0");
     if (!(rho >= 0.0) || !std::isfinite(rho)) return fail(g, ET_ERR_ARG, "rho must be finite and >= 0");
     if (op != ET_OP_CONSERVATIVE && op != ET_OP_LITERAL) return fail(g, ET_ERR_ARG, "unknown operator %d", (int)op);
     if (scheme != ET_SCHEME_ROSENBROCK && scheme != ET_SCHEME_EXPEULER)
@@ -647,7 +648,7 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     ET_CUDA(g, cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->stream));
     ET_CUDA(g, cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), g->stream));
     const double inv_h2 = 1.0 / (g->h * g->h);
-    cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w, g->rmax_bits, g->flags, g->stream);
+    cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w, g->rmax_bits, g->flags, g->stream, dscale);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
     unsigned long long bits = 0;
     unsigned flags = 0;
@@ -1237,14 +1238,24 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
 
 et_status et_set_coeffs(et_grid* g, const double* D, double rho, et_operator op, et_scheme scheme,
                         const et_options* options) {
+    NvtxRange nvtx_range("et_set_coeffs");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     if (!D || !aligned8(D)) return fail(g, ET_ERR_ARG, "D must be a non-NULL 8-byte aligned device pointer");
     DeviceGuard dg(g->device);
     return set_coeffs_impl(g, D, rho, op, scheme, options);
 }
 
+et_status et_set_coeffs_scaled(et_grid* g, const double* D, double dscale, double rho, et_operator op,
+                               et_scheme scheme, const et_options* options) {
+    NvtxRange nvtx_range("et_set_coeffs_scaled");
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!D || !aligned8(D)) return fail(g, ET_ERR_ARG, "D must be a non-NULL 8-byte aligned device pointer");
+    DeviceGuard dg(g->device);
+    return set_coeffs_impl(g, D, rho, op, scheme, options, dscale);
+}
 et_status et_set_coeffs_host(et_grid* g, const double* D_host, double rho, et_operator op, et_scheme scheme,
                              const et_options* options) {
+    NvtxRange nvtx_range("et_set_coeffs_host");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     if (!D_host) return fail(g, ET_ERR_ARG, "D_host must not be NULL");
     DeviceGuard dg(g->device);
@@ -1253,18 +1264,21 @@ et_status et_set_coeffs_host(et_grid* g, const double* D_host, double rho, et_op
 }
 
 et_status et_step(et_grid* g, double* u, double tau, et_step_info* info) {
+    NvtxRange nvtx_range("et_step");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
     return run_impl(g, u, tau, 1, info);
 }
 
 et_status et_run(et_grid* g, double* u, double tau, int nsteps, et_step_info* info) {
+    NvtxRange nvtx_range("et_run");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
     return run_impl(g, u, tau, nsteps, info);
 }
 
 et_status et_run_host(et_grid* g, double* u_host, double tau, int nsteps, et_step_info* info_host) {
+    NvtxRange nvtx_range("et_run_host");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     if (!u_host) return fail(g, ET_ERR_ARG, "u_host must not be NULL");
     if (nsteps < 1) return fail(g, ET_ERR_ARG, "nsteps must be >= 1");
@@ -1298,6 +1312,7 @@ et_status et_sync_info(et_grid* g, et_step_info* host_out) {
 }
 
 et_status et_cn_run(et_grid* g, double* u, double tau, int nsteps, double rtol, int max_iter, et_step_info* info) {
+    NvtxRange nvtx_range("et_cn_run");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
     if (g->prec != ET_F64) return fail(g, ET_ERR_UNSUPPORTED, "Crank-Nicolson steps run on ET_F64 grids");
@@ -1442,6 +1457,7 @@ size_t et_vjp_workspace_bytes(const et_grid* g, double tau, int nsteps, int chec
 et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int checkpoint_every,
                  const double* ubar_final, double* ubar0, double* grad_rho, double* grad_dscale,
                  void* workspace, size_t workspace_bytes) {
+    NvtxRange nvtx_range("et_vjp");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
     if (!u0 || !ubar_final || !ubar0 || !aligned8(u0) || !aligned8(ubar_final) || !aligned8(ubar0))
@@ -1463,6 +1479,7 @@ et_status et_vjp(et_grid* g, const double* u0, double tau, int nsteps, int check
 
 et_status et_run_checkpointed(et_grid* g, double* u, double tau, int nsteps, int checkpoint_every, void* workspace,
                               size_t workspace_bytes) {
+    NvtxRange nvtx_range("et_run_checkpointed");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
     if (!u || !aligned8(u)) return fail(g, ET_ERR_ARG, "u must be an 8-byte aligned device pointer");
@@ -1476,6 +1493,7 @@ et_status et_run_checkpointed(et_grid* g, double* u, double tau, int nsteps, int
 et_status et_vjp_checkpointed(et_grid* g, double tau, int nsteps, int checkpoint_every, const double* ubar_final,
                               double* ubar0, double* grad_rho, double* grad_dscale, void* workspace,
                               size_t workspace_bytes) {
+    NvtxRange nvtx_range("et_vjp_checkpointed");
     if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
     DeviceGuard dg(g->device);
     if (!ubar_final || !ubar0 || !aligned8(ubar_final) || !aligned8(ubar0))

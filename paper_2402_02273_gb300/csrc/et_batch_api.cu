@@ -704,6 +704,7 @@ et_status et_batch_create(int count, const int* dims, double h, et_precision pre
 
 et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, et_operator op, et_scheme scheme,
                               const et_options* options) {
+    NvtxRange nvtx_range("et_batch_set_coeffs");
     if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
     if (!D || ((uintptr_t)D & 7u) || !rho) return bfail(b, ET_ERR_ARG, "D (device) and rho (host) must be given");
     if (op != ET_OP_CONSERVATIVE && op != ET_OP_LITERAL) return bfail(b, ET_ERR_ARG, "unknown operator");
@@ -782,6 +783,7 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
 }
 
 et_status et_batch_run(et_batch* b, double* u, double tau, int nsteps, et_step_info* info) {
+    NvtxRange nvtx_range("et_batch_run");
     if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
     if (!b->coeffs_set) return bfail(b, ET_ERR_STATE, "et_batch_set_coeffs has not been called");
     if (!u || ((uintptr_t)u & 7u)) return bfail(b, ET_ERR_ARG, "u must be an 8-byte aligned device pointer");
@@ -795,6 +797,7 @@ et_status et_batch_run(et_batch* b, double* u, double tau, int nsteps, et_step_i
 }
 
 et_status et_batch_autotune(et_batch* b, double tau, int* variant, double* us_per_variant) {
+    NvtxRange nvtx_range("et_batch_autotune");
     if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
     if (!b->coeffs_set) return bfail(b, ET_ERR_STATE, "et_batch_set_coeffs has not been called");
     if (!(tau > 0.0) || !std::isfinite(tau)) return bfail(b, ET_ERR_ARG, "tau must be finite and > 0");

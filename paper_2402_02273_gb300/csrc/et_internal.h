@@ -10,8 +10,19 @@
 #include <utility>
 
 #include "et.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace et {
+
+// NVTX range over one call of the C ABI (header-only NVTX: a no-op unless a
+// tool such as ncu --nvtx is attached).  Kernels a call enqueues, and graphs
+// it launches, carry the range's name in the tool's view.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Density range accepted by the a-priori bound |1 - 2u| <= 1 + 2 * kRangeSlack
 // of the folded scheme (ET_FLAG_RANGE_IN outside it).
@@ -258,10 +269,10 @@ cudaError_t launch_batch_residual(et_operator op, int scheme, const BatchResidua
 cudaError_t launch_batch_stats(const BatchStats* d, int count, cudaStream_t stream);
 
 // Kernel launchers (et_kernels.cu).  All enqueue on `stream` and return the
-// launch error.
+// launch error.  launch_coeffs reads the diffusion field as D * dscale.
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op,
                           double* const w[5], unsigned long long* rmax_bits, unsigned* flags,
-                          cudaStream_t stream);
+                          cudaStream_t stream, double dscale = 1.0);
 // Typed copies of w[0..3] scaled by `scale` (1 / nu for the FP32 and DF64 forms).
 cudaError_t launch_convert_weights(const Geom& G, const double* const w[4], float* const wf[4],
                                    double scale, cudaStream_t stream);

@@ -62,7 +62,7 @@ dim3 voxel_grid(const Geom& G) {
 // coeffs: face weights, minus the row sums, and max_p sum_{q != p} |L_pq|.
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
-coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __restrict__ w0,
+coeffs_kernel(Geom G, const double* __restrict__ D, double dscale, double inv_h2, double* __restrict__ w0,
               double* __restrict__ w1, double* __restrict__ w2, double* __restrict__ w3,
               double* __restrict__ w4, unsigned long long* rmax_bits, unsigned* flags) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
@@ -71,7 +71,8 @@ coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __res
     double absrow = 0.0;
     if (i < G.nx && j < G.ny) {
         const long long p = i + G.sy * j + G.sz * k;
-        const double Dp = D[p];
+        // the field is read as D * dscale (a product rounded once; exact for dscale = 1)
+        const double Dp = D[p] * dscale;
         if (!(Dp >= 0.0) || !isfinite(Dp)) atomicOr(flags, ET_FLAG_D_INVALID);
         const int c[3] = {i, j, k};
         const int ext[3] = {G.nx, G.ny, G.nz};
@@ -81,8 +82,8 @@ coeffs_kernel(Geom G, const double* __restrict__ D, double inv_h2, double* __res
         for (int a = 0; a < 3; ++a) {
             const bool has_plus = c[a] + 1 < ext[a];
             const bool has_minus = c[a] > 0;
-            const double Dq = has_plus ? D[p + st[a]] : 0.0;
-            const double Dm = has_minus ? D[p - st[a]] : 0.0;
+            const double Dq = has_plus ? D[p + st[a]] * dscale : 0.0;
+            const double Dm = has_minus ? D[p - st[a]] * dscale : 0.0;
             double wplus, wminus;
             if (OP == ET_OP_CONSERVATIVE) {
                 wplus = has_plus ? harmonic_mean(Dp, Dq) * inv_h2 : 0.0;
@@ -648,14 +649,14 @@ int term_blocks_per_sm() {
 }  // namespace
 
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op, double* const w[5],
-                          unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream) {
+                          unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream, double dscale) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
         coeffs_kernel<ET_OP_CONSERVATIVE><<<voxel_grid(G), block, 0, stream>>>(
-            G, D, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
+            G, D, dscale, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
     else
         coeffs_kernel<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(
-            G, D, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
+            G, D, dscale, inv_h2, w[0], w[1], w[2], w[3], w[4], rmax_bits, flags);
     return cudaGetLastError();
 }
 

@@ -199,3 +199,31 @@ def test_autograd_function_gradients(env):
     assert np.abs(u0d.grad.cpu().numpy() - o_ub).max() <= 1e-9 * np.abs(o_ub).max()
     assert rho.grad.item() == pytest.approx(o_rho, rel=1e-9)
     assert ds.grad.item() == pytest.approx(o_ds / 1.2, rel=1e-9)
+
+
+def test_scaled_coefficients_equal_a_scaled_field_bitwise():
+    """et_set_coeffs_scaled reads dscale * D in the coefficient kernel: the same
+    weights, and so the same run, as et_set_coeffs on the field scaled in FP64
+    beforehand (the autograd function uses it for its D scale)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_02273_gb300 as et
+    D, u0 = phantom.case((14, 12, 20), seed=8, noise=0.1)
+    Dd = torch.from_numpy(D).cuda()
+    outs = []
+    for scaled in (True, False):
+        g = et.Grid(D.shape)
+        if scaled:
+            g.set_coeffs(Dd, dscale=1.7)
+        else:
+            g.set_coeffs(Dd * 1.7)
+        u = torch.from_numpy(u0.copy()).cuda()
+        g.run(u, 7.3, 3)
+        g.sync_info()
+        outs.append((u.cpu().numpy(), g.rmax()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    g = et.Grid(D.shape)
+    with pytest.raises(et.EtError) as ex:
+        g.set_coeffs(Dd, dscale=-1.0)
+    assert ex.value.status == et.ET_ERR_ARG

@@ -75,8 +75,8 @@ def launch_mix(prec, s, m, pairs):
 TERM_TRAFFIC = {
     ("f64", "term_kernel_f64", 128): (131120128 / 128 ** 3, "3bc61db3f5b7"),
     ("f32", "term_quad_kernel", 128): (403712 / 128 ** 3, "a6bae89026da"),
-    ("df64", "term2_kernel", 128): (98716672 / 128 ** 3, "6b1e73fcb9ec"),
-    ("df64", "term2_kernel", 192): (414701056 / 192 ** 3, "6b1e73fcb9ec"),
+    ("df64", "term2_kernel", 128): (126326272 / 128 ** 3, "6b1e73fcb9ec"),
+    ("df64", "term2_kernel", 192): (414991360 / 192 ** 3, "6b1e73fcb9ec"),
     ("f32", "term2_quad_kernel", 160): (80283136 / 160 ** 3, "6ba6fd188ae6"),
     ("f32", "term2_quad_kernel", 192): (200293888 / 192 ** 3, "6ba6fd188ae6"),
     ("f32", "batch_term2_quad_kernel", "batch"): (560431104 / 19017728, "6ba6fd188ae6"),

@@ -365,16 +365,14 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
             if constexpr (std::is_same<T, double>::value) {
                 e = launch_term(g->G, g->op, B.W, op.a1, st);
             } else {
-                bool done = false;
+                // FP32 Horner pairs on the vector two-term kernel where it
+                // applies, other pairs on the TMA-fed one
+                bool vec = false;
                 if constexpr (std::is_same<T, float>::value) {
-                    // FP32 Horner pairs on the four-voxel two-term kernel where
-                    // it applies, other pairs on the TMA-fed one
-                    if (op.pair && quad_pair_eligible(g->G, B.W, op.a1, op.a2)) {
-                        e = launch_term_quad_pair(g->G, g->op, B.W, op.a1, op.a2, st);
-                        done = true;
-                    }
+                    vec = op.pair && vec_pair_eligible<T>(g->G, g->op, B.W, op.a1, op.a2);
+                    if (vec) e = launch_term_vec_pair<T>(g->G, g->op, B.W, op.a1, op.a2, st);
                 }
-                if (!done)
+                if (!vec)
                     e = op.pair ? launch_term_pair(g->pair, g->G, g->op, op.a1, op.a2, g->flags, st, probe_ns(g))
                                 : launch_term(g->G, g->op, B.W, op.a1, st);
             }

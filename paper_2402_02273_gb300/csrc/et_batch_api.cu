@@ -47,7 +47,7 @@ size_t pair_desc_bytes(et_precision prec) {
     return prec == ET_F64 ? 0 : (prec == ET_F32 ? sizeof(BatchPair<float>) : sizeof(BatchPair<float2>));
 }
 // F32 Horner pairs on the four-voxel two-term kernel
-size_t qpair_desc_bytes(et_precision prec) { return prec == ET_F32 ? sizeof(QuadPairGrid) : 0; }
+size_t qpair_desc_bytes(et_precision prec) { return prec == ET_F32 ? sizeof(VecPairGrid<float>) : 0; }
 // Per grid: up to kMaxTermLaunches single terms, or half as many pairs, plus
 // its residual and stats descriptors.
 size_t desc_bytes_per_instance(et_precision prec) {
@@ -313,7 +313,7 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
     b->qpair_first.assign(nl, 0);
     std::vector<BatchTerm<T>> singles;
     std::vector<BatchPair<T>> pairs;
-    std::vector<QuadPairGrid> qpairs;
+    std::vector<VecPairGrid<T>> qpairs;
     for (int l = 0; l < nl; ++l) {
         b->single_first[l] = (long long)singles.size();
         b->pair_first[l] = (long long)pairs.size();
@@ -324,13 +324,13 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
             const ChainOp<T>& op = ops[i][l];
             bool quad = false;
             if constexpr (std::is_same<T, float>::value) {
-                // FP32 Horner pairs: the four-voxel two-term kernel where it applies
+                // FP32 Horner pairs: the vector two-term kernel where it applies
                 const Geom G = geom_of(b, i);
-                const Weights<float> W = typed_weights<float>(b, i);
-                if (op.pair && quad_pair_eligible(G, W, op.a1, op.a2)) {
+                const Weights<T> W = typed_weights<T>(b, i);
+                if (op.pair && vec_pair_eligible<T>(G, b->op, W, op.a1, op.a2)) {
                     const int tz = G.nz < 32 ? G.nz : 32;
-                    qpairs.push_back(quad_pair_grid(G, W, op.a1, op.a2, tz, qt));
-                    qt += quad_pair_tiles(G, tz);
+                    qpairs.push_back(vec_pair_grid<T>(G, W, op.a1, op.a2, tz, qt));
+                    qt += vec_pair_tiles<T>(G, tz);
                     quad = true;
                 }
             }
@@ -394,14 +394,14 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
     const size_t head = sizeof(BatchResidual<T>) * C + sizeof(BatchStats) * C;
     b->pair_table_offset = align64(head + sizeof(BatchTerm<T>) * singles.size());
     b->qpair_table_offset = align64(b->pair_table_offset + sizeof(BatchPair<T>) * pairs.size());
-    bytes.assign(b->qpair_table_offset + sizeof(QuadPairGrid) * qpairs.size(), 0);
+    bytes.assign(b->qpair_table_offset + sizeof(VecPairGrid<T>) * qpairs.size(), 0);
     char* p = bytes.data();
     std::memcpy(p, res.data(), sizeof(BatchResidual<T>) * C);
     std::memcpy(p + sizeof(BatchResidual<T>) * C, stv.data(), sizeof(BatchStats) * C);
     if (!singles.empty()) std::memcpy(p + head, singles.data(), sizeof(BatchTerm<T>) * singles.size());
     if (!pairs.empty()) std::memcpy(p + b->pair_table_offset, pairs.data(), sizeof(BatchPair<T>) * pairs.size());
     if (!qpairs.empty())
-        std::memcpy(p + b->qpair_table_offset, qpairs.data(), sizeof(QuadPairGrid) * qpairs.size());
+        std::memcpy(p + b->qpair_table_offset, qpairs.data(), sizeof(VecPairGrid<T>) * qpairs.size());
     return ET_OK;
 }
 
@@ -422,9 +422,12 @@ cudaError_t launch_index(et_batch* b, const char* dsingles, const char* dpairs, 
                                           b->opt_set && b->opt.timeout_probe_us > 0
                                               ? 1000ull * (unsigned long long)b->opt.timeout_probe_us
                                               : 0ull);
-        if (e == cudaSuccess && b->qpair_count[l] > 0)
-            e = launch_batch_term_quad_pair(b->op, reinterpret_cast<const QuadPairGrid*>(dqpairs) + b->qpair_first[l],
-                                            b->qpair_count[l], b->qpair_tiles[l], b->sms, st);
+        if constexpr (std::is_same<T, float>::value) {
+            if (e == cudaSuccess && b->qpair_count[l] > 0)
+                e = launch_batch_term_vec_pair<T>(b->op,
+                                                  reinterpret_cast<const VecPairGrid<T>*>(dqpairs) + b->qpair_first[l],
+                                                  b->qpair_count[l], b->qpair_tiles[l], b->sms, st);
+        }
     }
     return e;
 }
@@ -517,7 +520,7 @@ et_status autotune(et_batch* b, double tau, double* us_out) {
             if constexpr (!std::is_same<T, double>::value) {
                 const BatchPair<T>* pd = reinterpret_cast<const BatchPair<T>*>(bytes.data() + b->pair_table_offset);
                 for (int q = 0; q < b->pair_count[0]; ++q) vterms += 2.0 * (double)pd[q].G.n;
-                const QuadPairGrid* qd = reinterpret_cast<const QuadPairGrid*>(bytes.data() + b->qpair_table_offset);
+                const VecPairGrid<T>* qd = reinterpret_cast<const VecPairGrid<T>*>(bytes.data() + b->qpair_table_offset);
                 for (int q = 0; q < b->qpair_count[0]; ++q) vterms += 2.0 * (double)qd[q].G.n;
             }
         }

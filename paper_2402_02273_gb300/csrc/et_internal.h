@@ -349,29 +349,38 @@ int batch_pair_tz(const Geom& G);
 template <typename T>
 cudaError_t launch_batch_term_pair(et_operator op, const BatchPair<T>* d, int count, long long tiles, int sms,
                                    unsigned* flags, cudaStream_t stream, unsigned long long probe_ns = 0);
-// Two consecutive Horner terms of sub-step 0 in one launch, FP32, four voxels
-// per thread on full-width tiles of th rows and tz planes, fed by asynchronous
-// copies (et_quadpair.cu); the per-voxel arithmetic of the one-term kernels.
-// Eligible: nx % 4 == 0, nx <= 256, 16-byte aligned fields, n < 2^31, a1 and a2 Horner terms
-// (a1 not last, a2 not scaled) on the same b and diagonal.
-struct QuadPairGrid {
+// Two consecutive Horner terms of sub-step 0 in one launch, one 16-byte vector
+// of each field per thread (four FP32 voxels), on full-width tiles of th rows
+// and tz planes, fed by asynchronous copies (et_quadpair.cu); the per-voxel
+// arithmetic of the one-term kernels.  Eligible: FP32 (instantiated for
+// float; DF64 keeps the TMA-fed kernel), nx % 4 == 0, nx <= 256, 16-byte
+// aligned fields, n < 2^31, a1 and a2 Horner terms (a1 not last, a2 not
+// scaled) on the same b and diagonal.
+template <typename T>
+struct VecPairGrid {
     Geom G;
-    Weights<float> W;
-    TermArgs<float> a1, a2;
+    Weights<T> W;
+    TermArgs<T> a1, a2;
     long long tile_begin;  // first tile of this grid in a batched launch
     int th, tz;            // rows and planes of a tile
 };
-bool quad_pair_eligible(const Geom& G, const Weights<float>& W, const TermArgs<float>& a1,
-                        const TermArgs<float>& a2);
-int quad_pair_rows(const Geom& G);
-long long quad_pair_tiles(const Geom& G, int tz);
-QuadPairGrid quad_pair_grid(const Geom& G, const Weights<float>& W, const TermArgs<float>& a1,
-                            const TermArgs<float>& a2, int tz, long long tile_begin);
-cudaError_t launch_term_quad_pair(const Geom& G, et_operator op, const Weights<float>& W, const TermArgs<float>& a1,
-                                  const TermArgs<float>& a2, cudaStream_t stream);
+template <typename T>
+bool vec_pair_eligible(const Geom& G, et_operator op, const Weights<T>& W, const TermArgs<T>& a1,
+                       const TermArgs<T>& a2);
+template <typename T>
+int vec_pair_rows(const Geom& G);
+template <typename T>
+long long vec_pair_tiles(const Geom& G, int tz);
+template <typename T>
+VecPairGrid<T> vec_pair_grid(const Geom& G, const Weights<T>& W, const TermArgs<T>& a1, const TermArgs<T>& a2,
+                             int tz, long long tile_begin);
+template <typename T>
+cudaError_t launch_term_vec_pair(const Geom& G, et_operator op, const Weights<T>& W, const TermArgs<T>& a1,
+                                 const TermArgs<T>& a2, cudaStream_t stream);
 // Batched launch over count grids (device table d, tiles in all).
-cudaError_t launch_batch_term_quad_pair(et_operator op, const QuadPairGrid* d, int count, long long tiles, int sms,
-                                        cudaStream_t stream);
+template <typename T>
+cudaError_t launch_batch_term_vec_pair(et_operator op, const VecPairGrid<T>* d, int count, long long tiles, int sms,
+                                       cudaStream_t stream);
 cudaError_t prime_launch_limits_quad_pair();
 // min, max and sum of u and the non-finite flag into the step record.
 cudaError_t launch_stats(const Geom& G, const double* u, const StatsSink& sink, cudaStream_t stream);

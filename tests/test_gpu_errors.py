@@ -134,7 +134,9 @@ def test_bounded_wait_that_runs_out_reports_timeout(env, precision, use_graph):
 
 
 def test_bounded_wait_that_runs_out_reports_timeout_batched(env):
-    """The same hook on the batched two-term kernel (DF64, a two-term variant)."""
+    """The same hook on the batched TMA-fed two-term kernel (DF64, a two-term
+    variant, two sub-steps: its Horner pairs take the vector kernel, which has
+    no waits, its running-sum pairs the TMA-fed one)."""
     import oracle
     et, torch = env
     shapes = [(8, 16, 32), (10, 8, 16)]
@@ -142,14 +144,14 @@ def test_bounded_wait_that_runs_out_reports_timeout_batched(env):
     D = torch.from_numpy(np.concatenate([c[0].ravel() for c in cases])).cuda()
     u0 = np.concatenate([c[1].ravel() for c in cases])
     b = et.Batch(shapes, precision="df64")
-    b.set_coeffs(D, 0.025, timeout_probe_us=200)
+    b.set_coeffs(D, 0.025, timeout_probe_us=200, force_s=2)
     b.set_variant(0)  # the first half of the variants launch two terms at a time
     u = torch.from_numpy(u0.copy()).cuda()
     b.run(u, 7.3, 2)
     with pytest.raises(et.EtError) as ex:
         b.sync_info()
     assert ex.value.status == et.ET_ERR_TIMEOUT
-    b.set_coeffs(D, 0.025)
+    b.set_coeffs(D, 0.025, force_s=2)
     b.set_variant(0)
     u = torch.from_numpy(u0.copy()).cuda()
     b.run(u, 7.3, 2)

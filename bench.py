@@ -45,22 +45,33 @@ HORNER_BYTES = {"f64": 56, "df64": 56, "f32": 28}
 HORNER_FLOPS = {"f64": 15, "df64": 118, "f32": 15}
 TERM_BYTES = {"f64": 72, "df64": 72, "f32": 36}
 TERM_FLOPS = {"f64": 17, "df64": 139, "f32": 17}
+# In warp rows without off-diagonal entries (D = 0 around them) the FP64 term
+# kernel evaluates dt z + beta b only: z, the diagonal and b in, z out (32 B;
+# 48 with the running sum), 1 MUL + 1 FMA = 3 flops (5 with the running sum).
+ZERO_ROW_BYTES = {"horner": 32, "term": 48}
+ZERO_ROW_FLOPS = {"horner": 3, "term": 5}
 
 
-def launch_mix(prec, s, m, pairs):
+def launch_mix(prec, s, m, pairs, zero_frac=0.0):
     """(launches, algorithmic bytes, flops) per voxel of one step's term chain.
 
     Sub-step 0 has m - 1 Horner terms, each later sub-step m terms.  With pairs
     (the DF64 default) two consecutive terms of a sub-step share one launch
     that reads z, the weights, the diagonal and b once and writes one z (and the
-    sum), so a pair moves the bytes of one single term and does twice its flops."""
+    sum), so a pair moves the bytes of one single term and does twice its flops.
+    zero_frac: the share of voxels in warp rows without off-diagonal entries,
+    whose terms the FP64 kernel evaluates without the stencil."""
     def count(nterms):
         return (nterms // 2, nterms % 2) if pairs else (0, nterms)
     ph, sh = count(m - 1)
     pt, st = count(m)
     launches = ph + sh + (s - 1) * (pt + st)
-    nbytes = HORNER_BYTES[prec] * (ph + sh) + TERM_BYTES[prec] * (s - 1) * (pt + st)
-    flops = HORNER_FLOPS[prec] * (2 * ph + sh) + TERM_FLOPS[prec] * (s - 1) * (2 * pt + st)
+    hb = (1 - zero_frac) * HORNER_BYTES[prec] + zero_frac * ZERO_ROW_BYTES["horner"]
+    tb = (1 - zero_frac) * TERM_BYTES[prec] + zero_frac * ZERO_ROW_BYTES["term"]
+    hf = (1 - zero_frac) * HORNER_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["horner"]
+    tf = (1 - zero_frac) * TERM_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["term"]
+    nbytes = hb * (ph + sh) + tb * (s - 1) * (pt + st)
+    flops = hf * (2 * ph + sh) + tf * (s - 1) * (2 * pt + st)
     return launches, nbytes, flops
 
 
@@ -429,7 +440,9 @@ def main():
         avg_launch_ms = term_ms / max(term_launches, 1)
         s_, m_ = info["s"], info["m"]
         kname, pairs = term_kernel_of(prec, args.single_terms, ng)
-        nl, vb, vf = launch_mix(prec, s_, m_, pairs)
+        # the FP64 term kernel skips the stencil in rows without off-diagonal entries
+        zero_frac = g.zero_row_voxels() / ng if prec == "f64" else 0.0
+        nl, vb, vf = launch_mix(prec, s_, m_, pairs, zero_frac)
         bytes_per_launch = vb / nl * ng
         flops_per_launch = vf / nl * ng
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
@@ -459,6 +472,7 @@ def main():
                      "avg_launch_us": avg_launch_ms * 1e3, "launches_per_run": term_launches,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "algorithmic_flops_per_launch": flops_per_launch, "chain_field_bytes": chain_bytes,
+                     "zero_row_fraction": zero_frac,
                      "l2_resident": l2_resident, "l2_peak_gbs": l2_peak, "l2_frac": achieved_gbs / l2_peak,
                      "hbm_frac": hbm_frac, "hbm_achieved_gbs": achieved_gbs, "alu_frac": alu_frac})
         # stencil applications per time step: the residual and s m - 1 Taylor terms

@@ -270,6 +270,15 @@ ET_API int et_cn_iteration_cap(const et_grid* g, double tau, double rtol);
  * and copies the latest step's estimate (relative to max|u^n|) to *estimate. */
 ET_API et_status et_get_truncation(et_grid* g, double* estimate);
 
+/* Voxels of the grid that lie in warp rows (32 x-consecutive voxels of one
+ * grid row) without off-diagonal entries of the operator: every face weight
+ * of the row's voxels is zero (D = 0 there and, for the conservative operator,
+ * on one side of each face).  A Taylor term of the FP64 form there is
+ * dt z + beta b (two FP64 instructions and 32 bytes a voxel instead of eight
+ * and 56); the results are those of the full stencil, whose skipped products
+ * are exact zeros.  Counted by et_set_coeffs; synchronises the stream. */
+ET_API et_status et_get_zero_rows(et_grid* g, long long* voxels);
+
 /* Grid facts: n voxels, bytes of the workspace actually used, and the
  * diffusion bound rmax (0 before et_set_coeffs). */
 ET_API et_status et_get_info(const et_grid* g, long long* nvoxels, size_t* ws_used, double* rmax);

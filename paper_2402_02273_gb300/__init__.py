@@ -99,6 +99,7 @@ _SIGS = {
     "et_probe_alu_scratch_bytes": ([], ctypes.c_size_t),
     "et_probe_alu": ([_VP, ctypes.c_size_t, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "et_get_truncation": ([_VP, ctypes.POINTER(_D)], _I),
+    "et_get_zero_rows": ([_VP, ctypes.POINTER(ctypes.c_longlong)], _I),
     "et_set_coeffs_scaled": ([_VP, _VP, _D, _D, _I, _I, _VP], _I),
     "et_cn_run": ([_VP, _VP, _D, _I, _D, _I, _VP], _I),
     "et_cn_iteration_cap": ([_VP, _D, _D], _I),
@@ -295,6 +296,12 @@ class Grid:
 
     def cn_iteration_cap(self, tau, rtol=1e-12):
         return int(self.lib.et_cn_iteration_cap(self.handle, float(tau), float(rtol)))
+
+    def zero_row_voxels(self):
+        """Voxels in warp rows without off-diagonal entries (their terms skip the stencil)."""
+        v = ctypes.c_longlong()
+        self._chk(self.lib.et_get_zero_rows(self.handle, ctypes.byref(v)))
+        return v.value
 
     def truncation(self):
         """A-posteriori truncation estimate of the latest step (relative to max|u^n|)."""

@@ -43,12 +43,14 @@ struct Layout {
     size_t partial;   // 3 * kStatsBlocks doubles
     size_t wnorm;     // 2 * kBlockY * nblocks: the residual warps' max |b|, max |u^n|
     size_t npartial;  // 2 * kStatsBlocks doubles: the stats blocks' maxima of those
+    size_t zrow;      // one byte per warp row: rows without off-diagonal entries
     size_t misc;      // counters, flags, info slots
     size_t total;
     unsigned nblocks;
 };
 
-constexpr size_t kMiscBytes = 2048;  // counters, flags, info slot; truncation estimate at 1024, CN scalars at 1536
+constexpr size_t kMiscBytes = 2048;  // counters, flags, info slot; truncation estimate at 1024, CN scalars at 1536,
+                                     // zero-row count at 1600
 
 bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     if (nx <= 0 || ny <= 0 || nz <= 0) return false;
@@ -76,6 +78,13 @@ bool make_layout(int nx, int ny, int nz, et_precision prec, Layout* L) {
     L->partial = take(3ull * 8ull * kStatsBlocks);
     L->wnorm = take(2ull * 8ull * kBlockY * nb);
     L->npartial = take(2ull * 8ull * kStatsBlocks);
+    {
+        Geom G;
+        G.nx = nx;
+        G.ny = ny;
+        G.nz = nz;
+        L->zrow = take((size_t)zero_row_bytes(G));
+    }
     L->misc = take(kMiscBytes);
     L->total = off;
     return true;
@@ -178,6 +187,8 @@ struct et_grid {
     unsigned long long* wnorm;  // residual warps' norm slots of the truncation estimate
     double* npartial;           // the stats blocks' maxima of those
     double* trunc_est;          // the latest step's estimate
+    unsigned char* zrow;        // rows without off-diagonal entries (Weights::zrow)
+    unsigned long long* zrow_count;  // voxels in those rows
     // Crank-Nicolson: device scalars of the solve and the captured step
     CnScalars* cn_sc;
     cudaGraphExec_t cn_exec;
@@ -282,6 +293,8 @@ Buffers<T> typed_buffers(et_grid* g) {
     Buffers<T> B;
     for (int a = 0; a < 4; ++a) B.W.w[a] = g->prec == ET_F64 ? (const T*)g->w[a] : (const T*)g->wt[a];
     B.W.w[4] = nullptr;
+    // the FP64 term kernel skips the rows without off-diagonal entries
+    B.W.zrow = std::is_same<T, double>::value ? g->zrow : nullptr;
     B.b = (const T*)g->vec[0];
     B.dt = (T*)g->vec[1];
     B.Y[0] = (T*)g->vec[2];
@@ -648,6 +661,13 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
     const double inv_h2 = 1.0 / (g->h * g->h);
     cudaError_t e = launch_coeffs(g->G, D, inv_h2, op, g->w, g->rmax_bits, g->flags, g->stream, dscale);
     if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
+    {
+        Weights<double> W64;
+        for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+        ET_CUDA(g, cudaMemsetAsync(g->zrow_count, 0, sizeof(unsigned long long), g->stream));
+        e = launch_zero_rows(g->G, op, W64, g->zrow, g->zrow_count, g->stream);
+        if (e != cudaSuccess) return fail(g, ET_ERR_CUDA, "zero-row launch: %s", cudaGetErrorString(e));
+    }
     unsigned long long bits = 0;
     unsigned flags = 0;
     ET_CUDA(g, cudaMemcpyAsync(&bits, g->rmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, g->stream));
@@ -1201,6 +1221,8 @@ et_status et_create_grid(int nx, int ny, int nz, double h, et_precision precisio
     g->npartial = (double*)(g->ws + L.npartial);
     g->trunc_est = (double*)(misc + 1024);
     g->cn_sc = (CnScalars*)(misc + 1536);
+    g->zrow = (unsigned char*)(g->ws + L.zrow);
+    g->zrow_count = (unsigned long long*)(misc + 1600);
     g->cn_exec = nullptr;
     g->cn_u = nullptr;
     g->cn_info = nullptr;
@@ -1374,6 +1396,18 @@ et_status et_cn_run(et_grid* g, double* u, double tau, int nsteps, double rtol, 
 int et_cn_iteration_cap(const et_grid* g, double tau, double rtol) {
     if (!g || !g->coeffs_set || !(tau > 0.0) || !(rtol > 0.0 && rtol < 1.0)) return 0;
     return cn_cap_of(g, tau, rtol);
+}
+
+et_status et_get_zero_rows(et_grid* g, long long* voxels) {
+    if (!g) return fail(nullptr, ET_ERR_ARG, "grid is NULL");
+    if (!voxels) return fail(g, ET_ERR_ARG, "voxels must not be NULL");
+    if (!g->coeffs_set) return fail(g, ET_ERR_STATE, "et_set_coeffs has not been called");
+    DeviceGuard dg(g->device);
+    unsigned long long c = 0;
+    ET_CUDA(g, cudaMemcpyAsync(&c, g->zrow_count, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+    ET_CUDA(g, cudaStreamSynchronize(g->stream));
+    *voxels = (long long)c;
+    return ET_OK;
 }
 
 et_status et_get_truncation(et_grid* g, double* estimate) {

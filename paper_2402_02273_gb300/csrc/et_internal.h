@@ -69,6 +69,12 @@ constexpr int kThreads = kBlockX * kBlockY;
 template <typename T>
 struct Weights {
     const T* w[5];
+    // Rows without off-diagonal entries: one byte per warp row (32
+    // x-consecutive voxels of one grid row, index (i >> 5) + ceil(nx / 32) (j +
+    // ny k)), 1 where every off-diagonal weight of its voxels is zero (voxels
+    // in and next to D = 0 tissue); a term there is dt z + beta b.  nullptr:
+    // no rows are skipped.
+    const unsigned char* zrow = nullptr;
 };
 
 // Tile of the stencil kernels: a 32 x 8 block of threads, each thread marching
@@ -83,6 +89,11 @@ struct Geom {
     unsigned nblocks;  // blocks of a one-voxel-per-thread stencil launch (coeffs, residual)
     int sms;           // multiprocessors of the device
 };
+// Marks the warp rows without off-diagonal entries of the operator (zrow, as
+// in Weights) and adds their voxels to *count.
+cudaError_t launch_zero_rows(const Geom& G, et_operator op, const Weights<double>& W, unsigned char* zrow,
+                             unsigned long long* count, cudaStream_t stream);
+inline long long zero_row_bytes(const Geom& G) { return (long long)((G.nx + 31) / 32) * G.ny * G.nz; }
 
 // Device-side accumulation of per-step observables: block partials, a ticket
 // counter for the last-block reduction, the step index and the flag word.

@@ -147,6 +147,32 @@ __device__ __forceinline__ T minus_weight(const Weights<T>& W, int axis, long lo
 }
 
 // ---------------------------------------------------------------------------
+// Rows without off-diagonal entries, one flag per warp row (a ballot of the
+// row's 32 x-consecutive voxels, the weights as the term kernels read them).
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+zero_rows_kernel(Geom G, Weights<double> W, unsigned char* __restrict__ zrow, unsigned long long* count) {
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool in = i < G.nx && j < G.ny;
+    bool nonzero = false;
+    if (in) {
+        const long long p = i + G.sy * j + G.sz * k;
+        nonzero = W.w[0][p] != 0.0 || minus_weight<OP, double>(W, 0, p, 1, i > 0) != 0.0 || W.w[1][p] != 0.0 ||
+                  minus_weight<OP, double>(W, 1, p, G.sy, j > 0) != 0.0 || W.w[2][p] != 0.0 ||
+                  minus_weight<OP, double>(W, 2, p, G.sz, k > 0) != 0.0;
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, nonzero);
+    const unsigned lanes = __ballot_sync(0xffffffffu, in);
+    if (threadIdx.x == 0 && j < G.ny) {
+        const bool zero = any == 0u;
+        zrow[blockIdx.x + (long long)gridDim.x * (j + (long long)G.ny * k)] = zero ? 1 : 0;
+        if (zero) atomicAdd(count, (unsigned long long)__popc(lanes));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // residual: b = L u + rho u (1 - u), diag = rho(1 - 2u) - R - mu (or -R - mu).
 // L u = sum_e w_e u_e - R u_p with R from the coefficient pass: 12 FP64
 // operations per voxel; the range test on u runs on the integer bits.
@@ -307,12 +333,17 @@ __device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<doub
     const double* __restrict__ z = a.zin;
     const double zc = z[p];
     double acc = a.dt[p] * zc;
-    acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : 0.0, acc);
-    acc = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : 0.0, acc);
-    acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : 0.0, acc);
-    acc = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : 0.0, acc);
-    acc = fma(W.w[2][p], (k + 1 < G.nz) ? z[p + G.sz] : 0.0, acc);
-    acc = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? z[p - G.sz] : 0.0, acc);
+    // a warp row without off-diagonal entries (the same for all its lanes)
+    // skips the six products with zero weights, their loads included
+    const bool zero_row = W.zrow && W.zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
+    if (!zero_row) {
+        acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : 0.0, acc);
+        acc = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : 0.0, acc);
+        acc = fma(W.w[1][p], (j + 1 < G.ny) ? z[p + G.sy] : 0.0, acc);
+        acc = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? z[p - G.sy] : 0.0, acc);
+        acc = fma(W.w[2][p], (k + 1 < G.nz) ? z[p + G.sz] : 0.0, acc);
+        acc = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? z[p - G.sz] : 0.0, acc);
+    }
     if (a.has_beta) acc = fma(a.beta, a.b[p], acc);
     if (a.horner) {
         // sub-step 0 by Horner's rule: no running sum to read or write
@@ -647,6 +678,16 @@ int term_blocks_per_sm() {
 }
 
 }  // namespace
+
+cudaError_t launch_zero_rows(const Geom& G, et_operator op, const Weights<double>& W, unsigned char* zrow,
+                             unsigned long long* count, cudaStream_t stream) {
+    const dim3 block(kBlockX, kBlockY, 1);
+    if (op == ET_OP_CONSERVATIVE)
+        zero_rows_kernel<ET_OP_CONSERVATIVE><<<voxel_grid(G), block, 0, stream>>>(G, W, zrow, count);
+    else
+        zero_rows_kernel<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(G, W, zrow, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_coeffs(const Geom& G, const double* D, double inv_h2, et_operator op, double* const w[5],
                           unsigned long long* rmax_bits, unsigned* flags, cudaStream_t stream, double dscale) {

@@ -114,6 +114,12 @@ typedef struct {
                          completes, so its bounded wait runs out: the run
                          stops early and the next synchronising call returns
                          ET_ERR_TIMEOUT (the state u is then not valid) */
+    int every_row;    /* 0 (default): the one-term kernels evaluate only
+                         dt z + beta b in warp rows (32 x-consecutive voxels)
+                         whose operator rows have no off-diagonal entry (D = 0
+                         around them, et_get_zero_rows), which gives the full
+                         stencil's values up to the sign of zeros.  1: every
+                         product in every row (for comparison and timing) */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */
@@ -273,10 +279,12 @@ ET_API et_status et_get_truncation(et_grid* g, double* estimate);
 /* Voxels of the grid that lie in warp rows (32 x-consecutive voxels of one
  * grid row) without off-diagonal entries of the operator: every face weight
  * of the row's voxels is zero (D = 0 there and, for the conservative operator,
- * on one side of each face).  A Taylor term of the FP64 form there is
- * dt z + beta b (two FP64 instructions and 32 bytes a voxel instead of eight
- * and 56); the results are those of the full stencil, whose skipped products
- * are exact zeros.  Counted by et_set_coeffs; synchronises the stream. */
+ * on one side of each face).  A one-term launch evaluates dt z + beta b there
+ * (FP64: two FP64 instructions and 32 bytes a voxel instead of eight and 56),
+ * unless options.every_row is set; the results are those of the full
+ * stencil, whose skipped products are exact zeros, up to the sign of zeros.
+ * The two-term kernels (F32, DF64) evaluate every row.  Counted by
+ * et_set_coeffs; synchronises the stream. */
 ET_API et_status et_get_zero_rows(et_grid* g, long long* voxels);
 
 /* Grid facts: n voxels, bytes of the workspace actually used, and the

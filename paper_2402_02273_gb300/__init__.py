@@ -39,7 +39,7 @@ SCHEMES = {"rosenbrock": ET_SCHEME_ROSENBROCK, "expeuler": ET_SCHEME_EXPEULER}
 class et_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("theta_max", ctypes.c_double), ("shift", ctypes.c_int),
                 ("force_s", ctypes.c_int), ("force_m", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("single_terms", ctypes.c_int), ("timeout_probe_us", ctypes.c_int)]
+                ("single_terms", ctypes.c_int), ("timeout_probe_us", ctypes.c_int), ("every_row", ctypes.c_int)]
 
 
 class et_step_info(ctypes.Structure):
@@ -152,15 +152,16 @@ def _check(rc: int, handle=None):
 
 
 def make_options(tol=0.0, theta_max=0.0, shift=-1, force_s=0, force_m=0, use_graph=True, single_terms=False,
-                 two_terms=False, timeout_probe_us=0):
+                 two_terms=False, timeout_probe_us=0, every_row=False):
     """et_options; single_terms / two_terms force one / two Taylor terms per
     launch (default: the form's own choice); timeout_probe_us is the test hook
-    of the two-term kernel's bounded waits."""
+    of the two-term kernel's bounded waits; every_row evaluates the whole
+    stencil in rows without off-diagonal entries too."""
     if single_terms and two_terms:
         raise ValueError("single_terms and two_terms exclude each other")
     return et_options(float(tol), float(theta_max), int(shift), int(force_s), int(force_m),
                       1 if use_graph else -1, 1 if single_terms else (-1 if two_terms else 0),
-                      int(timeout_probe_us))
+                      int(timeout_probe_us), 1 if every_row else 0)
 
 
 def select_schedule(tau, rmax, rho, scheme="rosenbrock", precision="f64", **opts):

@@ -110,7 +110,7 @@ bool same_coeffs(const CoeffKey& a, const CoeffKey& b) {
     const et_options &x = a.opt, &y = b.opt;
     return eq(x.tol, y.tol) && eq(x.theta_max, y.theta_max) && x.shift == y.shift && x.force_s == y.force_s &&
            x.force_m == y.force_m && x.use_graph == y.use_graph && x.single_terms == y.single_terms &&
-           x.timeout_probe_us == y.timeout_probe_us;
+           x.timeout_probe_us == y.timeout_probe_us && x.every_row == y.every_row;
 }
 
 struct GraphEntry {
@@ -135,6 +135,7 @@ struct ResolvedOptions {
     int shift, force_s, force_m, use_graph;
     int single_terms;  // 1: one term per launch; -1: two where possible; 0: per form
     unsigned long long probe_ns;  // test hook of the two-term kernel's bounded waits (0: off)
+    bool skip_zero_rows;          // one-term kernels skip rows without off-diagonal entries
 };
 
 ResolvedOptions resolve(const et_options* o, et_precision prec) {
@@ -153,6 +154,7 @@ ResolvedOptions resolve(const et_options* o, et_precision prec) {
     r.use_graph = (o && o->use_graph < 0) ? 0 : 1;
     r.single_terms = !o ? 0 : (o->single_terms > 0 ? 1 : (o->single_terms < 0 ? -1 : 0));
     r.probe_ns = (o && o->timeout_probe_us > 0) ? 1000ull * (unsigned long long)o->timeout_probe_us : 0;
+    r.skip_zero_rows = !(o && o->every_row != 0);
     return r;
 }
 
@@ -293,8 +295,8 @@ Buffers<T> typed_buffers(et_grid* g) {
     Buffers<T> B;
     for (int a = 0; a < 4; ++a) B.W.w[a] = g->prec == ET_F64 ? (const T*)g->w[a] : (const T*)g->wt[a];
     B.W.w[4] = nullptr;
-    // the FP64 term kernel skips the rows without off-diagonal entries
-    B.W.zrow = std::is_same<T, double>::value ? g->zrow : nullptr;
+    // the one-term kernels skip the rows without off-diagonal entries
+    B.W.zrow = resolve(g->opt_set ? &g->opt : nullptr, g->prec).skip_zero_rows ? g->zrow : nullptr;
     B.b = (const T*)g->vec[0];
     B.dt = (T*)g->vec[1];
     B.Y[0] = (T*)g->vec[2];
@@ -652,6 +654,7 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
         if (opt->force_s < 0 || opt->force_m < 0) return fail(g, ET_ERR_ARG, "forced s, m must be >= 0");
         if (opt->timeout_probe_us < 0 || opt->timeout_probe_us > 1000000)
             return fail(g, ET_ERR_ARG, "options.timeout_probe_us must be in [0, 1000000]");
+        if (opt->every_row != 0 && opt->every_row != 1) return fail(g, ET_ERR_ARG, "options.every_row must be 0 or 1");
     }
     // cached graphs stay: a run reuses one only if its coefficient scalars match
     g->coeffs_set = false;

@@ -722,6 +722,8 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
         if (options->force_s < 0 || options->force_m < 0) return bfail(b, ET_ERR_ARG, "forced s, m must be >= 0");
         if (options->timeout_probe_us < 0 || options->timeout_probe_us > 1000000)
             return bfail(b, ET_ERR_ARG, "options.timeout_probe_us must be in [0, 1000000]");
+        if (options->every_row != 0 && options->every_row != 1)
+            return bfail(b, ET_ERR_ARG, "options.every_row must be 0 or 1");
     }
     BDeviceGuard dg(b->device);
     clear_graph(b);

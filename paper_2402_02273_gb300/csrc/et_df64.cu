@@ -25,6 +25,7 @@ using namespace df64;
 // and the -z neighbour, which are carried from the previous plane.
 struct PlaneDF {
     float2 dt, wxp, wxm, wyp, wym, zxp, zxm, zyp, zym, zp, wzp, bb, yy, w3;
+    bool zero;  // the warp row has no off-diagonal entries: dt z + beta b only
 };
 
 // One (i, j) column of kTileZ planes of a term in pair arithmetic.  The z-march
@@ -52,18 +53,27 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
     const bool xp = i + 1 < G.nx, xm = i > 0, yp = j + 1 < G.ny, ym = j > 0;
     const int k0 = tz * TZ;
     const int k1 = min(k0 + TZ, G.nz);
+    const long long tiles_x = (G.nx + 31) >> 5;
     auto load = [&](PlaneDF& L, long long q, int k) {
+        L.zero = W.zrow && W.zrow[(i >> 5) + tiles_x * (j + (long long)G.ny * k)];
         L.dt = dtv[q];
-        L.wxp = w0[q];
-        L.wyp = w1[q];
-        L.wzp = w2[q];
-        L.w3 = (OP == ET_OP_LITERAL) ? w3[q] : zero;
-        L.wxm = (OP == ET_OP_CONSERVATIVE && xm) ? w0[q - 1] : zero;
-        L.wym = (OP == ET_OP_CONSERVATIVE && ym) ? w1[q - G.sy] : zero;
-        L.zxp = xp ? z[q + 1] : zero;
-        L.zxm = xm ? z[q - 1] : zero;
-        L.zyp = yp ? z[q + G.sy] : zero;
-        L.zym = ym ? z[q - G.sy] : zero;
+        if (!L.zero) {
+            L.wxp = w0[q];
+            L.wyp = w1[q];
+            L.wzp = w2[q];
+            L.w3 = (OP == ET_OP_LITERAL) ? w3[q] : zero;
+            L.wxm = (OP == ET_OP_CONSERVATIVE && xm) ? w0[q - 1] : zero;
+            L.wym = (OP == ET_OP_CONSERVATIVE && ym) ? w1[q - G.sy] : zero;
+            L.zxp = xp ? z[q + 1] : zero;
+            L.zxm = xm ? z[q - 1] : zero;
+            L.zyp = yp ? z[q + G.sy] : zero;
+            L.zym = ym ? z[q - G.sy] : zero;
+        } else {
+            // every weight of the row is 0, its +z weight (the next plane's -z
+            // weight) included
+            L.wxp = L.wyp = L.wzp = L.w3 = L.wxm = L.wym = zero;
+            L.zxp = L.zxm = L.zyp = L.zym = zero;
+        }
         L.zp = (k + 1 < G.nz) ? z[q + G.sz] : zero;
         L.bb = need_b ? bv[q] : zero;
         L.yy = need_y ? yacc[q] : zero;
@@ -81,11 +91,16 @@ __device__ __forceinline__ void term_column_df64(const Geom& G, const Weights<fl
         const float2 wxm = (OP == ET_OP_CONSERVATIVE) ? cur.wxm : (xm ? cur.w3 : zero);
         const float2 wym = (OP == ET_OP_CONSERVATIVE) ? cur.wym : (ym ? cur.w3 : zero);
         const float2 wzm = (OP == ET_OP_CONSERVATIVE) ? wzm_c : ((k > 0) ? cur.w3 : zero);
-        const float2 acc =
-            a.has_zscale ? stencil<true>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
-                                         cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb)
-                         : stencil<false>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
-                                          cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb);
+        float2 acc;
+        if (cur.zero)
+            acc = a.has_zscale ? stencil_diag<true>(cur.dt, zc, a.zscale, a.has_beta != 0, a.beta, cur.bb)
+                               : stencil_diag<false>(cur.dt, zc, a.zscale, a.has_beta != 0, a.beta, cur.bb);
+        else
+            acc = a.has_zscale
+                      ? stencil<true>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
+                                      cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb)
+                      : stencil<false>(cur.dt, zc, cur.wxp, cur.zxp, wxm, cur.zxm, cur.wyp, cur.zyp, wym, cur.zym,
+                                       cur.wzp, cur.zp, wzm, zm, a.zscale, a.has_beta != 0, a.beta, cur.bb);
         if (a.horner) {
             if (!a.last) {
                 zout[p] = acc;

@@ -177,5 +177,28 @@ __device__ __forceinline__ float2 stencil(float2 dt, float2 zc, float2 wxp, floa
     return has_beta ? df_fma(beta, bval, acc) : acc;
 }
 
+// The same term at a voxel whose six off-diagonal weights are all zero: the
+// operations of stencil() with the products of zero weights left out.  Each
+// left-out step adds an exact zero (a product 0 * z, an error term 0) to a
+// sum, so the result is stencil()'s except possibly for the sign of a zero.
+template <bool ZS>
+__device__ __forceinline__ float2 stencil_diag(float2 dt, float2 zc, float2 zscale, bool has_beta, float2 beta,
+                                               float2 bval) {
+    DotAcc A;
+    dot_first(A, dt, zc);
+    if (!ZS) {
+        if (has_beta) {
+            DotAcc B;
+            B.s = 0.f;
+            B.c = 0.f;
+            dot_add(B, beta, bval);
+            dot_merge(A, B);
+        }
+        return dot_result(A);
+    }
+    const float2 acc = df_mul(zscale, dot_result(A));
+    return has_beta ? df_fma(beta, bval, acc) : acc;
+}
+
 }  // namespace df64
 }  // namespace et

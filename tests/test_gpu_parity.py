@@ -386,29 +386,38 @@ def _zero_row_voxels(D, op):
     return count
 
 
+@pytest.mark.parametrize("precision", FP64_FORMS + ["f32"])
 @pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "expeuler")])
-def test_zero_row_skip_matches_full_stencil_bitwise(et_mod, torch_cuda, op, scheme):
-    """The FP64 term kernel skips the stencil in warp rows without off-diagonal
-    entries (D = 0 around them).  Its count matches the one formed from D on the
-    host, and the state equals, bit for bit, the one of the batched form's
-    one-tile-per-block variant, which runs the same chain and evaluates every
-    product."""
+@pytest.mark.parametrize("shape", [(40, 36, 44), (9, 30, 100), (6, 7, 256)])
+def test_zero_row_skip_matches_full_stencil_bitwise(et_mod, torch_cuda, precision, op, scheme, shape):
+    """The one-term kernels skip the stencil in warp rows without off-diagonal
+    entries (D = 0 around them).  The count matches the one formed from D on
+    the host, and the state equals, bit for bit, the one of the same run with
+    every product evaluated (options.every_row); FP64 also equals the batched
+    form's one-tile-per-block variant, which runs the same chain without the
+    skip.  One term per launch in every form (the two-term kernels evaluate
+    every row); rows of 44 and 100 voxels end in a partial warp row, FP32
+    rows of a multiple of 4 voxels run the four-voxel kernel."""
     torch = torch_cuda
-    shape = (40, 36, 44)
     D, u0 = phantom.case(shape, seed=9, noise=0.1)
     Dd = torch.from_numpy(D).cuda()
-    g = et_mod.Grid(shape)
-    g.set_coeffs(Dd, op=op, scheme=scheme)
-    zr = g.zero_row_voxels()
-    assert zr == _zero_row_voxels(D, op)
-    assert 0 < zr < D.size
-    u = torch.from_numpy(u0.copy()).cuda()
-    g.run(u, 7.3, 3)
-    g.sync_info()
-    B = et_mod.Batch([shape])
-    B.set_coeffs(Dd, [0.025], op=op, scheme=scheme)
-    B.set_variant(0)
-    v = torch.from_numpy(u0.copy()).cuda()
-    B.run(v, 7.3, 3)
-    B.sync_info()
-    assert torch.equal(u, v)
+    states = []
+    for every_row in (False, True):
+        g = et_mod.Grid(shape, precision=precision)
+        g.set_coeffs(Dd, op=op, scheme=scheme, single_terms=True, every_row=every_row)
+        zr = g.zero_row_voxels()
+        assert zr == _zero_row_voxels(D, op)
+        assert 0 < zr < D.size
+        u = torch.from_numpy(u0.copy()).cuda()
+        g.run(u, 7.3, 3)
+        g.sync_info()
+        states.append(u)
+    assert torch.equal(states[0], states[1])
+    if precision == "f64":
+        B = et_mod.Batch([shape])
+        B.set_coeffs(Dd, [0.025], op=op, scheme=scheme)
+        B.set_variant(0)
+        v = torch.from_numpy(u0.copy()).cuda()
+        B.run(v, 7.3, 3)
+        B.sync_info()
+        assert torch.equal(states[0], v)

@@ -45,14 +45,21 @@ HORNER_BYTES = {"f64": 56, "df64": 56, "f32": 28}
 HORNER_FLOPS = {"f64": 15, "df64": 118, "f32": 15}
 TERM_BYTES = {"f64": 72, "df64": 72, "f32": 36}
 TERM_FLOPS = {"f64": 17, "df64": 139, "f32": 17}
-# In warp rows without off-diagonal entries (D = 0 around them) the FP64 term
-# kernel evaluates dt z + beta b only: z, the diagonal and b in, z out (32 B;
-# 48 with the running sum), 1 MUL + 1 FMA = 3 flops (5 with the running sum).
-ZERO_ROW_BYTES = {"horner": 32, "term": 48}
+# In warp rows without off-diagonal entries (D = 0 around them) the one-term
+# FP64 and DF64 kernels evaluate dt z + beta b only: z, the diagonal and b in,
+# z out (4 fields; 6 with the running sum), 1 MUL + 1 FMA = 3 flops (5 with
+# the running sum; DF64 counts its pair arithmetic as 118 / 139 for every
+# voxel, an upper bound).  The DF64 two-term kernel skips the arithmetic of
+# such voxels, but its TMA boxes still bring every field of its tiles, so its
+# bytes are those of every row; the FP32 kernels evaluate every row.
+ZERO_ROW_FIELDS = {"horner": 4, "term": 6}
 ZERO_ROW_FLOPS = {"horner": 3, "term": 5}
+# the kernels whose loads skip those rows: whether their flops do too
+ZERO_ROW_KERNELS = {"term_kernel_f64": True, "term_kernel_df64": True,
+                    "batch_term_f64_kernel": True, "batch_term_df64_kernel": True}
 
 
-def launch_mix(prec, s, m, pairs, zero_frac=0.0):
+def launch_mix(prec, s, m, pairs, zero_frac=0.0, zero_flops=True):
     """(launches, algorithmic bytes, flops) per voxel of one step's term chain.
 
     Sub-step 0 has m - 1 Horner terms, each later sub-step m terms.  With pairs
@@ -60,16 +67,21 @@ def launch_mix(prec, s, m, pairs, zero_frac=0.0):
     that reads z, the weights, the diagonal and b once and writes one z (and the
     sum), so a pair moves the bytes of one single term and does twice its flops.
     zero_frac: the share of voxels in warp rows without off-diagonal entries,
-    whose terms the FP64 kernel evaluates without the stencil."""
+    whose terms move the bytes of 4 (6) fields; zero_flops: their flops are
+    those of dt z + beta b too (else every product is evaluated)."""
     def count(nterms):
         return (nterms // 2, nterms % 2) if pairs else (0, nterms)
     ph, sh = count(m - 1)
     pt, st = count(m)
     launches = ph + sh + (s - 1) * (pt + st)
-    hb = (1 - zero_frac) * HORNER_BYTES[prec] + zero_frac * ZERO_ROW_BYTES["horner"]
-    tb = (1 - zero_frac) * TERM_BYTES[prec] + zero_frac * ZERO_ROW_BYTES["term"]
-    hf = (1 - zero_frac) * HORNER_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["horner"]
-    tf = (1 - zero_frac) * TERM_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["term"]
+    zb = VALUE_BYTES[prec]
+    hb = (1 - zero_frac) * HORNER_BYTES[prec] + zero_frac * zb * ZERO_ROW_FIELDS["horner"]
+    tb = (1 - zero_frac) * TERM_BYTES[prec] + zero_frac * zb * ZERO_ROW_FIELDS["term"]
+    if prec == "df64" or not zero_flops:
+        hf, tf = HORNER_FLOPS[prec], TERM_FLOPS[prec]
+    else:
+        hf = (1 - zero_frac) * HORNER_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["horner"]
+        tf = (1 - zero_frac) * TERM_FLOPS[prec] + zero_frac * ZERO_ROW_FLOPS["term"]
     nbytes = hb * (ph + sh) + tb * (s - 1) * (pt + st)
     flops = hf * (2 * ph + sh) + tf * (s - 1) * (2 * pt + st)
     return launches, nbytes, flops
@@ -146,6 +158,10 @@ def parse():
     ap.add_argument("--adjoint-forms", default="f64,f32")
     ap.add_argument("--no-forms", action="store_true", help="time the plain FP64 form only")
     ap.add_argument("--single-terms", action="store_true", help="one Taylor term per launch in every form")
+    ap.add_argument("--every-row", action="store_true",
+                    help="evaluate the stencil in every row (no zero-row skip) in every form")
+    ap.add_argument("--every-row-forms", default="f64",
+                    help="forms also timed on the 128^3 run with every row evaluated, for comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip timing the batched many-grid form")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--batch-runs", type=int, default=1, help="timed runs of the batched form (one warm-up run)")
@@ -343,14 +359,14 @@ def l2_peak_gbs(et, stream):
     return max(copy, mix), {"copy": copy, "six_in_one_out": mix}
 
 
-def measure_form(et, torch, D, u0, precision, args, stream, flush, timing=True):
+def measure_form(et, torch, D, u0, precision, args, stream, flush, timing=True, every_row=False):
     """Times K bench steps of one precision form; returns a dict of numbers."""
     n = D.size
     g = et.Grid(D.shape, precision=precision, stream=stream)
     Dd = torch.from_numpy(D).to("cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.set_coeffs(Dd, rho=RHO, single_terms=args.single_terms)
+    g.set_coeffs(Dd, rho=RHO, single_terms=args.single_terms, every_row=every_row or args.every_row)
     setup_ms = (time.perf_counter() - t0) * 1e3
     u0d = torch.from_numpy(u0).to("cuda")
     u = torch.empty_like(u0d)
@@ -429,20 +445,22 @@ def main():
         barrier()
         return ms, clocks
 
-    def time_form(Dg, ug, prec):
+    def time_form(Dg, ug, prec, every_row=False):
         """K timed runs of one precision form on grid Dg from ug; a result dict."""
         ng = Dg.size
         edge = Dg.shape[0]
-        g, step_fn, info = measure_form(et, torch, Dg, ug, prec, args, stream, flush)
+        every_row = every_row or args.every_row
+        g, step_fn, info = measure_form(et, torch, Dg, ug, prec, args, stream, flush, every_row=every_row)
         ms, clocks = timed(step_fn)
         term_ms, term_launches, other_launches = g.timing()  # last run of the timed region
         rec = g.sync_info()
         avg_launch_ms = term_ms / max(term_launches, 1)
         s_, m_ = info["s"], info["m"]
         kname, pairs = term_kernel_of(prec, args.single_terms, ng)
-        # the FP64 term kernel skips the stencil in rows without off-diagonal entries
-        zero_frac = g.zero_row_voxels() / ng if prec == "f64" else 0.0
-        nl, vb, vf = launch_mix(prec, s_, m_, pairs, zero_frac)
+        # the one-term kernels skip the stencil in rows without off-diagonal entries
+        zk = ZERO_ROW_KERNELS.get(kname)
+        zero_frac = g.zero_row_voxels() / ng if (zk is not None and not every_row) else 0.0
+        nl, vb, vf = launch_mix(prec, s_, m_, pairs, zero_frac, zero_flops=bool(zk))
         bytes_per_launch = vb / nl * ng
         flops_per_launch = vf / nl * ng
         achieved_gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
@@ -472,7 +490,7 @@ def main():
                      "avg_launch_us": avg_launch_ms * 1e3, "launches_per_run": term_launches,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "algorithmic_flops_per_launch": flops_per_launch, "chain_field_bytes": chain_bytes,
-                     "zero_row_fraction": zero_frac,
+                     "zero_row_fraction": zero_frac, "every_row": every_row,
                      "l2_resident": l2_resident, "l2_peak_gbs": l2_peak, "l2_frac": achieved_gbs / l2_peak,
                      "hbm_frac": hbm_frac, "hbm_achieved_gbs": achieved_gbs, "alu_frac": alu_frac})
         # stencil applications per time step: the residual and s m - 1 Taylor terms
@@ -490,6 +508,13 @@ def main():
     forms = ["f64"] if args.no_forms else [f for f in args.forms.split(",") if f]
     for prec in forms:
         results[prec] = time_form(D, u0, prec)
+
+    # the same forms with the stencil evaluated in every row (no zero-row
+    # skip): the work of a dense 7-point operator, for comparison
+    every = {}
+    if not args.no_forms and not args.every_row:
+        for prec in [f for f in args.every_row_forms.split(",") if f]:
+            every[prec] = time_form(D, u0, prec, every_row=True)
 
     # the FP32 and DF64 forms on a grid whose chain is far beyond the L2, where
     # the HBM fraction applies (the same phantom type and run, larger grid)
@@ -571,30 +596,40 @@ def main():
             # the autotuned variant: two terms per launch in the first half of
             # the index range (F32 / DF64)
             pairs = prec != "f64" and variant < len(tune_us) // 2
+            if not pairs:
+                bkernel = "batch_term_f64_kernel" if (prec == "f64" and variant == 0) else \
+                    ("batch_term_df64_kernel" if prec == "df64" else "batch_term_kernel")
+            else:
+                bkernel = "batch_term2_quad_kernel" if prec == "f32" else "batch_term2_kernel"
+            # voxels in rows without off-diagonal entries, per grid, where the
+            # chosen kernel skips them
+            zk = ZERO_ROW_KERNELS.get(bkernel)
+            zrows = B.zero_row_voxels() if zk is not None else [0] * len(sizes)
+            zfr = [z_i / n_i for z_i, n_i in zip(zrows, sizes)]
+            zf_all = sum(zrows) / nb
             # algorithmic bytes of the term launches over the whole run, per grid
-            term_bytes = sum(n_i * launch_mix(prec, s_i, m_i, pairs)[1]
-                             for n_i, s_i, m_i in zip(sizes, s_list, m_list)) * args.nsteps
+            term_bytes = sum(n_i * launch_mix(prec, s_i, m_i, pairs, z_i, bool(zk))[1]
+                             for n_i, s_i, m_i, z_i in zip(sizes, s_list, m_list, zfr)) * args.nsteps
             gbs = term_bytes / (ms * 1e-3) / 1e9
             # the autotuner's timing of the chosen variant on the first launch
             # of every grid (Horner terms), per term; cold L2 is not enforced
             # between its repeats: the launch streams 4-8 GB, far above L2
             t_us = tune_us[variant]
+            # one Horner term (pair: one launch) over all grids, zero rows at their cost
+            _, hb_v, hf_v = launch_mix(prec, 1, 3 if pairs else 2, pairs, zf_all, bool(zk))
             if prec == "f64":
-                ach = HORNER_FLOPS[prec] * nb / (t_us * 1e-6) / 1e12
+                ach = hf_v * nb / (t_us * 1e-6) / 1e12
+                hbm_b = hb_v * nb / (t_us * 1e-6) / 1e9
                 broof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": ach / fp64_peak}
+                         "frac": ach / fp64_peak, "hbm_frac": hbm_b / hbm_peak}
             else:
-                per_term = HORNER_BYTES[prec] / (2.0 if pairs else 1.0)
+                per_term = hb_v / (2.0 if pairs else 1.0)
                 ach = per_term * nb / (t_us * 1e-6) / 1e9
                 broof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
-            if not pairs:
-                bkernel = "batch_term_kernel"
-            else:
-                bkernel = "batch_term2_quad_kernel" if prec == "f32" else "batch_term2_kernel"
-            broof.update({"kernel": bkernel + (" (two terms per launch" if pairs else " (one term per launch")
+            broof.update({"zero_row_fraction": zf_all, "kernel": bkernel + (" (two terms per launch" if pairs else " (one term per launch")
                           + ", first launch of every grid)", "us_per_term": t_us,
                           "traffic": term_traffic(prec, bkernel, "batch", nb),
-                          "algorithmic_bytes_per_launch": HORNER_BYTES[prec] * nb,
+                          "algorithmic_bytes_per_launch": hb_v * nb,
                           "launch_us": t_us * (2.0 if pairs else 1.0)})
             batch[prec] = {"value": whole_job_rate(world, nb, args.nsteps, ms), "unit": UNIT,
                            "ms_per_run": ms, "voxels": nb, "grids": len(shapes), "steps": args.nsteps,
@@ -726,6 +761,9 @@ def main():
                                      "m": large[p]["info"]["m"], "roofline": large[p]["roofline"],
                                      "clocks": large[p]["clocks"]}
                                  for p in large},
+            "forms_every_row": {p: {"value": every[p]["value"], "ms_per_step": every[p]["ms_per_step"],
+                                    "dtype": p, "roofline": every[p]["roofline"], "clocks": every[p]["clocks"]}
+                                for p in every},
             "stream_probe_gbs": {"l2": l2_peak, "l2_probes": l2_probes, "hbm_copy_1gib": hbm_probe},
             "crank_nicolson": crank,
         }

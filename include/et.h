@@ -114,12 +114,15 @@ typedef struct {
                          completes, so its bounded wait runs out: the run
                          stops early and the next synchronising call returns
                          ET_ERR_TIMEOUT (the state u is then not valid) */
-    int every_row;    /* 0 (default): the one-term kernels evaluate only
-                         dt z + beta b in warp rows (32 x-consecutive voxels)
-                         whose operator rows have no off-diagonal entry (D = 0
-                         around them, et_get_zero_rows), which gives the full
-                         stencil's values up to the sign of zeros.  1: every
-                         product in every row (for comparison and timing) */
+    int every_row;    /* 0 (default): the one-term F64 and DF64 kernels
+                         evaluate only dt z + beta b in warp rows (32
+                         x-consecutive voxels) whose operator rows have no
+                         off-diagonal entry (D = 0 around them,
+                         et_get_zero_rows), and the DF64 two-term kernel at
+                         each voxel whose six face weights are zero; this gives
+                         the full stencil's values up to the sign of zeros.
+                         The F32 kernels evaluate every row.  1: every product
+                         in every row (for comparison and timing) */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */
@@ -283,7 +286,9 @@ ET_API et_status et_get_truncation(et_grid* g, double* estimate);
  * (FP64: two FP64 instructions and 32 bytes a voxel instead of eight and 56),
  * unless options.every_row is set; the results are those of the full
  * stencil, whose skipped products are exact zeros, up to the sign of zeros.
- * The two-term kernels (F32, DF64) evaluate every row.  Counted by
+ * The F64 and DF64 one-term kernels skip such rows, the DF64 two-term kernel
+ * skips the arithmetic of each voxel with six zero weights (its loads are
+ * whole tiles), the F32 kernels evaluate every row.  Counted by
  * et_set_coeffs; synchronises the stream. */
 ET_API et_status et_get_zero_rows(et_grid* g, long long* voxels);
 
@@ -327,7 +332,10 @@ ET_API et_status et_vjp_checkpointed(et_grid* g, double tau, int nsteps, int che
  * every grid whose chain has that term) and one batched stats launch; a run is
  * captured as one CUDA graph.  The term-launch kernel variant (planes per tile,
  * looping or one-tile-per-block grids) is picked by timing the candidates on
- * the batch (et_batch_autotune, or automatically on the first run).
+ * the batch (et_batch_autotune, or automatically on the first run).  As on a
+ * single grid, the FP64 one-tile-per-block kernel and the DF64 kernels skip
+ * the products of rows without off-diagonal entries unless options.every_row
+ * is set (et_batch_set_coeffs marks those rows per grid).
  *  dims: host array of 3*count ints (nx, ny, nz of grid i at 3i); count <= 1024.
  *  D, u: device, the grids' fields concatenated in order (sum of n_i FP64).
  *  rho: host array of count rates.  info: device array of nsteps*count records
@@ -353,6 +361,11 @@ ET_API et_status et_batch_set_variant(et_batch* b, int variant);
 /* Synchronises; copies the latest record of every grid (count records). */
 ET_API et_status et_batch_sync_info(et_batch* b, et_step_info* host_out);
 ET_API et_status et_batch_get_schedule(const et_batch* b, double tau, int* s, int* m);
+/* Voxels of all grids that lie in warp rows without off-diagonal entries (as
+ * et_get_zero_rows, per grid, summed); voxels: host, count entries, the
+ * per-grid figures (NULL: only the total); *total may be NULL.  Marked by
+ * et_batch_set_coeffs; synchronises the stream. */
+ET_API et_status et_batch_get_zero_rows(et_batch* b, long long* voxels, long long* total);
 ET_API et_status et_batch_set_stream(et_batch* b, void* cuda_stream);
 ET_API const char* et_batch_last_error(const et_batch* b);
 ET_API void et_batch_destroy(et_batch* b);

@@ -92,6 +92,7 @@ _SIGS = {
     "et_batch_set_variant": ([_VP, _I], _I),
     "et_batch_sync_info": ([_VP, _VP], _I),
     "et_batch_get_schedule": ([_VP, _D, _VP, _VP], _I),
+    "et_batch_get_zero_rows": ([_VP, _VP, ctypes.POINTER(ctypes.c_longlong)], _I),
     "et_batch_set_stream": ([_VP, _VP], _I),
     "et_batch_last_error": ([_VP], ctypes.c_char_p),
     "et_batch_destroy": ([_VP], None),
@@ -492,6 +493,12 @@ class Batch:
         m = (ctypes.c_int * self.count)()
         self._chk(self.lib.et_batch_get_schedule(self.handle, float(tau), s, m))
         return list(s), list(m)
+
+    def zero_row_voxels(self):
+        """Per grid, the voxels in warp rows without off-diagonal entries."""
+        v = (ctypes.c_longlong * self.count)()
+        self._chk(self.lib.et_batch_get_zero_rows(self.handle, v, None))
+        return list(v)
 
     def split(self, t):
         """Views of a concatenated tensor, one per grid, shaped (nz, ny, nx)."""

@@ -686,6 +686,8 @@ et_status set_coeffs_impl(et_grid* g, const double* D, double rho, et_operator o
         const double rho_c = (scheme == ET_SCHEME_ROSENBROCK) ? rho * (1.0 + 2.0 * kRangeSlack) : 0.0;
         const double nu = ro.shift ? rmax + rho_c : 2.0 * rmax + rho_c;
         g->nu = nu > 0.0 ? nu : 1.0;
+        // the two-term kernel skips voxels without off-diagonal entries too
+        pair_plan_set_skip(g->pair, ro.skip_zero_rows);
     }
     if (g->prec != ET_F64) {
         const double* src[4] = {g->w[0], g->w[1], g->w[2], g->w[3]};

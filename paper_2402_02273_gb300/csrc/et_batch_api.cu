@@ -62,16 +62,20 @@ struct BatchLayout {
     // wpair: F32 pair weights of the residual; ush: F32 / DF64 pair copy of u
     // wnorm: the residual warps' norm slots (2 per warp, 8 warps per residual
     // tile of every grid); npartial: per grid the stats blocks' maxima of them
-    size_t w[5], wt[5], wpair[5], vec[6], stage, ush, partial, wnorm, npartial, desc, tune_desc, misc;
+    // zrow: per grid one byte per warp row without off-diagonal entries
+    // (Weights::zrow), zcount: per grid the voxels of those rows
+    size_t w[5], wt[5], wpair[5], vec[6], stage, ush, partial, wnorm, npartial, desc, tune_desc, misc, zrow, zcount;
     size_t total;
     long long ntot;
     long long res_tiles;  // 32 x 8 residual tiles of all grids
 };
 
-bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L, std::vector<long long>* offs) {
+bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L, std::vector<long long>* offs,
+                  std::vector<long long>* zoffs = nullptr) {
     if (count < 1 || count > kMaxBatch || !dims) return false;
-    long long ntot = 0, res_tiles = 0;
+    long long ntot = 0, res_tiles = 0, zbytes = 0;
     offs->assign(count + 1, 0);
+    if (zoffs) zoffs->assign(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
         if (nx <= 0 || ny <= 0 || nz <= 0) return false;
@@ -79,7 +83,10 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
         (*offs)[i] = ntot;
         ntot += n;
         res_tiles += (long long)((nx + kBlockX - 1) / kBlockX) * ((ny + kBlockY - 1) / kBlockY) * nz;
+        if (zoffs) (*zoffs)[i] = zbytes;
+        zbytes += (long long)((nx + kBlockX - 1) / kBlockX) * ny * nz;
     }
+    if (zoffs) (*zoffs)[count] = zbytes;
     L->res_tiles = res_tiles;
     (*offs)[count] = ntot;
     if (ntot >= (1ll << 40)) return false;
@@ -103,6 +110,8 @@ bool batch_layout(int count, const int* dims, et_precision prec, BatchLayout* L,
     L->desc = take(desc_bytes_per_instance(prec) * count);
     L->tune_desc = take((term_desc_bytes(prec) + pair_desc_bytes(prec) + qpair_desc_bytes(prec)) * count + 256);
     L->misc = take(misc_bytes(count));
+    L->zrow = take((size_t)zbytes);
+    L->zcount = take(8ull * count);
     L->total = off;
     return true;
 }
@@ -118,6 +127,7 @@ struct et_batch {
     int count;
     std::vector<int> dims;
     std::vector<long long> offs;
+    std::vector<long long> zoffs;  // per grid: byte offset of its zero-row flags
     long long ntot;
     double h;
     et_precision prec;
@@ -233,6 +243,10 @@ Weights<T> typed_weights(et_batch* b, int i) {
     Weights<T> W;
     for (int a = 0; a < 5; ++a)
         W.w[a] = b->prec == ET_F64 ? (const T*)field<double>(b, b->L.w[a], i) : field<T>(b, b->L.wt[a], i);
+    // the one-term kernels skip the warp rows without off-diagonal entries
+    // (their products all have zero weights) unless every row is asked for
+    const bool every_row = b->opt_set && b->opt.every_row != 0;
+    W.zrow = every_row ? nullptr : (const unsigned char*)(b->ws + b->L.zrow) + b->zoffs[i];
     return W;
 }
 
@@ -633,8 +647,8 @@ et_status et_batch_create(int count, const int* dims, double h, et_precision pre
     if (precision != ET_F64 && precision != ET_F32 && precision != ET_DF64)
         return bfail(nullptr, ET_ERR_ARG, "unknown precision");
     BatchLayout L;
-    std::vector<long long> offs;
-    if (!batch_layout(count, dims, precision, &L, &offs))
+    std::vector<long long> offs, zoffs;
+    if (!batch_layout(count, dims, precision, &L, &offs, &zoffs))
         return bfail(nullptr, ET_ERR_ARG, "batch of %d grids is empty, too large or has an empty grid", count);
     for (int i = 0; i < count; ++i)
         if (dims[3 * i + 2] > 65535 || (long long)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2] >= (1ll << 31))
@@ -652,6 +666,7 @@ et_status et_batch_create(int count, const int* dims, double h, et_precision pre
     b->count = count;
     b->dims.assign(dims, dims + 3 * count);
     b->offs = offs;
+    b->zoffs = zoffs;
     b->ntot = L.ntot;
     b->h = h;
     b->prec = precision;
@@ -731,12 +746,19 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
     b->table_tau = -1.0;
     const double inv_h2 = 1.0 / (b->h * b->h);
     BT_CUDA(b, cudaMemsetAsync(misc(b), 0, misc_bytes(b->count), b->stream));
+    BT_CUDA(b, cudaMemsetAsync(b->ws + b->L.zcount, 0, 8ull * b->count, b->stream));
     for (int i = 0; i < b->count; ++i) {
         double* w[5];
         for (int a = 0; a < 5; ++a) w[a] = field<double>(b, b->L.w[a], i);
-        const cudaError_t e =
+        cudaError_t e =
             launch_coeffs(geom_of(b, i), D + b->offs[i], inv_h2, op, w, rmax_bits_of(b, i), flags_of(b), b->stream);
         if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "coeffs launch: %s", cudaGetErrorString(e));
+        // the warp rows without off-diagonal entries of this grid's operator
+        Weights<double> W64;
+        for (int a = 0; a < 5; ++a) W64.w[a] = w[a];
+        e = launch_zero_rows(geom_of(b, i), op, W64, (unsigned char*)(b->ws + b->L.zrow) + b->zoffs[i],
+                             (unsigned long long*)(b->ws + b->L.zcount) + i, b->stream);
+        if (e != cudaSuccess) return bfail(b, ET_ERR_CUDA, "zero-row launch: %s", cudaGetErrorString(e));
     }
     std::vector<unsigned long long> bits(b->count);
     unsigned flags = 0;
@@ -750,6 +772,7 @@ et_status et_batch_set_coeffs(et_batch* b, const double* D, const double* rho, e
     b->opt_set = options != nullptr;
     if (options) b->opt = *options;
     const bool shift = !(options && options->shift == 0);
+    for (PairPlan* P : b->pair_plans) pair_plan_set_skip(P, !(options && options->every_row != 0));
     for (int i = 0; i < b->count; ++i) {
         std::memcpy(&b->rmax[i], &bits[i], sizeof(double));
         b->rho[i] = rho[i];
@@ -857,6 +880,22 @@ et_status et_batch_get_schedule(const et_batch* b, double tau, int* s, int* m) {
         if (s) s[i] = S.s;
         if (m) m[i] = S.m;
     }
+    return ET_OK;
+}
+
+et_status et_batch_get_zero_rows(et_batch* b, long long* voxels, long long* total) {
+    if (!b) return bfail(nullptr, ET_ERR_ARG, "batch is NULL");
+    if (!b->coeffs_set) return bfail(b, ET_ERR_STATE, "et_batch_set_coeffs has not been called");
+    BDeviceGuard dg(b->device);
+    std::vector<unsigned long long> c(b->count);
+    BT_CUDA(b, cudaMemcpyAsync(c.data(), b->ws + b->L.zcount, 8ull * b->count, cudaMemcpyDeviceToHost, b->stream));
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    long long sum = 0;
+    for (int i = 0; i < b->count; ++i) {
+        if (voxels) voxels[i] = (long long)c[i];
+        sum += (long long)c[i];
+    }
+    if (total) *total = sum;
     return ET_OK;
 }
 

@@ -52,6 +52,7 @@ struct PairPlan {
     CUtensorMap zj[5];       // 12-row boxes of b, Y0, Y1, Z0, Z1
     const void* zj_ptr[5];
     CUtensorMap w0, w1, w2, dt, b, w3;  // w1: 11 rows; the others 10
+    int skip_zero = 1;
 };
 
 namespace {
@@ -340,6 +341,10 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags, unsig
         const bool kBaseZ = kTable ? a1.base_mode == 2 : (MODE & kModeBaseZ) != 0;
         const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
         const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
+        // DF64 (bound by its pair arithmetic) skips the products of voxels
+        // without off-diagonal entries; the FP32 instances evaluate every
+        // voxel (the test would push the batched FP32 kernel into spills)
+        const bool skip = sizeof(T) == 8 && src.maps(gi)->skip_zero != 0;
         const T* const ysrc = a1.yacc;
         T* const zfirst = kTable ? nullptr : a1.zout;  // nullptr unless the chain is recorded
         T* const zout = a2.zout;
@@ -467,6 +472,49 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags, unsig
             if (store_c) second_store(qc, zb, acen);
             c_w2m = wzpc;
         };
+        // Voxels without off-diagonal entries (six zero face weights; D = 0
+        // around them): the term is dt z + beta b, the stencil's value up to
+        // the sign of a zero.  A warp takes that path only when all its voxels
+        // qualify, so the full path keeps its interleaved code.
+        auto zero_first = [&]() -> bool {  // the first-term voxel on plane L - 1
+            if (!has_b) return true;
+            const T* W0 = reinterpret_cast<const T*>(sp + S::kW0);
+            const T* W1 = reinterpret_cast<const T*>(sp + S::kW1);
+            const T* W2 = reinterpret_cast<const T*>(sp + S::kW2);
+            if (kLit) {
+                const T w3 = reinterpret_cast<const T*>(sp + S::kW3)[b10];
+                return A::zero6(W0[b10], W1[b11], W2[b10], w3, w3, w3);
+            }
+            return A::zero6(W0[b10], W0[b10 - 1], W1[b11], W1[b11 - BX], W2[b10], b_w2m);
+        };
+        auto zero_second = [&]() -> bool {  // the second-term voxel on plane L - 3
+            const T* W0 = reinterpret_cast<const T*>(s3 + S::kW0);
+            const T* W1 = reinterpret_cast<const T*>(s3 + S::kW1);
+            const T* W2 = reinterpret_cast<const T*>(s3 + S::kW2);
+            if (kLit) {
+                const T w3 = reinterpret_cast<const T*>(s3 + S::kW3)[c10];
+                return A::zero6(W0[c10], W1[c11], W2[c10], w3, w3, w3);
+            }
+            return A::zero6(W0[c10], W0[c10 - 1], W1[c11], W1[c11 - BX], W2[c10], c_w2m);
+        };
+        auto first_diag = [&](int q) {
+            if (!has_b) return;
+            const T zc = reinterpret_cast<const T*>(sp + S::kZj)[bz];
+            const T dt = reinterpret_cast<const T*>(sp + S::kDt)[b10];
+            const T bval = hb1 ? reinterpret_cast<const T*>(sp + S::kB)[b10] : zero;
+            za[(q & 3) * kHalo + t] = kZs ? A::template diag<true>(dt, zc, zscale1, hb1, beta1, bval)
+                                          : A::template diag<false>(dt, zc, zscale1, hb1, beta1, bval);
+            b_zm = zc;
+            b_w2m = reinterpret_cast<const T*>(sp + S::kW2)[b10];
+        };
+        auto second_diag = [&](int q) {
+            const T acen = za[(q & 3) * kHalo + ca];
+            const T dt = reinterpret_cast<const T*>(s3 + S::kDt)[c10];
+            const T bval = hb2 ? reinterpret_cast<const T*>(s3 + S::kB)[c10] : zero;
+            const T zb = A::template diag<false>(dt, acen, zero, hb2, beta2, bval);
+            if (store_c) second_store(q, zb, acen);
+            c_w2m = reinterpret_cast<const T*>(s3 + S::kW2)[c10];
+        };
 
         // Plane L arrives: the first term runs on plane L - 1, the second on
         // plane L - 3, whose z_a neighbours were all written in earlier
@@ -496,8 +544,18 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags, unsig
             ok = advance();
             // (a first term from a stage whose load failed is never read: the
             // block stops at the vote below)
-            if (has_c) both(L - 1, L - 3);
-            else first(L - 1);
+            if (has_c) {
+                if (skip && __all_sync(0xffffffffu, zero_first() && zero_second())) {
+                    first_diag(L - 1);
+                    second_diag(L - 3);
+                } else {
+                    both(L - 1, L - 3);
+                }
+            } else if (skip && __all_sync(0xffffffffu, zero_first())) {
+                first_diag(L - 1);
+            } else {
+                first(L - 1);
+            }
             if (timed_out(ok)) return;
         }
         // plane k1 - 1: its z_a neighbours are complete
@@ -683,6 +741,10 @@ PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const w
 
 void pair_plan_destroy(PairPlan* P) { delete P; }
 
+void pair_plan_set_skip(PairPlan* P, bool skip) {
+    if (P) P->skip_zero = skip ? 1 : 0;
+}
+
 bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out) {
     if (!P) return false;
     int zi = -1;
@@ -690,6 +752,7 @@ bool pair_maps(const PairPlan* P, const void* zin, PairMaps* out) {
         if (P->zj_ptr[i] == zin) zi = i;
     if (zi < 0) return false;
     out->zj = P->zj[zi];
+    out->skip_zero = P->skip_zero;
     out->w0 = P->w0;
     out->w1 = P->w1;
     out->w2 = P->w2;
@@ -708,6 +771,7 @@ bool pair_maps_for(const PairPlan* P, const Geom& G, et_precision prec, const vo
     out->w1 = P->w1;
     out->w2 = P->w2;
     out->w3 = P->w3;
+    out->skip_zero = P->skip_zero;
     return encode(&out->zj, zin, G, es, bx, 12) && encode(&out->b, b, G, es, bx, 10) &&
            encode(&out->dt, dt, G, es, bx, 10);
 }

@@ -311,6 +311,8 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<float2> W, const 
 // z_j with a two-voxel halo, the weights, the diagonal and b.
 struct PairMaps {
     CUtensorMap zj, w0, w1, w2, dt, b, w3;
+    // voxels whose six off-diagonal weights are zero take dt z + beta b only
+    int skip_zero;
 };
 
 // One grid of a batched two-term launch.
@@ -334,6 +336,9 @@ struct PairPlan;
 PairPlan* pair_plan_create(const Geom& G, et_precision prec, const void* const wt[4], const void* b, const void* dt,
                            const void* const yz[4]);
 void pair_plan_destroy(PairPlan* P);
+// Whether the plan's launches skip the products of voxels without
+// off-diagonal entries (set by et_set_coeffs from options.every_row).
+void pair_plan_set_skip(PairPlan* P, bool skip);
 template <typename T>
 cudaError_t launch_term_pair(const PairPlan* P, const Geom& G, et_operator op, const TermArgs<T>& a1,
                              const TermArgs<T>& a2, unsigned* flags, cudaStream_t stream,

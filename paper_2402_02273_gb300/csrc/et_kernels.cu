@@ -597,13 +597,15 @@ __global__ void __launch_bounds__(kThreads) batch_term_f64_kernel(const BatchTer
     const int di = find_desc(d, count, tile);
     copy_desc(sd, d + di);
     __syncthreads();
-    const long long lt = tile - sd.tile_begin;
-    const int tiles_x = (sd.G.nx + kBlockX - 1) / kBlockX;
-    const int tiles_y = (sd.G.ny + kBlockY - 1) / kBlockY;
-    const int i = (int)(lt % tiles_x) * kBlockX + threadIdx.x;
-    const long long rest = lt / tiles_x;
-    const int j = (int)(rest % tiles_y) * kBlockY + threadIdx.y;
-    const int k = (int)(rest / tiles_y);
+    // a grid's tiles number fewer than 2^31 (n < 2^31): 32-bit division
+    const unsigned lt = (unsigned)(tile - sd.tile_begin);
+    const unsigned tiles_x = ((unsigned)sd.G.nx + kBlockX - 1) / kBlockX;
+    const unsigned tiles_y = ((unsigned)sd.G.ny + kBlockY - 1) / kBlockY;
+    const unsigned rest = lt / tiles_x;
+    const int i = (int)(lt - rest * tiles_x) * kBlockX + threadIdx.x;
+    const unsigned kk = rest / tiles_y;
+    const int j = (int)(rest - kk * tiles_y) * kBlockY + threadIdx.y;
+    const int k = (int)kk;
     if (i >= sd.G.nx || j >= sd.G.ny) return;
     term_point_f64<OP>(sd.G, sd.W, sd.a, i, j, k);
 }

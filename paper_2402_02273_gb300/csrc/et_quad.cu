@@ -78,41 +78,34 @@ term_quad_kernel(const __grid_constant__ Geom G, const __grid_constant__ Weights
     float4 zc = ld4(z + p);
     float4 zm = k0 > 0 ? ld4(z + p - sz) : zero4;
     float4 wzm = (kCons && k0 > 0) ? ld4(w2 + p - sz) : zero4;  // conservative: w2 of the plane below
-    const unsigned tiles_x = ((unsigned)G.nx + 31u) >> 5;
     for (int k = k0; k < k1; ++k, p += sz) {
-        // the quad's warp row has no off-diagonal entries: dt z + beta b only
-        // (its +z weight, the next plane's -z weight, is then 0 as well)
-        const bool zero_row = W.zrow && W.zrow[(unsigned)(i >> 5) + tiles_x * ((unsigned)j + (unsigned)G.ny * k)];
         const bool has_zp = k + 1 < G.nz;
-        const float4 zp = has_zp ? ld4(z + p + sz) : zero4;  // the next plane's centre
+        const float4 zp = has_zp ? ld4(z + p + sz) : zero4;
+        const float4 zyp = has_yp ? ld4(z + p + sy) : zero4;
+        const float4 zym = has_ym ? ld4(z + p - sy) : zero4;
+        const float4 w0v = ld4(w0 + p);
+        const float4 w1v = ld4(w1 + p);
+        const float4 w2v = ld4(w2 + p);
         const float4 dv = ld4(dtv + p);
         const float4 bq = need_b ? ld4(bv + p) : zero4;
-        float4 zyp = zero4, zym = zero4, w0v = zero4, w1v = zero4, w2v = zero4, w3v = zero4, wym = zero4,
-               wzmk = zero4;
-        if (!zero_row) {
-            zyp = has_yp ? ld4(z + p + sy) : zero4;
-            zym = has_ym ? ld4(z + p - sy) : zero4;
-            w0v = ld4(w0 + p);
-            w1v = ld4(w1 + p);
-            w2v = ld4(w2 + p);
-            if (kCons) {
-                wym = has_ym ? ld4(w1 + p - sy) : zero4;
-                wzmk = wzm;
-            } else {
-                w3v = ld4(w3 + p);
-                wym = has_ym ? w3v : zero4;
-                wzmk = k > 0 ? w3v : zero4;
-            }
+        float4 w3v = zero4, wym, wzmk;
+        if (kCons) {
+            wym = has_ym ? ld4(w1 + p - sy) : zero4;
+            wzmk = wzm;
+        } else {
+            w3v = ld4(w3 + p);
+            wym = has_ym ? w3v : zero4;
+            wzmk = k > 0 ? w3v : zero4;
         }
-        // x neighbours of the quad's end voxels (every lane takes part)
+        // x neighbours of the quad's end voxels
         float zl = __shfl_up_sync(kFull, zc.w, 1);
         float zr = __shfl_down_sync(kFull, zc.x, 1);
         float w0l = __shfl_up_sync(kFull, w0v.w, 1);
-        if (lane == 0 && has_xm && !zero_row) {
+        if (lane == 0 && has_xm) {
             zl = z[p - 1];
             if (kCons) w0l = w0[p - 1];
         }
-        if (lane == 31 && has_xp && !zero_row) zr = z[p + 4];
+        if (lane == 31 && has_xp) zr = z[p + 4];
         if (!has_xm) {
             zl = 0.f;
             w0l = 0.f;
@@ -126,14 +119,12 @@ term_quad_kernel(const __grid_constant__ Geom G, const __grid_constant__ Weights
             const float zxm = e > 0 ? at(zc, e - 1) : zl;
             const float wxm = kCons ? (e > 0 ? at(w0v, e - 1) : w0l) : ((e > 0 || has_xm) ? at(w3v, e) : 0.f);
             float acc = at(dv, e) * at(zc, e);
-            if (!zero_row) {
-                acc = fmaf(at(w0v, e), zxp, acc);
-                acc = fmaf(wxm, zxm, acc);
-                acc = fmaf(at(w1v, e), at(zyp, e), acc);
-                acc = fmaf(at(wym, e), at(zym, e), acc);
-                acc = fmaf(at(w2v, e), at(zp, e), acc);
-                acc = fmaf(at(wzmk, e), at(zm, e), acc);
-            }
+            acc = fmaf(at(w0v, e), zxp, acc);
+            acc = fmaf(wxm, zxm, acc);
+            acc = fmaf(at(w1v, e), at(zyp, e), acc);
+            acc = fmaf(at(wym, e), at(zym, e), acc);
+            acc = fmaf(at(w2v, e), at(zp, e), acc);
+            acc = fmaf(at(wzmk, e), at(zm, e), acc);
             if (a.has_zscale) acc *= a.zscale;
             if (a.has_beta) acc = fmaf(a.beta, at(bq, e), acc);
             set(r, e, acc);

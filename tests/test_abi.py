@@ -184,3 +184,16 @@ def test_bench_launch_mix_and_kernel_choice():
     assert bench.term_kernel_of("f32", False, 160 ** 3) == ("term2_quad_kernel", True)
     assert bench.term_kernel_of("f32", False, 192 ** 3) == ("term2_quad_kernel", True)
     assert bench.term_kernel_of("f32", True, 192 ** 3) == ("term_quad_kernel", False)
+    # rows without off-diagonal entries: z, the diagonal and b in, z out
+    # (4 values per voxel), 3 flops; a share f of them scales in linearly
+    nl, nb, nf = bench.launch_mix("f64", 1, 3, False, zero_frac=0.25)
+    assert nl == 2
+    assert nb == pytest.approx(2 * (0.75 * bench.HORNER_BYTES["f64"] + 0.25 * 32))
+    assert nf == pytest.approx(2 * (0.75 * bench.HORNER_FLOPS["f64"] + 0.25 * 3))
+    _, nb, _ = bench.launch_mix("df64", 1, 3, False, zero_frac=1.0)
+    assert nb == pytest.approx(2 * 32)
+    assert "term2_kernel" not in bench.ZERO_ROW_KERNELS and "term_kernel_df64" in bench.ZERO_ROW_KERNELS
+    # a kernel whose loads skip zero rows but which evaluates every product
+    nl, nb, nf = bench.launch_mix("f32", 1, 3, True, zero_frac=1.0, zero_flops=False)
+    assert nl == 1 and nb == pytest.approx(16) and nf == pytest.approx(2 * bench.HORNER_FLOPS["f32"])
+    assert "term2_quad_kernel" not in bench.ZERO_ROW_KERNELS

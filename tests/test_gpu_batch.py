@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from zero_rows import zero_row_voxels
 from paper_2402_02273_gb300 import phantom
 
 pytestmark = pytest.mark.gpu
@@ -285,3 +286,39 @@ def test_two_term_batch_matches_single_grids(et_mod, torch_cuda, precision):
                 ref = oracle.Problem(Ds[i], rho=PAIR_RHOS[i]).run(us[i], TAU, nsteps)[0]
                 e_max, e_l2 = _errs(got[i], ref)
                 assert e_max <= TOL64 and e_l2 <= TOL64, (v, i, e_max, e_l2)
+
+
+@pytest.mark.parametrize("precision", ["f64", "df64"])
+@pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "expeuler")])
+def test_batch_zero_row_skip_matches_every_row_bitwise(et_mod, torch_cuda, precision, op, scheme):
+    """The batched FP64 one-tile-per-block kernel and the DF64 kernels (one
+    term per launch: warp rows marked per grid by et_batch_set_coeffs; two
+    terms per launch: voxels whose six weights are zero) skip the products
+    of rows without off-diagonal entries.  Every variant gives, bit for bit,
+    the state of the same batch with every product evaluated
+    (options.every_row) and, for FP64 variant 0, the single-grid path's.  Rows
+    of 44 and 100 voxels end in a partial warp row; the last grid has D = 0."""
+    torch = torch_cuda
+    shapes = [(40, 36, 44), (9, 30, 100), (6, 7, 256), (7, 13, 3)]
+    rhos = [0.025, 0.04, 0.015, 0.03]
+    Ds, us = [], []
+    for i, sh in enumerate(shapes):
+        D, u0 = phantom.case(sh, seed=20 + i, noise=0.1)
+        Ds.append(D * (0.0 if i == 3 else 1.0))
+        us.append(u0 if np.any(u0 > 0.1) else np.full(sh, 0.3))
+    nsteps = 3
+    for v in _variants(et_mod, precision):
+        B, skip, _, _ = _batch_run(et_mod, torch, shapes, Ds, us, rhos, nsteps, precision, variant=v, op=op,
+                                   scheme=scheme)
+        assert B.zero_row_voxels() == [zero_row_voxels(D, op) for D in Ds]
+        _, full, _, _ = _batch_run(et_mod, torch, shapes, Ds, us, rhos, nsteps, precision, variant=v, op=op,
+                                   scheme=scheme, every_row=True)
+        for i in range(len(shapes)):
+            assert np.array_equal(skip[i], full[i]), (precision, v, i)
+    if precision == "f64":
+        _, got, _, _ = _batch_run(et_mod, torch, shapes, Ds, us, rhos, nsteps, precision, variant=0, op=op,
+                                  scheme=scheme)
+        for i in range(len(shapes)):
+            want = _single_run(et_mod, torch, Ds[i], us[i], rhos[i], nsteps, precision, op=op, scheme=scheme,
+                               single_terms=True)[0]
+            assert np.array_equal(got[i].reshape(shapes[i]), want), i

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from zero_rows import zero_row_voxels as _zero_row_voxels
 from paper_2402_02273_gb300 import phantom
 
 pytestmark = pytest.mark.gpu
@@ -357,47 +358,18 @@ def test_full_size_128cubed_100_steps_match_oracle(et_mod, torch_cuda, oracle_12
           f"mass {worst[2]:.2e}")
 
 
-def _zero_row_voxels(D, op):
-    """Voxels in warp rows (32 x-consecutive voxels) whose operator rows have no
-    off-diagonal entry, from D alone: conservative faces vanish when either side
-    has D = 0; literal faces towards +e carry D_p + D_q, towards -e 2 D_p."""
-    nz, ny, nx = D.shape
-    zero = np.ones(D.shape, dtype=bool)
-    for ax in range(3):
-        a = 2 - ax  # numpy axis of x, y, z
-        n = D.shape[a]
-        lo = [slice(None)] * 3
-        hi = [slice(None)] * 3
-        lo[a] = slice(0, n - 1)
-        hi[a] = slice(1, n)
-        Dp, Dq = D[tuple(lo)], D[tuple(hi)]
-        if op == "conservative":
-            face = (Dp > 0) & (Dq > 0)  # the face between p and p + e
-            zero[tuple(lo)] &= ~face
-            zero[tuple(hi)] &= ~face
-        else:
-            zero[tuple(lo)] &= ~((Dp + Dq) > 0)  # towards +e
-            zero[tuple(hi)] &= ~(Dq > 0)         # towards -e: 2 D_p of the voxel itself
-    count = 0
-    for x0 in range(0, nx, 32):
-        seg = zero[:, :, x0:x0 + 32]
-        rows = seg.all(axis=2)
-        count += int(rows.sum()) * seg.shape[2]
-    return count
-
-
 @pytest.mark.parametrize("precision", FP64_FORMS + ["f32"])
 @pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "expeuler")])
 @pytest.mark.parametrize("shape", [(40, 36, 44), (9, 30, 100), (6, 7, 256)])
 def test_zero_row_skip_matches_full_stencil_bitwise(et_mod, torch_cuda, precision, op, scheme, shape):
-    """The one-term kernels skip the stencil in warp rows without off-diagonal
-    entries (D = 0 around them).  The count matches the one formed from D on
-    the host, and the state equals, bit for bit, the one of the same run with
-    every product evaluated (options.every_row); FP64 also equals the batched
-    form's one-tile-per-block variant, which runs the same chain without the
-    skip.  One term per launch in every form (the two-term kernels evaluate
-    every row); rows of 44 and 100 voxels end in a partial warp row, FP32
-    rows of a multiple of 4 voxels run the four-voxel kernel."""
+    """The one-term FP64 and DF64 kernels skip the stencil in warp rows
+    without off-diagonal entries (D = 0 around them).  The count matches the
+    one formed from D on the host, and the state equals, bit for bit, the one
+    of the same run with every product evaluated (options.every_row); FP64
+    also equals the batched form's one-tile-per-block variant, which skips the
+    same rows.  One term per launch in every form; rows of 44 and 100 voxels
+    end in a partial warp row, FP32 rows of a multiple of 4 voxels run the
+    four-voxel kernel (which evaluates every row)."""
     torch = torch_cuda
     D, u0 = phantom.case(shape, seed=9, noise=0.1)
     Dd = torch.from_numpy(D).cuda()
@@ -421,3 +393,31 @@ def test_zero_row_skip_matches_full_stencil_bitwise(et_mod, torch_cuda, precisio
         B.run(v, 7.3, 3)
         B.sync_info()
         assert torch.equal(states[0], v)
+
+
+@pytest.mark.parametrize("precision", ["df64", "f32"])
+@pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "expeuler")])
+@pytest.mark.parametrize("shape", [(40, 36, 44), (9, 30, 100)])
+@pytest.mark.parametrize("force_s", [0, 2])
+def test_two_term_zero_voxel_skip_matches_every_product_bitwise(et_mod, torch_cuda, precision, op, scheme, shape,
+                                                                force_s):
+    """Two terms per launch: the TMA-fed DF64 kernel evaluates dt z + beta b
+    alone at voxels whose six off-diagonal weights are zero (first and second
+    term, halo voxels included).  Its states equal, bit for bit, those of the
+    same runs with every product evaluated (options.every_row) and those of
+    one term per launch; with s = 2 the running-sum pairs of the second
+    sub-step run too.  FP32 (every voxel evaluated) is checked the same way."""
+    torch = torch_cuda
+    D, u0 = phantom.case(shape, seed=13, noise=0.1)
+    Dd = torch.from_numpy(D).cuda()
+    states = []
+    for every_row, single in ((False, False), (True, False), (False, True)):
+        g = et_mod.Grid(shape, precision=precision)
+        g.set_coeffs(Dd, op=op, scheme=scheme, every_row=every_row, single_terms=single, two_terms=not single,
+                     force_s=force_s, force_m=9 if force_s else 0)
+        u = torch.from_numpy(u0.copy()).cuda()
+        g.run(u, 7.3, 3)
+        g.sync_info()
+        states.append(u)
+    assert torch.equal(states[0], states[1])
+    assert torch.equal(states[0], states[2])

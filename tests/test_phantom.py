@@ -52,3 +52,22 @@ def test_batch_case_ranges():
         assert c["n"] in (96, 112, 128, 144, 160)
         assert 0.01 <= c["rho"] <= 0.05 and 0.5 <= c["dscale"] <= 2.0
         assert c["D"].shape == (c["n"],) * 3 and c["u0"].max() > 0.5
+
+
+def test_zero_row_count_helper_on_hand_cases():
+    """The host count the GPU tests compare et_get_zero_rows with: a lone
+    voxel with D > 0 has no face with D > 0 on both sides (conservative: every
+    row is empty), but its literal row has 2 D_p towards -e and its +x / +y /
+    +z neighbours' literal rows carry D_p + D_q towards it."""
+    import numpy as np
+    from zero_rows import zero_row_voxels
+    D = np.zeros((3, 4, 40))
+    assert zero_row_voxels(D, "conservative") == D.size
+    assert zero_row_voxels(D, "literal") == D.size
+    D[1, 2, 5] = 0.1
+    assert zero_row_voxels(D, "conservative") == D.size
+    # literal: rows of voxel (z1, y2, x5) and its -x / -y / -z neighbours are
+    # not empty: three warp rows of 32 voxels (y2 and y1 of z1, y2 of z0)
+    assert zero_row_voxels(D, "literal") == D.size - 3 * 32
+    D[1, 2, 6] = 0.1  # a face with D > 0 on both sides
+    assert zero_row_voxels(D, "conservative") == D.size - 32

@@ -479,6 +479,7 @@ et_status enqueue_form(et_grid* g, double* u, const Schedule& S, double hstep, d
     } else {
         Weights<double> W64;
         for (int a = 0; a < 5; ++a) W64.w[a] = g->w[a];
+        W64.zrow = B.W.zrow;  // the term chain's zero rows, skipped by the residual too
         e = launch_residual<T>(g->G, g->op, u, W64, g->rho, dt_shift, 1.0, g->scheme, const_cast<T*>(B.b), B.dt,
                                g->flags, st, g->wnorm);
     }

@@ -186,12 +186,17 @@ __device__ __forceinline__ void residual_point(const Geom& G, const double* __re
     const double up = u[p];
     const double negR = W.w[4][p];
     double Lu = negR * up;
-    Lu = fma(W.w[0][p], (i + 1 < G.nx) ? u[p + 1] : 0.0, Lu);
-    Lu = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? u[p - 1] : 0.0, Lu);
-    Lu = fma(W.w[1][p], (j + 1 < G.ny) ? u[p + G.sy] : 0.0, Lu);
-    Lu = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? u[p - G.sy] : 0.0, Lu);
-    Lu = fma(W.w[2][p], (k + 1 < G.nz) ? u[p + G.sz] : 0.0, Lu);
-    Lu = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? u[p - G.sz] : 0.0, Lu);
+    // a warp row without off-diagonal entries (W.zrow, nullptr: none marked)
+    // skips the six products with zero weights, their loads included
+    const bool zero_row = W.zrow && W.zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
+    if (!zero_row) {
+        Lu = fma(W.w[0][p], (i + 1 < G.nx) ? u[p + 1] : 0.0, Lu);
+        Lu = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? u[p - 1] : 0.0, Lu);
+        Lu = fma(W.w[1][p], (j + 1 < G.ny) ? u[p + G.sy] : 0.0, Lu);
+        Lu = fma(minus_weight<OP, double>(W, 1, p, G.sy, j > 0), (j > 0) ? u[p - G.sy] : 0.0, Lu);
+        Lu = fma(W.w[2][p], (k + 1 < G.nz) ? u[p + G.sz] : 0.0, Lu);
+        Lu = fma(minus_weight<OP, double>(W, 2, p, G.sz, k > 0), (k > 0) ? u[p - G.sz] : 0.0, Lu);
+    }
     const double bp = fma(rho * up, 1.0 - up, Lu);
     double dp;
     if (scheme == ET_SCHEME_ROSENBROCK) dp = fma(-2.0 * rho, up, negR + dt_shift);
@@ -219,6 +224,7 @@ residual_kernel(Geom G, const double* __restrict__ u, Weights<double> W, double 
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
+    pdl_begin();  // launched by launch_pdl
     double babs = 0.0, uabs = 0.0;
     if (i < G.nx && j < G.ny)
         residual_point<OP, T>(G, u, W, rho, dt_shift, dt_scale, scheme, b, dt, flags, i, j, k, &babs, &uabs);
@@ -326,16 +332,20 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
 // FP64 term, one voxel per thread over a (32 x 8 x nz)-block grid.  The FP64
 // kernel is bound by the FP64 pipe, so it is kept lean for full occupancy
 // (no plane loop, operands straight from the kernel parameters).
+// Whether the voxel's warp row has no off-diagonal entries (the same for all
+// its lanes; W.zrow nullptr: none marked).
+__device__ __forceinline__ bool zero_row_of(const Geom& G, const unsigned char* zrow, int i, int j, int k) {
+    return zrow && zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
+}
+
 template <int OP>
 __device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<double>& W, const TermArgs<double>& a,
-                                               int i, int j, int k) {
+                                               int i, int j, int k, bool zero_row) {
     const long long p = i + G.sy * j + G.sz * k;
     const double* __restrict__ z = a.zin;
     const double zc = z[p];
     double acc = a.dt[p] * zc;
-    // a warp row without off-diagonal entries (the same for all its lanes)
-    // skips the six products with zero weights, their loads included
-    const bool zero_row = W.zrow && W.zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
+    // a zero row skips the six products with zero weights, their loads included
     if (!zero_row) {
         acc = fma(W.w[0][p], (i + 1 < G.nx) ? z[p + 1] : 0.0, acc);
         acc = fma(minus_weight<OP, double>(W, 0, p, 1, i > 0), (i > 0) ? z[p - 1] : 0.0, acc);
@@ -373,8 +383,12 @@ term_kernel_f64(Geom G, Weights<double> W, TermArgs<double> a) {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int k = blockIdx.z;
+    // the zero-row marks are written by et_set_coeffs, never by the chain: read
+    // before the wait for the previous grid
+    const bool zero_row = i < G.nx && j < G.ny && zero_row_of(G, W.zrow, i, j, k);
+    pdl_begin();  // launched by launch_pdl
     if (i >= G.nx || j >= G.ny) return;
-    term_point_f64<OP>(G, W, a, i, j, k);
+    term_point_f64<OP>(G, W, a, i, j, k, zero_row);
 }
 
 // ---------------------------------------------------------------------------
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) batch_term_f64_kernel(const BatchTer
     const int j = (int)(rest - kk * tiles_y) * kBlockY + threadIdx.y;
     const int k = (int)kk;
     if (i >= sd.G.nx || j >= sd.G.ny) return;
-    term_point_f64<OP>(sd.G, sd.W, sd.a, i, j, k);
+    term_point_f64<OP>(sd.G, sd.W, sd.a, i, j, k, zero_row_of(sd.G, sd.W.zrow, i, j, k));
 }
 
 // Blocks loop over tiles of TZ planes (grid = resident capacity).
@@ -731,12 +745,10 @@ cudaError_t launch_residual(const Geom& G, et_operator op, const double* u, Weig
                             cudaStream_t stream, unsigned long long* wnorm) {
     const dim3 block(kBlockX, kBlockY, 1);
     if (op == ET_OP_CONSERVATIVE)
-        residual_kernel<ET_OP_CONSERVATIVE, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags, wnorm);
-    else
-        residual_kernel<ET_OP_LITERAL, T><<<voxel_grid(G), block, 0, stream>>>(
-            G, u, W, rho, dt_shift, dt_scale, (int)scheme, b, dt, flags, wnorm);
-    return cudaGetLastError();
+        return launch_pdl(residual_kernel<ET_OP_CONSERVATIVE, T>, voxel_grid(G), block, stream, G, u, W, rho, dt_shift,
+                          dt_scale, (int)scheme, b, dt, flags, wnorm);
+    return launch_pdl(residual_kernel<ET_OP_LITERAL, T>, voxel_grid(G), block, stream, G, u, W, rho, dt_shift,
+                      dt_scale, (int)scheme, b, dt, flags, wnorm);
 }
 
 template <typename T>
@@ -745,10 +757,8 @@ cudaError_t launch_term(const Geom& G, et_operator op, Weights<T> W, const TermA
     const dim3 block(kBlockX, kBlockY, 1);
     if constexpr (std::is_same<T, double>::value) {
         if (op == ET_OP_CONSERVATIVE)
-            term_kernel_f64<ET_OP_CONSERVATIVE><<<voxel_grid(G), block, 0, stream>>>(G, W, a);
-        else
-            term_kernel_f64<ET_OP_LITERAL><<<voxel_grid(G), block, 0, stream>>>(G, W, a);
-        return cudaGetLastError();
+            return launch_pdl(term_kernel_f64<ET_OP_CONSERVATIVE>, voxel_grid(G), block, stream, G, W, a);
+        return launch_pdl(term_kernel_f64<ET_OP_LITERAL>, voxel_grid(G), block, stream, G, W, a);
     }
     if constexpr (std::is_same<T, float>::value) {
         if (quad_eligible(G, W, a)) return launch_term_quad(G, op, W, a, stream);

@@ -98,11 +98,11 @@ def launch_mix(prec, s, m, pairs, zero_frac=0.0, zero_flops=True):
 TERM_TRAFFIC = {
     ("f64", "term_kernel_f64", 128): (131120128 / 128 ** 3, "3bc61db3f5b7"),
     ("f32", "term_quad_kernel", 128): (403712 / 128 ** 3, "a6bae89026da"),
-    ("df64", "term2_kernel", 128): (126326272 / 128 ** 3, "6b1e73fcb9ec"),
-    ("df64", "term2_kernel", 192): (414991360 / 192 ** 3, "6b1e73fcb9ec"),
-    ("f32", "term2_quad_kernel", 160): (80283136 / 160 ** 3, "6ba6fd188ae6"),
-    ("f32", "term2_quad_kernel", 192): (200293888 / 192 ** 3, "6ba6fd188ae6"),
-    ("f32", "batch_term2_quad_kernel", "batch"): (560431104 / 19017728, "6ba6fd188ae6"),
+    ("df64", "term2_kernel", 128): (101615872 / 128 ** 3, "bac2a73d8148"),
+    ("df64", "term2_kernel", 192): (415784704 / 192 ** 3, "bac2a73d8148"),
+    ("f32", "term2_quad_kernel", 160): (101667584 / 160 ** 3, "4cf51af4dc30"),
+    ("f32", "term2_quad_kernel", 192): (200058368 / 192 ** 3, "4cf51af4dc30"),
+    ("f32", "batch_term2_quad_kernel", "batch"): (560926464 / 19017728, "4cf51af4dc30"),
 }
 KERNEL_SOURCE = {"term_kernel_f64": "et_kernels.cu", "term2_kernel": "et_fused.cu",
                  "term_quad_kernel": "et_quad.cu", "term_kernel_df64": "et_df64.cu",

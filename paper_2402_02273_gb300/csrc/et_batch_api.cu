@@ -287,6 +287,8 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
         r.G = geom_of(b, i);
         r.u = u + b->offs[i];
         for (int a = 0; a < 5; ++a) r.W.w[a] = field<double>(b, b->L.w[a], i);
+        // the FP64 residual skips the products of zero rows as the term chain does
+        r.W.zrow = b->prec == ET_F64 ? typed_weights<T>(b, i).zrow : nullptr;
         r.rho = b->rho[i];
         r.dt_shift = (b->scheme == ET_SCHEME_ROSENBROCK ? b->rho[i] : 0.0) - S[i].mu;
         r.dt_scale = b->prec == ET_F64 ? 1.0 : 1.0 / b->nu[i];

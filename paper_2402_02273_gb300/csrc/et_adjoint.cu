@@ -63,7 +63,12 @@ adj_term_kernel(Geom G, Weights<T> W, AdjTermArgs<T> a) {
     const long long p = i + G.sy * j + G.sz * k;
     // w = wscale * wsrc (wsrc = ybar_{k+1} on the first reverse term of a sub-step)
     const T wp = a.wscale * a.wsrc[p];
-    const T off = a.wscale * offdiag_transpose<OP, T>(W, a.wsrc, G, i, j, k, p);
+    // A conservative operator is symmetric: a row without off-diagonal entries
+    // (W.zrow) is a column without them, and its transpose sum is the +0 that
+    // offdiag_transpose forms from zero weights (the sum starts at +0 and every
+    // product with a zero weight adds a zero to it).
+    const bool skip = OP == ET_OP_CONSERVATIVE && zero_row_of(G, W.zrow, i, j, k);
+    const T off = a.wscale * (skip ? T(0) : offdiag_transpose<OP, T>(W, a.wsrc, G, i, j, k, p));
     const T dtp = a.dt[p];
     const T atw = fma(dtp, wp, off);                     // A^T w
     const T sbar = a.gamma * a.ybar_next[p];             // Sbar

@@ -89,6 +89,13 @@ struct Geom {
     unsigned nblocks;  // blocks of a one-voxel-per-thread stencil launch (coeffs, residual)
     int sms;           // multiprocessors of the device
 };
+// Whether voxel (i, j, k)'s warp row (32 x-consecutive voxels) has no
+// off-diagonal entries of the operator (the same for all its lanes; zrow
+// nullptr: none marked).
+__device__ __forceinline__ bool zero_row_of(const Geom& G, const unsigned char* zrow, int i, int j, int k) {
+    return zrow && zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
+}
+
 // Marks the warp rows without off-diagonal entries of the operator (zrow, as
 // in Weights) and adds their voxels to *count.
 cudaError_t launch_zero_rows(const Geom& G, et_operator op, const Weights<double>& W, unsigned char* zrow,

@@ -332,12 +332,6 @@ term_kernel(Geom G, Weights<T> W, TermArgs<T> a) {
 // FP64 term, one voxel per thread over a (32 x 8 x nz)-block grid.  The FP64
 // kernel is bound by the FP64 pipe, so it is kept lean for full occupancy
 // (no plane loop, operands straight from the kernel parameters).
-// Whether the voxel's warp row has no off-diagonal entries (the same for all
-// its lanes; W.zrow nullptr: none marked).
-__device__ __forceinline__ bool zero_row_of(const Geom& G, const unsigned char* zrow, int i, int j, int k) {
-    return zrow && zrow[(i >> 5) + (long long)((G.nx + 31) >> 5) * (j + (long long)G.ny * k)];
-}
-
 template <int OP>
 __device__ __forceinline__ void term_point_f64(const Geom& G, const Weights<double>& W, const TermArgs<double>& a,
                                                int i, int j, int k, bool zero_row) {

@@ -46,6 +46,28 @@ def test_vjp_matches_oracle_adjoint(env, op, scheme):
     assert g_ds == pytest.approx(o_ds, rel=1e-9)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("op", ["conservative", "literal"])
+def test_zero_row_skip_leaves_the_gradient_unchanged(env, precision, op):
+    """The reverse terms of the conservative operator skip the transpose
+    products of rows without off-diagonal entries (a symmetric operator's
+    empty row is an empty column); the forward chains skip them as well.  The
+    gradients equal those with every product evaluated (options.every_row)
+    bit for bit; the literal operator, whose transpose is not empty there,
+    is checked the same way."""
+    et, torch = env
+    shape, tau, K = (12, 30, 44), 7.3, 4
+    D, u0, tgt = _problem(shape, seed=6)
+    got = []
+    for every_row in (False, True):
+        g = et.Grid(shape, precision=precision)
+        g.set_coeffs(torch.from_numpy(D).cuda(), op=op, every_row=every_row)
+        assert g.zero_row_voxels() > 0
+        got.append(g.vjp(torch.from_numpy(u0.copy()).cuda(), tau, K, torch.from_numpy(tgt.copy()).cuda(),
+                         checkpoint_every=2))
+    assert torch.equal(got[0][0], got[1][0]) and got[0][1] == got[1][1] and got[0][2] == got[1][2]
+
+
 def test_checkpoint_spacing_does_not_change_the_gradient(env):
     et, torch = env
     shape, tau, K = (16, 16, 16), 7.3, 7

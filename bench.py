@@ -96,7 +96,7 @@ def launch_mix(prec, s, m, pairs, zero_frac=0.0, zero_flops=True):
 # captured on the first 8 grids of the batch (19.0 M voxels) and scaled to the
 # whole launch by its voxels (traffic grows with them: no re-reads across grids).
 TERM_TRAFFIC = {
-    ("f64", "term_kernel_f64", 128): (55065856 / 128 ** 3, "067e00387a2f"),
+    ("f64", "term_kernel_f64", 128): (32060160 / 128 ** 3, "be16966deb22"),
     ("f32", "term_quad_kernel", 128): (403712 / 128 ** 3, "a6bae89026da"),
     ("df64", "term2_kernel", 128): (101615872 / 128 ** 3, "bac2a73d8148"),
     ("df64", "term2_kernel", 192): (415784704 / 192 ** 3, "bac2a73d8148"),

@@ -119,10 +119,11 @@ typedef struct {
                          x-consecutive voxels) whose operator rows have no
                          off-diagonal entry (D = 0 around them,
                          et_get_zero_rows), and the DF64 two-term kernel at
-                         each voxel whose six face weights are zero; this gives
-                         the full stencil's values up to the sign of zeros.
-                         The F32 kernels evaluate every row.  1: every product
-                         in every row (for comparison and timing) */
+                         each voxel whose six face weights are zero, and the
+                         residual of every form in such rows; this gives the
+                         full stencil's values up to the sign of zeros.  The
+                         F32 term kernels evaluate every row.  1: every
+                         product in every row (for comparison and timing) */
 } et_options;
 
 /* Per-step record written by the device (40 bytes). */
@@ -286,10 +287,10 @@ ET_API et_status et_get_truncation(et_grid* g, double* estimate);
  * (FP64: two FP64 instructions and 32 bytes a voxel instead of eight and 56),
  * unless options.every_row is set; the results are those of the full
  * stencil, whose skipped products are exact zeros, up to the sign of zeros.
- * The F64 and DF64 one-term kernels skip such rows, the DF64 two-term kernel
- * skips the arithmetic of each voxel with six zero weights (its loads are
- * whole tiles), the F32 kernels evaluate every row.  Counted by
- * et_set_coeffs; synchronises the stream. */
+ * The F64 and DF64 one-term kernels and the residual of every form skip such
+ * rows, the DF64 two-term kernel skips the arithmetic of each voxel with six
+ * zero weights (its loads are whole tiles), the F32 term kernels evaluate
+ * every row.  Counted by et_set_coeffs; synchronises the stream. */
 ET_API et_status et_get_zero_rows(et_grid* g, long long* voxels);
 
 /* Grid facts: n voxels, bytes of the workspace actually used, and the

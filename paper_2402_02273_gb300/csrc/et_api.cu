@@ -462,7 +462,8 @@ cudaError_t enqueue_chain(et_grid* g, const Buffers<T>& B, double* u, const Sche
 template <typename T>
 cudaError_t enqueue_pair_residual(et_grid* g, const float2* ush, const Buffers<T>& B, double dt_shift,
                                   cudaStream_t st, unsigned long long* wnorm = nullptr) {
-    const PairResidualArgs R = pair_residual_args(ush, g->wres, g->nu, g->rho, dt_shift, g->scheme);
+    PairResidualArgs R = pair_residual_args(ush, g->wres, g->nu, g->rho, dt_shift, g->scheme);
+    R.W.zrow = B.W.zrow;  // the term chain's zero rows, skipped by the residual too
     return launch_residual_df64<T>(g->G, g->op, R, g->scheme, const_cast<T*>(B.b), B.dt, g->flags, st, wnorm);
 }
 

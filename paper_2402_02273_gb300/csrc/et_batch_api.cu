@@ -297,6 +297,7 @@ et_status build_tables(et_batch* b, double* u, double tau, int variant, std::vec
             float2* wres[5];
             for (int a = 0; a < 5; ++a) wres[a] = pair_weight(b, a, i);
             r.P = pair_residual_args(field<float2>(b, b->L.ush, i), wres, b->nu[i], b->rho[i], r.dt_shift, b->scheme);
+            r.P.W.zrow = typed_weights<T>(b, i).zrow;  // zero rows skipped as in the term chain
         }
         r.b = field<T>(b, b->L.vec[0], i);
         r.dt = field<T>(b, b->L.vec[1], i);

@@ -35,14 +35,21 @@ __device__ __forceinline__ void residual_pair_point(const Geom& G, const PairRes
     const float2 zero = make_float2(0.f, 0.f);
     const float2 uc = ush[p];
     const float2 w4 = W.w[4][p];
-    const bool xm = i > 0, ym = j > 0, zmk = k > 0;
-    const float2 wxm = xm ? (OP == ET_OP_CONSERVATIVE ? W.w[0][p - 1] : W.w[3][p]) : zero;
-    const float2 wym = ym ? (OP == ET_OP_CONSERVATIVE ? W.w[1][p - G.sy] : W.w[3][p]) : zero;
-    const float2 wzm = zmk ? (OP == ET_OP_CONSERVATIVE ? W.w[2][p - G.sz] : W.w[3][p]) : zero;
-    const float2 S = stencil<false>(w4, uc, W.w[0][p], (i + 1 < G.nx) ? ush[p + 1] : zero, wxm, xm ? ush[p - 1] : zero,
-                                    W.w[1][p], (j + 1 < G.ny) ? ush[p + G.sy] : zero, wym, ym ? ush[p - G.sy] : zero,
-                                    W.w[2][p], (k + 1 < G.nz) ? ush[p + G.sz] : zero, wzm, zmk ? ush[p - G.sz] : zero,
-                                    zero, false, zero, zero);
+    float2 S;
+    if (zero_row_of(G, W.zrow, i, j, k)) {
+        // a warp row without off-diagonal entries: the six products have zero
+        // weights (the same sum up to the sign of a zero), their loads skipped
+        S = stencil_diag<false>(w4, uc, zero, false, zero, zero);
+    } else {
+        const bool xm = i > 0, ym = j > 0, zmk = k > 0;
+        const float2 wxm = xm ? (OP == ET_OP_CONSERVATIVE ? W.w[0][p - 1] : W.w[3][p]) : zero;
+        const float2 wym = ym ? (OP == ET_OP_CONSERVATIVE ? W.w[1][p - G.sy] : W.w[3][p]) : zero;
+        const float2 wzm = zmk ? (OP == ET_OP_CONSERVATIVE ? W.w[2][p - G.sz] : W.w[3][p]) : zero;
+        S = stencil<false>(w4, uc, W.w[0][p], (i + 1 < G.nx) ? ush[p + 1] : zero, wxm, xm ? ush[p - 1] : zero,
+                           W.w[1][p], (j + 1 < G.ny) ? ush[p + G.sy] : zero, wym, ym ? ush[p - G.sy] : zero,
+                           W.w[2][p], (k + 1 < G.nz) ? ush[p + G.sz] : zero, wzm, zmk ? ush[p - G.sz] : zero, zero,
+                           false, zero, zero);
+    }
     const float2 one_minus_u = df_add(make_float2(1.f, 0.f), make_float2(-uc.x, -uc.y));
     const float2 bp = df_add(df_mul(R.nu, S), df_mul(R.rho, df_mul(uc, one_minus_u)));
     store_pair(&b[p], bp);

@@ -288,13 +288,14 @@ def test_two_term_batch_matches_single_grids(et_mod, torch_cuda, precision):
                 assert e_max <= TOL64 and e_l2 <= TOL64, (v, i, e_max, e_l2)
 
 
-@pytest.mark.parametrize("precision", ["f64", "df64"])
+@pytest.mark.parametrize("precision", ["f64", "df64", "f32"])
 @pytest.mark.parametrize("op,scheme", [("conservative", "rosenbrock"), ("literal", "expeuler")])
 def test_batch_zero_row_skip_matches_every_row_bitwise(et_mod, torch_cuda, precision, op, scheme):
     """The batched FP64 one-tile-per-block kernel and the DF64 kernels (one
     term per launch: warp rows marked per grid by et_batch_set_coeffs; two
     terms per launch: voxels whose six weights are zero) skip the products
-    of rows without off-diagonal entries.  Every variant gives, bit for bit,
+    of rows without off-diagonal entries, and so do the residuals (FP32 and
+    DF64: the pair-arithmetic one).  Every variant gives, bit for bit,
     the state of the same batch with every product evaluated
     (options.every_row) and, for FP64 variant 0, the single-grid path's.  Rows
     of 44 and 100 voxels end in a partial warp row; the last grid has D = 0."""

@@ -341,10 +341,9 @@ __device__ __forceinline__ void pair_body(const Src& src, unsigned* flags, unsig
         const bool kBaseZ = kTable ? a1.base_mode == 2 : (MODE & kModeBaseZ) != 0;
         const T zscale1 = a1.zscale, beta1 = a1.beta, beta2 = a2.beta, g1 = a1.g, g2 = a2.g, gamma2 = a2.gamma;
         const bool hb1 = a1.has_beta != 0, hb2 = a2.has_beta != 0, last2 = a2.last != 0;
-        // DF64 skips the products of voxels without off-diagonal entries
-        // (15 % fewer instructions; measured 3-6 % faster in the batched
-        // form, 3 % slower on one 128^3 grid); the FP32 instances evaluate
-        // every voxel (the test would push the batched FP32 kernel into spills)
+        // DF64 (bound by its pair arithmetic) skips the products of voxels
+        // without off-diagonal entries; the FP32 instances evaluate every
+        // voxel (the test would push the batched FP32 kernel into spills)
         const bool skip = sizeof(T) == 8 && src.maps(gi)->skip_zero != 0;
         const T* const ysrc = a1.yacc;
         T* const zfirst = kTable ? nullptr : a1.zout;  // nullptr unless the chain is recorded

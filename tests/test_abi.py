@@ -197,3 +197,22 @@ def test_bench_launch_mix_and_kernel_choice():
     nl, nb, nf = bench.launch_mix("f32", 1, 3, True, zero_frac=1.0, zero_flops=False)
     assert nl == 1 and nb == pytest.approx(16) and nf == pytest.approx(2 * bench.HORNER_FLOPS["f32"])
     assert "term2_quad_kernel" not in bench.ZERO_ROW_KERNELS
+
+
+def test_bench_traffic_table_names_existing_sources():
+    """Every steady-state traffic entry of the bench names a kernel whose source
+    file exists and carries a 12-digit SHA-256 prefix; an entry whose prefix
+    no longer matches its file reports no traffic (null) instead of a stale
+    figure."""
+    import importlib.util
+    import re
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for (prec, kernel, grid), (per_voxel, sha) in bench.TERM_TRAFFIC.items():
+        assert prec in ("f64", "f32", "df64") and per_voxel > 0
+        assert re.fullmatch(r"[0-9a-f]{12}", sha)
+        assert bench.source_sha(kernel) is not None, kernel
+        if bench.source_sha(kernel) == sha:
+            assert bench.term_traffic(prec, kernel, grid, 1000) == pytest.approx(per_voxel * 1000)
+    assert bench.term_traffic("f64", "no_such_kernel", 128, 1000) is None
